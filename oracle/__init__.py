@@ -1,0 +1,157 @@
+"""CPU oracle for block-matching motion estimation -- TEST INFRASTRUCTURE ONLY.
+
+Plain single-threaded C (``me_oracle.c``) behind ctypes.  Only the test
+suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py``
+may import this package.  It shares nothing with the CUDA library: no code,
+headers, tables or constants.
+
+Functions (each follows a passage of Jia & Zhang, "Directional Cross Diamond
+Search Algorithm for Fast Block Motion Estimation"):
+
+* :func:`fs`      -- full search, Sec. I / Table IX row "FS";
+* :func:`dcds`    -- DCDS, Sec. III-B steps 1-4, switching strategies one/two;
+                     ``simplified=True`` gives DCDS^S of Sec. IV-C;
+* :func:`search`  -- the same DCDS search with a caller-supplied distortion
+                     function, used for the ideal-condition analysis of
+                     Sec. III-C-2 (Table VII);
+* :func:`evaluate` -- the six measures of Sec. IV (MAD, MSE, NSP, PSNR,
+                     distance and probability relative to FS).
+
+Parity: FS, DCDS and evaluate are pinned by the tests (brute force, Table
+VII, the counts of Sec. III-C-1, Table VI, closed forms).  DCDS^S is
+"parity unpinned": the paper prints only sequence averages for it.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "me_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+BDM_FN = ctypes.CFUNCTYPE(ctypes.c_int64, ctypes.c_void_p, ctypes.c_int, ctypes.c_int)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with the host C compiler (plain -O2, no tuning)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    srcs = [_SRC] + [os.path.join(_HERE, f) for f in os.listdir(_HERE) if f.endswith(".c") and f != "me_oracle.c"]
+    stale = force or not os.path.exists(_LIB) or any(
+        os.path.getmtime(s) > os.path.getmtime(_LIB) for s in srcs)
+    if stale:
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp] + srcs + ["-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            P = ctypes.c_void_p
+            I = ctypes.c_int
+            lib.oracle_sad.restype = ctypes.c_uint32
+            lib.oracle_sad.argtypes = [P, P, I, I, I, I, I, I]
+            lib.oracle_fs_frame.restype = I
+            lib.oracle_fs_frame.argtypes = [P, P, I, I, I, I, I, P, P, P]
+            lib.oracle_dcds_frame.restype = I
+            lib.oracle_dcds_frame.argtypes = [P, P, I, I, I, I, I, I, P, P, P]
+            lib.oracle_search.restype = I
+            lib.oracle_search.argtypes = [BDM_FN, P, I, I, I, I, I, I, P]
+            lib.oracle_eval_frame.restype = I
+            lib.oracle_eval_frame.argtypes = [P, P, I, I, I, I, P, P, P, P]
+            lib.oracle_hcsp_offsets.restype = None
+            lib.oracle_hcsp_offsets.argtypes = [P]
+            _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else ctypes.c_void_p(a.ctypes.data)
+
+
+def _frames(cur, ref):
+    cur = np.ascontiguousarray(cur, dtype=np.uint8)
+    ref = np.ascontiguousarray(ref, dtype=np.uint8)
+    if cur.shape != ref.shape or cur.ndim != 2:
+        raise ValueError("cur and ref must be 2-D uint8 frames of one shape")
+    return cur, ref
+
+
+def sad(cur, ref, bx, by, block, dx, dy) -> int:
+    cur, ref = _frames(cur, ref)
+    return int(_load().oracle_sad(_ptr(cur), _ptr(ref), cur.shape[1], bx, by, block, dx, dy))
+
+
+def hcsp_offsets():
+    out = np.zeros(14, dtype=np.int32)
+    _load().oracle_hcsp_offsets(_ptr(out))
+    return [tuple(int(v) for v in out[2 * i:2 * i + 2]) for i in range(7)]
+
+
+def fs(cur, ref, block, rng):
+    """Full search.  Returns (mv int16[nb,2], sad uint32[nb], nsp uint16[nb])."""
+    cur, ref = _frames(cur, ref)
+    h, w = cur.shape
+    nb = (w // block) * (h // block)
+    mv = np.zeros((nb, 2), np.int16)
+    sd = np.zeros(nb, np.uint32)
+    ns = np.zeros(nb, np.uint16)
+    rc = _load().oracle_fs_frame(_ptr(cur), _ptr(ref), w, h, w, block, rng, _ptr(mv), _ptr(sd), _ptr(ns))
+    if rc:
+        raise ValueError("oracle_fs_frame rejected its arguments")
+    return mv, sd, ns
+
+
+def dcds(cur, ref, block, rng, simplified=False):
+    """DCDS (or DCDS^S).  Returns (mv int16[nb,2], sad uint32[nb], nsp uint16[nb])."""
+    cur, ref = _frames(cur, ref)
+    h, w = cur.shape
+    nb = (w // block) * (h // block)
+    mv = np.zeros((nb, 2), np.int16)
+    sd = np.zeros(nb, np.uint32)
+    ns = np.zeros(nb, np.uint16)
+    rc = _load().oracle_dcds_frame(_ptr(cur), _ptr(ref), w, h, w, block, rng, int(bool(simplified)),
+                                   _ptr(mv), _ptr(sd), _ptr(ns))
+    if rc:
+        raise ValueError("oracle_dcds_frame rejected its arguments")
+    return mv, sd, ns
+
+
+def search(bdm, rng, dx_lim=(-10**6, 10**6), dy_lim=(-10**6, 10**6), simplified=False):
+    """DCDS search with a Python distortion function ``bdm(dx, dy) -> int``.
+
+    Returns (mvx, mvy, bdm_at_mv, nsp).
+    """
+    cb = BDM_FN(lambda _u, dx, dy: int(bdm(dx, dy)))
+    out = (ctypes.c_int64 * 4)()
+    rc = _load().oracle_search(cb, None, rng, dx_lim[0], dx_lim[1], dy_lim[0], dy_lim[1],
+                               int(bool(simplified)), ctypes.cast(out, ctypes.c_void_p))
+    if rc:
+        raise MemoryError("oracle_search failed")
+    return int(out[0]), int(out[1]), int(out[2]), int(out[3])
+
+
+def evaluate(cur, ref, block, mv, mv_fs=None, nsp=None):
+    """The six measures of Sec. IV for one frame.  Returns a dict."""
+    cur, ref = _frames(cur, ref)
+    h, w = cur.shape
+    mv = np.ascontiguousarray(mv, dtype=np.int16)
+    mv_fs = None if mv_fs is None else np.ascontiguousarray(mv_fs, dtype=np.int16)
+    nsp = None if nsp is None else np.ascontiguousarray(nsp, dtype=np.uint16)
+    out = np.zeros(6, np.float64)
+    rc = _load().oracle_eval_frame(_ptr(cur), _ptr(ref), w, h, w, block, _ptr(mv), _ptr(mv_fs),
+                                   _ptr(nsp), _ptr(out))
+    if rc:
+        raise ValueError("oracle_eval_frame rejected its arguments")
+    return dict(mad=out[0], mse=out[1], nsp=out[2], psnr=out[3], distance=out[4], probability=out[5])
