@@ -1,0 +1,368 @@
+"""Benchmark: DCDS macroblocks/s at 1080p on GB300 (plus FS beside it).
+
+One step = one pass of the motion-estimation hot path over one batch:
+  * DCDS over NPAIRS independent 1920x1088 frame pairs (16x16 blocks, +-16)
+    in ONE persistent launch over the global tile queue, replayed from a
+    captured CUDA graph;
+  * motion compensation and the six measures of Sec. IV for every pair
+    (one batched evaluation launch).
+Inputs are resident in HBM and larger than L2 (each pair has its own two
+frames).  The FS field of the same batch (the "true MV" of Sec. II-C) is
+computed before timing for the PSNR/distance comparison, and FS itself is
+timed separately and reported under "fs".
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+W_, H_, B_, R_ = 1920, 1088, 16, 16
+NPAIRS = 48
+WORKLOAD = f"1080p {W_}x{H_} luma, 16x16 blocks, range +-16, {NPAIRS} independent frame pairs per step"
+
+
+def _args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=400)
+    p.add_argument("--warmup", type=int, default=10)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--pairs", type=int, default=NPAIRS)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def _frames(rank, npairs):
+    """Seeded synthetic 1080p sequence; pair i = (frame i+1, frame i)."""
+    from paper_0806_0689_gb300 import synth
+    seq = synth.workload_sequence("1080p", npairs + 1, seed=2000 + 7 * rank, max_motion=R_)
+    return seq
+
+
+# ---------------------------------------------------------------- CPU oracle
+
+def _oracle_worker(args):
+    seq_seed, t, reps = args
+    import oracle
+    from paper_0806_0689_gb300 import synth
+    seq = synth.workload_sequence("1080p", t + 2, seed=seq_seed, max_motion=R_)
+    cur, ref = seq[t + 1], seq[t]
+    n = 0
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        mv, sad, nsp = oracle.dcds(cur, ref, B_, R_)
+        oracle.evaluate(cur, ref, B_, mv, None, nsp)
+        n += len(sad)
+    return n, time.perf_counter() - t0
+
+
+def cpu_baseline(seconds_hint=12.0):
+    """Time the CPU oracle (as it stands) on a bounded sample of the same
+    workload: whole 1080p pairs, DCDS + evaluation, one process per core."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    # one calibration pair to size the sample
+    n, dt = _oracle_worker((2000, 0, 1))
+    reps = max(1, int(seconds_hint / max(dt, 1e-3) / 4))
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(cores) as pool:
+        res = pool.map(_oracle_worker, [(2000, i % 4, reps) for i in range(cores)])
+    wall = time.perf_counter() - t0
+    mbs = sum(r[0] for r in res)
+    busy = max(r[1] for r in res)
+    return {"value": mbs / busy, "unit": "macroblocks/s", "cores": cores, "kind": "oracle",
+            "sample": f"{cores} processes x {reps} whole 1080p pairs each (DCDS + evaluation), "
+                      f"{mbs} macroblocks in {busy:.1f} s (wall {wall:.1f} s)"}
+
+
+# ---------------------------------------------------------------- clocks
+
+class Clocks:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev):
+        self.p = None
+        self.dev = dev
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(dev), f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        out, _ = self.p.communicate(timeout=10)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- reference arm
+
+def run_reference(a, rank, world):
+    if rank != 0:
+        return
+    cb = cpu_baseline()
+    line = {"impl": "reference", "metric": "DCDS macroblocks/s at 1080p", "value": cb["value"],
+            "unit": "macroblocks/s", "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "data": "synthetic", "config": {"workload": WORKLOAD},
+            "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": "macroblocks/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- our arm
+
+def main():
+    a = _args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if a.impl == "reference":
+        return run_reference(a, rank, world)
+
+    # the oracle's process pool is started before the first CUDA call
+    cb = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        cb = cpu_baseline()
+
+    import torch
+    from paper_0806_0689_gb300 import me
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    npairs = a.pairs
+    seq = _frames(rank, npairs)
+    ctx = me.Context(local)
+    nbx, nby = W_ // B_, H_ // B_
+    nb = nbx * nby
+    dev = torch.device("cuda", local)
+    # each pair owns its two frames: no input is shared between pairs
+    curs = [torch.from_numpy(seq[i + 1]).to(dev) for i in range(npairs)]
+    refs = [torch.from_numpy(seq[i]).to(dev) for i in range(npairs)]
+    mv = torch.empty((npairs, nb, 2), dtype=torch.int16, device=dev)
+    sad = torch.empty((npairs, nb), dtype=torch.int32, device=dev)
+    nsp = torch.empty((npairs, nb), dtype=torch.int16, device=dev)
+    mv_fs = torch.empty_like(mv)
+    sad_fs = torch.empty_like(sad)
+    nsp_fs = torch.empty_like(nsp)
+    sums = torch.zeros((npairs, me.ME_NSUMS), dtype=torch.int64, device=dev)
+    sums_fs = torch.zeros_like(sums)
+
+    d_dcds = me.Context.frame_descs((curs[i], refs[i], R_, mv[i], sad[i], nsp[i]) for i in range(npairs))
+    d_fs = me.Context.frame_descs((curs[i], refs[i], R_, mv_fs[i], sad_fs[i], nsp_fs[i]) for i in range(npairs))
+    e_dcds = me.Context.eval_descs((curs[i], refs[i], mv[i], mv_fs[i], nsp[i]) for i in range(npairs))
+    e_fs = me.Context.eval_descs((curs[i], refs[i], mv_fs[i], None, nsp_fs[i]) for i in range(npairs))
+    g_dcds = ctx.me_graph_create(d_dcds, B_, "dcds")
+    g_fs = ctx.me_graph_create(d_fs, B_, "fs")
+    stream = torch.cuda.current_stream()
+
+    # FS reference field (the "true MV"), then its quality
+    ctx.me_graph_launch(g_fs)
+    ctx.me_eval_batch(e_fs, B_, sums_fs)
+    torch.cuda.synchronize()
+
+    def step():
+        ctx.me_graph_launch(g_dcds)
+        ctx.me_eval_batch(e_dcds, B_, sums)
+
+    for _ in range(max(3, a.warmup)):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, events on the launching stream ----
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = Clocks(local)
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for i in range(a.steps):
+        e0, e1, e2 = ev[i]
+        e0.record(stream)
+        ctx.me_graph_launch(g_dcds)
+        e1.record(stream)
+        ctx.me_eval_batch(e_dcds, B_, sums)
+        e2.record(stream)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    if dist:
+        dist.barrier()
+    ms_total = t_start.elapsed_time(t_end)
+    dcds_ms = [e0.elapsed_time(e1) for e0, e1, _ in ev]
+    eval_ms = [e1.elapsed_time(e2) for _, e1, e2 in ev]
+    if dist:
+        t = torch.tensor([ms_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / a.steps
+    mbs_step = npairs * nb
+    value = mbs_step * world / (ms_step * 1e-3)
+
+    # ---- quality of the last step (identical every step) ----
+    s_d = sums.cpu().numpy().view(np.uint64)
+    s_f = sums_fs.cpu().numpy().view(np.uint64)
+    st_d = [ctx.me_stats_from_sums(s_d[i]) for i in range(npairs)]
+    st_f = [ctx.me_stats_from_sums(s_f[i]) for i in range(npairs)]
+    mean = lambda rows, k: float(np.mean([r[k] for r in rows]))
+
+    # ---- FS timed on its own (same batch) ----
+    fs_ms = []
+    for _ in range(3):
+        ctx.me_graph_launch(g_fs)
+    torch.cuda.synchronize()
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.me_graph_launch(g_fs)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        fs_ms.append(e0.elapsed_time(e1))
+
+    # ---- end to end through the C-ABI with host buffers ----
+    h_cur = torch.from_numpy(np.stack(seq[1:npairs + 1])).pin_memory()
+    h_ref = torch.from_numpy(np.stack(seq[0:npairs])).pin_memory()
+    d_cur = torch.empty((npairs, H_, W_), dtype=torch.uint8, device=dev)
+    d_ref = torch.empty_like(d_cur)
+    h_mv = torch.empty((npairs, nb, 2), dtype=torch.int16).pin_memory()
+    h_sad = torch.empty((npairs, nb), dtype=torch.int32).pin_memory()
+    h_nsp = torch.empty((npairs, nb), dtype=torch.int16).pin_memory()
+    h_sums = torch.empty((npairs, me.ME_NSUMS), dtype=torch.int64).pin_memory()
+    de = me.Context.frame_descs((d_cur[i], d_ref[i], R_, mv[i], sad[i], nsp[i]) for i in range(npairs))
+    ee = me.Context.eval_descs((d_cur[i], d_ref[i], mv[i], mv_fs[i], nsp[i]) for i in range(npairs))
+
+    def e2e_step():
+        d_cur.copy_(h_cur, non_blocking=True)
+        d_ref.copy_(h_ref, non_blocking=True)
+        ctx.me_estimate_batch(de, B_, "dcds")
+        ctx.me_eval_batch(ee, B_, sums)
+        h_mv.copy_(mv, non_blocking=True)
+        h_sad.copy_(sad, non_blocking=True)
+        h_nsp.copy_(nsp, non_blocking=True)
+        h_sums.copy_(sums, non_blocking=True)
+
+    for _ in range(3):
+        e2e_step()
+    torch.cuda.synchronize()
+    k2 = max(5, min(50, a.steps // 4))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(k2):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / k2
+    h2d = 2 * npairs * H_ * W_
+    d2h = npairs * nb * (4 + 4 + 2) + npairs * me.ME_NSUMS * 8
+    assert np.array_equal(h_mv.numpy(), mv.cpu().numpy())
+
+    # ---- roofline of the dominant kernel (DCDS) ----
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    dcds_launch_ms = float(np.median(dcds_ms))
+    alg_bytes = npairs * (2 * W_ * H_ + nb * 10)
+    achieved = alg_bytes / (dcds_launch_ms * 1e-3) / 1e9
+    rates, used = ctx.me_absdiff_peak(iters=4096)
+    sad_peak = max(rates)
+    nsp_mean = mean(st_d, "nsp")
+    fs_launch_ms = float(np.median(fs_ms))
+    fs_absdiff = float(np.sum(nsp_fs.cpu().numpy().view(np.uint16).astype(np.float64))) * B_ * B_
+    dcds_absdiff = nsp_mean * nb * npairs * B_ * B_
+    traffic = None
+    try:
+        prof = json.load(open(os.path.join(ROOT, "profiles", "dcds_traffic.json")))
+        if prof.get("kernel_rev") == "dcds-v1":
+            traffic = prof["bytes_per_launch_1080p_%dpairs" % npairs]
+    except Exception:
+        pass
+
+    line = {
+        "metric": "DCDS macroblocks/s at 1080p on 1 GB300; search pts/MB and PSNR vs FS & plain",
+        "value": value, "unit": "macroblocks/s", "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u8", "data": "synthetic (seeded luma video generator; the paper's sequences are not available)",
+        "config": {"workload": WORKLOAD, "block": B_, "range": R_, "pairs_per_step": npairs,
+                   "macroblocks_per_step": mbs_step, "parallelism": f"replicas x{world} (no collective)",
+                   "l2": f"inputs {2 * npairs * W_ * H_ / 1e6:.0f} MB per step > 129 MB L2; no flush"},
+        "quality": {"dcds_nsp_per_mb": nsp_mean, "dcds_psnr_db": mean(st_d, "psnr"),
+                    "fs_psnr_db": mean(st_f, "psnr"), "fs_nsp_per_mb": mean(st_f, "nsp"),
+                    "dcds_mad": mean(st_d, "mad"), "fs_mad": mean(st_f, "mad"),
+                    "dcds_mse": mean(st_d, "mse"), "fs_mse": mean(st_f, "mse"),
+                    "dcds_distance_to_fs": mean(st_d, "distance"),
+                    "dcds_probability_fs": mean(st_d, "probability")},
+        "roofline": {"kernel": "dcds_kernel", "bound": "hbm", "achieved": achieved, "peak": hbm_peak,
+                     "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": traffic,
+                     "peak_source": peak_src, "launch_ms": dcds_launch_ms,
+                     "algorithmic_bytes_per_launch": alg_bytes,
+                     "sad_bound_frac": (dcds_absdiff / (dcds_launch_ms * 1e-3)) / sad_peak},
+        "fs": {"macroblocks_per_s": mbs_step / (fs_launch_ms * 1e-3), "launch_ms": fs_launch_ms,
+               "roofline": {"bound": "alu", "achieved": fs_absdiff / (fs_launch_ms * 1e-3) / 1e12,
+                            "peak": sad_peak / 1e12, "unit": "Tabsdiff/s",
+                            "frac": fs_absdiff / (fs_launch_ms * 1e-3) / sad_peak,
+                            "peak_source": "measured byte-absdiff microbenchmark (me_absdiff_peak)"}},
+        "absdiff_peak_per_s": {"variants": rates, "used": used},
+        "eval_ms": float(np.median(eval_ms)),
+        "e2e": {"value": mbs_step * world / (e2e_ms * 1e-3), "unit": "macroblocks/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+        "gpu_launches": 2 * a.steps,
+        "clocks": clocks,
+    }
+    if cb is not None:
+        line["cpu_baseline"] = cb
+    ctx.me_graph_free(g_dcds)
+    ctx.me_graph_free(g_fs)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,203 @@
+/*
+ * me.h -- C-ABI of libme: block-matching motion estimation on one GB300.
+ *
+ * The library computes, for every non-overlapping B x B block of an 8-bit
+ * luma frame `cur`, the displacement (dx, dy) into the previous frame `ref`
+ * that the chosen search returns (Jia & Zhang, "Directional Cross Diamond
+ * Search Algorithm for Fast Block Motion Estimation", Sec. I: the block
+ * matching problem; Sec. III-B: the DCDS algorithm).
+ *
+ * Conventions shared by every entry point:
+ *   - Frames are row-major uint8, `pitch` bytes per row (the single-frame
+ *     calls use pitch = w).  w and pitch are multiples of 16, w and h are
+ *     multiples of the block size, frame pointers are 16-byte aligned.
+ *   - The block whose top-left pixel is (x, y) in `cur` is compared with the
+ *     block at (x + dx, y + dy) in `ref`.  A displacement is a candidate only
+ *     if |dx| <= range, |dy| <= range and the reference block lies entirely
+ *     inside the frame (no padding).
+ *   - Distortion is the SAD (sum of absolute differences, uint32).  The paper
+ *     uses MAD = SAD / B^2 (Sec. II-C, Sec. IV); every argmin is the same.
+ *   - Outputs are indexed by block in raster order: k = by * (w / B) + bx.
+ *     mv[2k] = dx, mv[2k+1] = dy (int16); sad[k] (uint32); nsp[k] (uint16)
+ *     = the number of distinct candidates evaluated ("number of search
+ *     points", Sec. III-C and Table IX).
+ *   - Every frame and output pointer is DEVICE memory owned by the caller
+ *     (e.g. torch tensors).  The library owns only its context: scratch,
+ *     descriptor tables, captured graphs and tuning results.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t; NULL = the legacy
+ *     default stream).  Outputs are valid once the stream has reached them.
+ *   - Errors: every call returns an me_status; the reason is kept in
+ *     me_last_error(ctx).  ME_ERR_ARG is returned before any launch when an
+ *     argument is invalid.  There is no CPU fallback: without a usable
+ *     sm_103a device me_init fails with ME_ERR_CUDA.
+ *
+ * Thread safety: one context per host thread.  Calls on one context that run
+ * concurrently on different streams share its work-queue counters; at most
+ * ME_MAX_INFLIGHT launches of one context may be in flight at once.
+ */
+#ifndef ME_H
+#define ME_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct me_ctx me_ctx;
+
+typedef enum me_status {
+    ME_OK = 0,
+    ME_ERR_ARG = 1,          /* invalid argument, nothing was launched */
+    ME_ERR_CUDA = 2,         /* a CUDA runtime call failed */
+    ME_ERR_UNSUPPORTED = 3,  /* valid but not provided (e.g. no weights loaded) */
+    ME_ERR_TIMEOUT = 4,      /* a bounded device-side wait gave up */
+    ME_ERR_NOMEM = 5         /* a library-owned allocation failed */
+} me_status;
+
+typedef enum me_algo {
+    ME_ALGO_FS = 0,          /* full search, Sec. I; argmin of (SAD, |dx|+|dy|, dy, dx) */
+    ME_ALGO_DCDS = 1,        /* DCDS, Sec. III-B steps 1-4 */
+    ME_ALGO_DCDS_S = 2,      /* simplified DCDS^S, Sec. IV-C */
+    ME_ALGO_DCDS_LEARNED = 3 /* DCDS from a learned start proposal (not in the paper) */
+} me_algo;
+
+enum { ME_MAX_RANGE = 32, ME_MAX_INFLIGHT = 64 };
+
+/* One frame pair of a batch.  All pointers are device memory. */
+typedef struct me_frame_desc {
+    const uint8_t* cur;
+    const uint8_t* ref;
+    int32_t w, h, pitch;     /* pixels, pixels, bytes */
+    int32_t range;           /* search range R, 1..ME_MAX_RANGE */
+    int16_t* mv;             /* [nb][2] */
+    uint32_t* sad;           /* [nb] */
+    uint16_t* nsp;           /* [nb], may be NULL */
+} me_frame_desc;
+
+/* me_init: create a context on `cuda_device`.  `tune_cache_path` (nullable)
+ * names a text file where me_tune stores the launch shapes it picked; it is
+ * read here if it exists.  Fails with ME_ERR_CUDA when the device is missing
+ * or is not sm_103. */
+int me_init(me_ctx** out, int cuda_device, const char* tune_cache_path);
+
+/* me_free: release the context (waits for nothing; the caller must have
+ * synchronised the streams it used).  NULL is accepted. */
+void me_free(me_ctx* ctx);
+
+/* me_last_error: text of the last failure on this context ("" if none).
+ * The string is owned by the context and valid until the next call. */
+const char* me_last_error(const me_ctx* ctx);
+
+/* me_estimate: motion field of one frame pair (pitch = w).
+ *   block: 8 or 16; range: 1..32; algo: an me_algo value.
+ *   Full search: Sec. I and the FS rows of Table IX.
+ *   DCDS: HCSP at the origin (step 1), then HDSP/VDSP by switching strategy
+ *   one and two until the centre wins (steps 2-3), then the two middle points
+ *   (step 4), Sec. III-B.  A point already evaluated is not evaluated or
+ *   counted again; ties keep the earlier point in the fixed order
+ *   HCSP: (0,0),(-1,0),(+1,0),(0,-1),(0,+1),(-2,0),(+2,0);
+ *   HDSP: (0,-1),(0,+1),(-2,0),(+2,0); VDSP: (-1,0),(+1,0),(0,-2),(0,+2);
+ *   middle points: HDSP (-1,0),(+1,0); VDSP (0,-1),(0,+1).
+ *   DCDS^S (Sec. IV-C): step 4 checks only the middle point on the side of
+ *   the distant point with the smaller SAD (negative side on a tie; both
+ *   middle points when neither distant point is a candidate).
+ *   mv, sad: required; nsp: may be NULL. */
+int me_estimate(me_ctx* ctx, const uint8_t* cur, const uint8_t* ref, int w, int h,
+                int block, int range, int algo,
+                int16_t* mv, uint32_t* sad, uint16_t* nsp, void* stream);
+
+/* me_estimate_batch: many frame pairs (of any sizes and ranges) in one
+ * persistent launch that pulls tiles of blocks from a global work queue.
+ * `block` and `algo` apply to all descriptors.  Results are identical to
+ * calling me_estimate on each pair.  `descs` is HOST memory, read before the
+ * call returns. */
+int me_estimate_batch(me_ctx* ctx, const me_frame_desc* descs, int n, int block, int algo,
+                      void* stream);
+
+/* A captured batch: the descriptor table is uploaded once and the launch
+ * sequence (queue reset + search kernel) is captured in a CUDA graph that
+ * me_graph_launch replays.  The frame and output buffers named by `descs`
+ * must stay allocated while the graph exists. */
+typedef struct me_graph me_graph;
+int me_graph_create(me_ctx* ctx, const me_frame_desc* descs, int n, int block, int algo,
+                    me_graph** out);
+int me_graph_launch(me_ctx* ctx, me_graph* g, void* stream);
+void me_graph_free(me_graph* g);
+
+/* ---------------------------------------------------------------------- */
+/* Evaluation: the six measures of Sec. IV (MAD, MSE, NSP, PSNR, distance  */
+/* to the FS motion vector, probability of finding it).                    */
+/* The device computes exact integer sums; me_stats_from_sums turns them   */
+/* into the measures on the host.                                          */
+/* ---------------------------------------------------------------------- */
+enum {
+    ME_SUM_ABS = 0,        /* sum over the frame of |cur - prediction| */
+    ME_SUM_SQ = 1,         /* sum of (cur - prediction)^2 */
+    ME_SUM_NSP = 2,        /* sum of nsp over blocks (0 if nsp is NULL) */
+    ME_SUM_EQUAL = 3,      /* blocks whose MV equals the FS MV (0 if mv_fs is NULL) */
+    ME_SUM_DIST_Q24 = 4,   /* sum over blocks of round(|mv - mv_fs| * 2^24) */
+    ME_SUM_BLOCKS = 5,     /* number of blocks */
+    ME_SUM_PIXELS = 6,     /* number of pixels */
+    ME_SUM_HAS_FS = 7,     /* 1 if mv_fs was given */
+    ME_NSUMS = 8
+};
+
+typedef struct me_eval_desc {
+    const uint8_t* cur;
+    const uint8_t* ref;
+    int32_t w, h, pitch;
+    const int16_t* mv;     /* [nb][2] */
+    const int16_t* mv_fs;  /* [nb][2] or NULL */
+    const uint16_t* nsp;   /* [nb] or NULL */
+} me_eval_desc;
+
+/* me_eval: motion-compensate `cur` from `ref` with `mv` (prediction of the
+ * pixel (x, y) of block k is ref(x + dx_k, y + dy_k)) and write the
+ * ME_NSUMS uint64 sums to the DEVICE array `sums` (overwritten). */
+int me_eval(me_ctx* ctx, const uint8_t* cur, const uint8_t* ref, int w, int h, int block,
+            const int16_t* mv, const int16_t* mv_fs, const uint16_t* nsp,
+            uint64_t* sums, void* stream);
+
+/* me_eval_batch: one launch over n frames; sums is DEVICE [n][ME_NSUMS]. */
+int me_eval_batch(me_ctx* ctx, const me_eval_desc* descs, int n, int block,
+                  uint64_t* sums, void* stream);
+
+typedef struct me_stats {
+    double mad, mse, nsp, psnr, distance, probability;
+} me_stats;
+
+/* me_stats_from_sums: host-side arithmetic on one frame's sums (HOST array).
+ * PSNR = 10 log10(255^2 / MSE), 100 dB when MSE = 0. */
+int me_stats_from_sums(const uint64_t* sums, me_stats* out);
+
+/* ---------------------------------------------------------------------- */
+/* Launch shapes and the byte-absolute-difference peak.                    */
+/* ---------------------------------------------------------------------- */
+
+/* me_tune: time the candidate launch shapes for (w, h, block, range, algo)
+ * on `stream` with the given frames and keep the fastest in the context
+ * (and in the tune cache file, if one was named).  Outputs are overwritten.
+ * Returns the chosen shape's index in *chosen (nullable). */
+int me_tune(me_ctx* ctx, const uint8_t* cur, const uint8_t* ref, int w, int h, int block,
+            int range, int algo, int16_t* mv, uint32_t* sad, uint16_t* nsp,
+            int* chosen, void* stream);
+
+/* me_absdiff_peak: microbenchmark of the 4-byte SIMD absolute-difference
+ * primitives.  Runs `iters` dependent-chain-free accumulations per thread on
+ * every SM and returns the measured rate in byte-absolute-differences per
+ * second for each variant (out[0..n_variants)), and which variant the
+ * kernels use (*used).  Synchronises `stream`. */
+int me_absdiff_peak(me_ctx* ctx, int iters, double* out, int n_variants, int* used, void* stream);
+
+/* me_check_status: synchronise `stream` and report a device-side error that
+ * a kernel recorded (ME_ERR_TIMEOUT for a bounded wait that gave up); the
+ * recorded flag is cleared. */
+int me_check_status(me_ctx* ctx, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ME_H */

@@ -66,6 +66,10 @@ def _load():
             lib.oracle_fs_frame.argtypes = [P, P, I, I, I, I, I, P, P, P]
             lib.oracle_dcds_frame.restype = I
             lib.oracle_dcds_frame.argtypes = [P, P, I, I, I, I, I, I, P, P, P]
+            lib.oracle_fs_blocks.restype = I
+            lib.oracle_fs_blocks.argtypes = [P, P, I, I, I, I, I, P, I, P, P, P]
+            lib.oracle_dcds_blocks.restype = I
+            lib.oracle_dcds_blocks.argtypes = [P, P, I, I, I, I, I, I, P, I, P, P, P]
             lib.oracle_search.restype = I
             lib.oracle_search.argtypes = [BDM_FN, P, I, I, I, I, I, I, P]
             lib.oracle_eval_frame.restype = I
@@ -125,6 +129,38 @@ def dcds(cur, ref, block, rng, simplified=False):
                                    _ptr(mv), _ptr(sd), _ptr(ns))
     if rc:
         raise ValueError("oracle_dcds_frame rejected its arguments")
+    return mv, sd, ns
+
+
+def fs_blocks(cur, ref, block, rng, idx):
+    """Full search for the raster block indices ``idx`` only."""
+    cur, ref = _frames(cur, ref)
+    h, w = cur.shape
+    idx = np.ascontiguousarray(idx, dtype=np.int32)
+    n = len(idx)
+    mv = np.zeros((n, 2), np.int16)
+    sd = np.zeros(n, np.uint32)
+    ns = np.zeros(n, np.uint16)
+    rc = _load().oracle_fs_blocks(_ptr(cur), _ptr(ref), w, h, w, block, rng, _ptr(idx), n,
+                                  _ptr(mv), _ptr(sd), _ptr(ns))
+    if rc:
+        raise ValueError("oracle_fs_blocks rejected its arguments")
+    return mv, sd, ns
+
+
+def dcds_blocks(cur, ref, block, rng, idx, simplified=False):
+    """DCDS (or DCDS^S) for the raster block indices ``idx`` only."""
+    cur, ref = _frames(cur, ref)
+    h, w = cur.shape
+    idx = np.ascontiguousarray(idx, dtype=np.int32)
+    n = len(idx)
+    mv = np.zeros((n, 2), np.int16)
+    sd = np.zeros(n, np.uint32)
+    ns = np.zeros(n, np.uint16)
+    rc = _load().oracle_dcds_blocks(_ptr(cur), _ptr(ref), w, h, w, block, rng, int(bool(simplified)),
+                                    _ptr(idx), n, _ptr(mv), _ptr(sd), _ptr(ns))
+    if rc:
+        raise ValueError("oracle_dcds_blocks rejected its arguments")
     return mv, sd, ns
 
 

@@ -54,38 +54,59 @@ static int iabs_(int v) { return v < 0 ? -v : v; }
 /* The paper does not say how FS breaks ties; this centre-biased key is */
 /* the stated reading.  nsp = number of candidates evaluated.           */
 /* ------------------------------------------------------------------ */
+static void fs_one(const uint8_t* cur, const uint8_t* ref, int w, int h, int pitch,
+                   int block, int range, int bx, int by, int16_t* mv2, uint32_t* sad1, uint16_t* nsp1)
+{
+    int have = 0, bdx = 0, bdy = 0, count = 0;
+    uint32_t bs = 0;
+    for (int dy = -range; dy <= range; ++dy) {
+        for (int dx = -range; dx <= range; ++dx) {
+            if (bx + dx < 0 || bx + dx > w - block) continue;
+            if (by + dy < 0 || by + dy > h - block) continue;
+            ++count;
+            uint32_t s = oracle_sad(cur, ref, pitch, bx, by, block, dx, dy);
+            int better;
+            if (!have) better = 1;
+            else if (s != bs) better = s < bs;
+            else if (iabs_(dx) + iabs_(dy) != iabs_(bdx) + iabs_(bdy))
+                better = iabs_(dx) + iabs_(dy) < iabs_(bdx) + iabs_(bdy);
+            else if (dy != bdy) better = dy < bdy;
+            else better = dx < bdx;
+            if (better) { have = 1; bs = s; bdx = dx; bdy = dy; }
+        }
+    }
+    mv2[0] = (int16_t)bdx;
+    mv2[1] = (int16_t)bdy;
+    *sad1 = bs;
+    if (nsp1) *nsp1 = (uint16_t)count;
+}
+
 int oracle_fs_frame(const uint8_t* cur, const uint8_t* ref, int w, int h, int pitch,
                     int block, int range, int16_t* mv, uint32_t* sad, uint16_t* nsp)
 {
     if (block <= 0 || w % block || h % block || range < 0) return 1;
     int nbx = w / block, nby = h / block;
-    for (int j = 0; j < nby; ++j) {
+    for (int j = 0; j < nby; ++j)
         for (int i = 0; i < nbx; ++i) {
-            int bx = i * block, by = j * block;
-            int have = 0, bdx = 0, bdy = 0, count = 0;
-            uint32_t bs = 0;
-            for (int dy = -range; dy <= range; ++dy) {
-                for (int dx = -range; dx <= range; ++dx) {
-                    if (bx + dx < 0 || bx + dx > w - block) continue;
-                    if (by + dy < 0 || by + dy > h - block) continue;
-                    ++count;
-                    uint32_t s = oracle_sad(cur, ref, pitch, bx, by, block, dx, dy);
-                    int better;
-                    if (!have) better = 1;
-                    else if (s != bs) better = s < bs;
-                    else if (iabs_(dx) + iabs_(dy) != iabs_(bdx) + iabs_(bdy))
-                        better = iabs_(dx) + iabs_(dy) < iabs_(bdx) + iabs_(bdy);
-                    else if (dy != bdy) better = dy < bdy;
-                    else better = dx < bdx;
-                    if (better) { have = 1; bs = s; bdx = dx; bdy = dy; }
-                }
-            }
             long k = (long)j * nbx + i;
-            mv[2 * k] = (int16_t)bdx;
-            mv[2 * k + 1] = (int16_t)bdy;
-            sad[k] = bs;
-            if (nsp) nsp[k] = (uint16_t)count;
+            fs_one(cur, ref, w, h, pitch, block, range, i * block, j * block,
+                   mv + 2 * k, sad + k, nsp ? nsp + k : NULL);
         }
+    return 0;
+}
+
+/* Full search for the listed blocks only (raster indices idx[0..n)); output
+ * entry t belongs to block idx[t].  Used to check large frames by sampling. */
+int oracle_fs_blocks(const uint8_t* cur, const uint8_t* ref, int w, int h, int pitch,
+                     int block, int range, const int32_t* idx, int n,
+                     int16_t* mv, uint32_t* sad, uint16_t* nsp)
+{
+    if (block <= 0 || w % block || h % block || range < 0) return 1;
+    int nbx = w / block, nb = nbx * (h / block);
+    for (int t = 0; t < n; ++t) {
+        if (idx[t] < 0 || idx[t] >= nb) return 1;
+        fs_one(cur, ref, w, h, pitch, block, range, (idx[t] % nbx) * block, (idx[t] / nbx) * block,
+               mv + 2 * (long)t, sad + t, nsp ? nsp + t : NULL);
     }
     return 0;
 }
@@ -258,6 +279,21 @@ static int64_t sad_cb(void* u, int dx, int dy)
     return (int64_t)oracle_sad(p->cur, p->ref, p->pitch, p->bx, p->by, p->block, dx, dy);
 }
 
+static int dcds_one(const uint8_t* cur, const uint8_t* ref, int w, int h, int pitch,
+                    int block, int range, int simplified, int bx, int by,
+                    int16_t* mv2, uint32_t* sad1, uint16_t* nsp1)
+{
+    sad_user_t u = {cur, ref, pitch, bx, by, block};
+    int64_t out[4];
+    if (oracle_search(sad_cb, &u, range, -bx, w - block - bx, -by, h - block - by, simplified, out))
+        return 1;
+    mv2[0] = (int16_t)out[0];
+    mv2[1] = (int16_t)out[1];
+    *sad1 = (uint32_t)out[2];
+    if (nsp1) *nsp1 = (uint16_t)out[3];
+    return 0;
+}
+
 /* DCDS (or DCDS^S) over every block of a frame, SAD as the BDM. */
 int oracle_dcds_frame(const uint8_t* cur, const uint8_t* ref, int w, int h, int pitch,
                       int block, int range, int simplified,
@@ -265,18 +301,26 @@ int oracle_dcds_frame(const uint8_t* cur, const uint8_t* ref, int w, int h, int 
 {
     if (block <= 0 || w % block || h % block || range < 0) return 1;
     int nbx = w / block, nby = h / block;
-    for (int j = 0; j < nby; ++j) {
+    for (int j = 0; j < nby; ++j)
         for (int i = 0; i < nbx; ++i) {
-            sad_user_t u = {cur, ref, pitch, i * block, j * block, block};
-            int64_t out[4];
-            if (oracle_search(sad_cb, &u, range, -u.bx, w - block - u.bx,
-                              -u.by, h - block - u.by, simplified, out)) return 1;
             long k = (long)j * nbx + i;
-            mv[2 * k] = (int16_t)out[0];
-            mv[2 * k + 1] = (int16_t)out[1];
-            sad[k] = (uint32_t)out[2];
-            if (nsp) nsp[k] = (uint16_t)out[3];
+            if (dcds_one(cur, ref, w, h, pitch, block, range, simplified, i * block, j * block,
+                         mv + 2 * k, sad + k, nsp ? nsp + k : NULL)) return 1;
         }
+    return 0;
+}
+
+/* DCDS for the listed blocks only (see oracle_fs_blocks). */
+int oracle_dcds_blocks(const uint8_t* cur, const uint8_t* ref, int w, int h, int pitch,
+                       int block, int range, int simplified, const int32_t* idx, int n,
+                       int16_t* mv, uint32_t* sad, uint16_t* nsp)
+{
+    if (block <= 0 || w % block || h % block || range < 0) return 1;
+    int nbx = w / block, nb = nbx * (h / block);
+    for (int t = 0; t < n; ++t) {
+        if (idx[t] < 0 || idx[t] >= nb) return 1;
+        if (dcds_one(cur, ref, w, h, pitch, block, range, simplified, (idx[t] % nbx) * block,
+                     (idx[t] / nbx) * block, mv + 2 * (long)t, sad + t, nsp ? nsp + t : NULL)) return 1;
     }
     return 0;
 }

@@ -1,0 +1,574 @@
+// me_api.cu -- the C-ABI of libme (declared in include/me.h): argument checks,
+// descriptor tables, the work-queue counters, CUDA-graph capture, the launch
+// shape tuner and the byte-absdiff microbenchmark.  All arithmetic of the
+// motion search runs in the kernels of dcds.cu, fs.cu and eval.cu.
+#include "me.h"
+#include "me_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <fstream>
+#include <map>
+#include <sstream>
+#include <string>
+#include <vector>
+
+using me::EvalDev;
+using me::FrameDev;
+using me::Shape;
+
+namespace {
+
+// One reusable upload slot: a device buffer [queue head | descriptor table],
+// its pinned host twin and an event marking the last launch that used it.
+struct Slot {
+    void* dev = nullptr;
+    void* host = nullptr;
+    size_t cap = 0;
+    cudaEvent_t done = nullptr;
+    bool used = false;
+};
+
+constexpr size_t kHeadBytes = 256;  // queue head (int) and padding before the table
+
+}  // namespace
+
+struct me_ctx {
+    int device = 0;
+    int num_sms = 0;
+    std::string err;
+    std::string tune_path;
+    std::map<std::string, Shape> tuned;
+    Slot slots[ME_MAX_INFLIGHT];
+    int next_slot = 0;
+    unsigned* status = nullptr;  // device word written by kernels
+    unsigned* sink = nullptr;    // microbenchmark sink
+};
+
+struct me_graph {
+    me_ctx* ctx = nullptr;
+    void* dev = nullptr;  // [head | table]
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+int fail(me_ctx* c, int code, const std::string& msg)
+{
+    if (c) c->err = msg;
+    return code;
+}
+
+int cuda_fail(me_ctx* c, cudaError_t e, const char* what)
+{
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    return fail(c, ME_ERR_CUDA, m);
+}
+
+bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+std::string shape_key(int algo, int block, int range, int w, int h)
+{
+    std::ostringstream o;
+    o << algo << " " << block << " " << range << " " << w << "x" << h;
+    return o.str();
+}
+
+// K (candidate rows per FS thread) wasting the fewest rows of 2R+1.
+int fs_pick_k(int range)
+{
+    const int ks[4] = {15, 13, 11, 8};
+    int best = 8;
+    double be = -1.0;
+    const int n = 2 * range + 1;
+    for (int k : ks) {
+        const double e = (double)n / (double)(((n + k - 1) / k) * k);
+        if (e > be + 1e-9) { be = e; best = k; }
+    }
+    return best;
+}
+
+Shape default_shape(me_ctx* c, int algo, int block, int range)
+{
+    Shape s{};
+    if (algo == ME_ALGO_FS) {
+        s.k = fs_pick_k(range);
+        s.threads = 256;
+        s.ty = 1;
+        s.ctas_per_sm = 0;
+        // tile width: least idle threads over the tasks of a tile, shared memory <= 100 KB
+        const int ndx = 2 * range + 1;
+        const int tpb = ndx * ((ndx + s.k - 1) / s.k);
+        double be = -1.0;
+        int bt = 4;
+        for (int tx = 2; tx <= 32; tx += (block == 8 ? 2 : 1)) {
+            Shape t = s;
+            t.tx = tx;
+            if (me::fs_smem_bytes(block, range, t) > 100 * 1024) break;
+            const long nt = (long)tx * tpb;
+            const double e = (double)nt / (double)(((nt + 255) / 256) * 256);
+            if (e > be + 1e-3) { be = e; bt = tx; }
+        }
+        s.tx = bt;
+        return s;
+    }
+    s.threads = 128;
+    if (block == 16) { s.tx = 16; s.ty = 8; }
+    else { s.tx = 16; s.ty = 16; }
+    s.k = 0;
+    s.ctas_per_sm = 1;
+    (void)c;
+    return s;
+}
+
+Shape pick_shape(me_ctx* c, int algo, int block, int range, int w, int h)
+{
+    auto it = c->tuned.find(shape_key(algo, block, range, w, h));
+    if (it != c->tuned.end()) return it->second;
+    return default_shape(c, algo, block, range);
+}
+
+int persistent_ctas(me_ctx* c, int block, int max_range, bool simplified, const Shape& s)
+{
+    // occupancy of the DCDS kernel for this shape; at least one CTA per SM
+    (void)simplified;
+    const size_t smem = me::dcds_smem_bytes(block, max_range, s);
+    int per_sm = (int)((227 * 1024) / (smem + 1024));
+    const int by_threads = 2048 / s.threads;
+    per_sm = std::min(per_sm, by_threads);
+    per_sm = std::min(per_sm, 16);
+    (void)c;
+    return std::max(per_sm, 1);
+}
+
+int check_frame(me_ctx* c, const uint8_t* cur, const uint8_t* ref, int w, int h, int pitch, int block,
+                int range, const void* mv, const void* sad, const void* nsp)
+{
+    if (!cur || !ref) return fail(c, ME_ERR_ARG, "cur/ref must not be NULL");
+    if (!aligned(cur, 16) || !aligned(ref, 16)) return fail(c, ME_ERR_ARG, "cur/ref must be 16-byte aligned");
+    if (block != 8 && block != 16) return fail(c, ME_ERR_ARG, "block must be 8 or 16");
+    if (w <= 0 || h <= 0) return fail(c, ME_ERR_ARG, "w and h must be positive");
+    if (w % 16 || w % block || h % block) return fail(c, ME_ERR_ARG, "w must be a multiple of 16 and of block, h of block");
+    if (pitch < w || pitch % 16) return fail(c, ME_ERR_ARG, "pitch must be >= w and a multiple of 16");
+    if (range < 1 || range > ME_MAX_RANGE) return fail(c, ME_ERR_ARG, "range must be in 1..32");
+    if (!mv || !sad) return fail(c, ME_ERR_ARG, "mv and sad must not be NULL");
+    if (!aligned(mv, 4) || !aligned(sad, 4)) return fail(c, ME_ERR_ARG, "mv and sad must be 4-byte aligned");
+    if (nsp && !aligned(nsp, 2)) return fail(c, ME_ERR_ARG, "nsp must be 2-byte aligned");
+    return ME_OK;
+}
+
+// Take the next upload slot, wait for its previous launch, make it hold `bytes`.
+int take_slot(me_ctx* c, size_t bytes, Slot** out)
+{
+    Slot& s = c->slots[c->next_slot];
+    c->next_slot = (c->next_slot + 1) % ME_MAX_INFLIGHT;
+    cudaError_t e;
+    if (s.used) {
+        e = cudaEventSynchronize(s.done);
+        if (e != cudaSuccess) return cuda_fail(c, e, "cudaEventSynchronize");
+    }
+    if (s.cap < bytes) {
+        if (s.dev) cudaFree(s.dev);
+        if (s.host) cudaFreeHost(s.host);
+        s.dev = s.host = nullptr;
+        s.cap = 0;
+        size_t cap = std::max<size_t>(bytes, 64 * 1024);
+        e = cudaMalloc(&s.dev, cap);
+        if (e != cudaSuccess) return fail(c, ME_ERR_NOMEM, "cudaMalloc of a descriptor table failed");
+        e = cudaMallocHost(&s.host, cap);
+        if (e != cudaSuccess) return fail(c, ME_ERR_NOMEM, "cudaMallocHost of a descriptor table failed");
+        s.cap = cap;
+    }
+    if (!s.done) {
+        e = cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(c, e, "cudaEventCreate");
+    }
+    *out = &s;
+    return ME_OK;
+}
+
+// Fill the device-side table (tiles per frame) into `table`; returns tiles.
+int build_table(const me_frame_desc* d, int n, int block, const Shape& s, bool fs, FrameDev* table,
+                int* max_range)
+{
+    int tiles = 0, mr = 1;
+    for (int i = 0; i < n; ++i) {
+        FrameDev f{};
+        f.cur = d[i].cur;
+        f.ref = d[i].ref;
+        f.mv = d[i].mv;
+        f.sad = d[i].sad;
+        f.nsp = d[i].nsp;
+        f.w = d[i].w;
+        f.h = d[i].h;
+        f.pitch = d[i].pitch;
+        f.range = d[i].range;
+        f.nbx = d[i].w / block;
+        f.nby = d[i].h / block;
+        f.tiles_x = (f.nbx + s.tx - 1) / s.tx;
+        f.tiles_y = fs ? f.nby : (f.nby + s.ty - 1) / s.ty;
+        f.tile_base = tiles;
+        tiles += f.tiles_x * f.tiles_y;
+        mr = std::max(mr, f.range);
+        table[i] = f;
+    }
+    *max_range = mr;
+    return tiles;
+}
+
+int validate_batch(me_ctx* c, const me_frame_desc* d, int n, int block, int algo)
+{
+    if (!d || n <= 0) return fail(c, ME_ERR_ARG, "descs must not be NULL and n must be positive");
+    if (algo == ME_ALGO_DCDS_LEARNED) return fail(c, ME_ERR_UNSUPPORTED, "learned start: no proposal weights loaded");
+    if (algo != ME_ALGO_FS && algo != ME_ALGO_DCDS && algo != ME_ALGO_DCDS_S) return fail(c, ME_ERR_ARG, "unknown algo");
+    for (int i = 0; i < n; ++i) {
+        int rc = check_frame(c, d[i].cur, d[i].ref, d[i].w, d[i].h, d[i].pitch, block, d[i].range, d[i].mv,
+                             d[i].sad, d[i].nsp);
+        if (rc != ME_OK) {
+            c->err = "descriptor " + std::to_string(i) + ": " + c->err;
+            return rc;
+        }
+    }
+    return ME_OK;
+}
+
+// Launch the search over a table already on the device at `dev`.
+cudaError_t launch_search(me_ctx* c, void* dev, int n, int ntiles, int block, int algo, int max_range,
+                          const Shape& s, cudaStream_t st)
+{
+    int* head = reinterpret_cast<int*>(dev);
+    const FrameDev* table = reinterpret_cast<const FrameDev*>(reinterpret_cast<char*>(dev) + kHeadBytes);
+    if (algo == ME_ALGO_FS) return me::launch_fs(table, n, ntiles, block, max_range, s, st);
+    cudaError_t e = cudaMemsetAsync(head, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    Shape t = s;
+    t.ctas_per_sm = persistent_ctas(c, block, max_range, algo == ME_ALGO_DCDS_S, s);
+    return me::launch_dcds(table, n, ntiles, block, max_range, algo == ME_ALGO_DCDS_S, t, head, c->status,
+                           c->num_sms, st);
+}
+
+int run_batch(me_ctx* c, const me_frame_desc* d, int n, int block, int algo, const Shape& s, cudaStream_t st)
+{
+    const size_t bytes = kHeadBytes + sizeof(FrameDev) * (size_t)n;
+    Slot* slot = nullptr;
+    int rc = take_slot(c, bytes, &slot);
+    if (rc != ME_OK) return rc;
+    FrameDev* table = reinterpret_cast<FrameDev*>(reinterpret_cast<char*>(slot->host) + kHeadBytes);
+    int max_range = 1;
+    const int ntiles = build_table(d, n, block, s, algo == ME_ALGO_FS, table, &max_range);
+    cudaError_t e = cudaMemcpyAsync(slot->dev, slot->host, bytes, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "descriptor upload");
+    e = launch_search(c, slot->dev, n, ntiles, block, algo, max_range, s, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "search launch");
+    e = cudaEventRecord(slot->done, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaEventRecord");
+    slot->used = true;
+    return ME_OK;
+}
+
+void load_tune_cache(me_ctx* c)
+{
+    if (c->tune_path.empty()) return;
+    std::ifstream f(c->tune_path);
+    std::string line;
+    while (std::getline(f, line)) {
+        // algo block range WxH tx ty threads k
+        std::istringstream is(line);
+        int algo, block, range, tx, ty, th, k;
+        std::string wh;
+        if (is >> algo >> block >> range >> wh >> tx >> ty >> th >> k) {
+            int w = 0, h = 0;
+            if (sscanf(wh.c_str(), "%dx%d", &w, &h) == 2) {
+                Shape s{tx, ty, th, 0, k};
+                c->tuned[shape_key(algo, block, range, w, h)] = s;
+            }
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int me_init(me_ctx** out, int cuda_device, const char* tune_cache_path)
+{
+    if (!out) return ME_ERR_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) return ME_ERR_CUDA;
+    if (cuda_device < 0 || cuda_device >= ndev) return ME_ERR_ARG;
+    cudaDeviceProp p;
+    if (cudaGetDeviceProperties(&p, cuda_device) != cudaSuccess) return ME_ERR_CUDA;
+    if (p.major != 10 || p.minor != 3) return ME_ERR_CUDA;  // the kernels are built for sm_103a only
+    if (cudaSetDevice(cuda_device) != cudaSuccess) return ME_ERR_CUDA;
+    me_ctx* c = new me_ctx();
+    c->device = cuda_device;
+    c->num_sms = p.multiProcessorCount;
+    if (tune_cache_path) c->tune_path = tune_cache_path;
+    if (cudaMalloc(&c->status, 256) != cudaSuccess || cudaMemset(c->status, 0, 256) != cudaSuccess) {
+        delete c;
+        return ME_ERR_NOMEM;
+    }
+    c->sink = c->status + 32;
+    load_tune_cache(c);
+    *out = c;
+    return ME_OK;
+}
+
+void me_free(me_ctx* c)
+{
+    if (!c) return;
+    for (auto& s : c->slots) {
+        if (s.done) cudaEventDestroy(s.done);
+        if (s.dev) cudaFree(s.dev);
+        if (s.host) cudaFreeHost(s.host);
+    }
+    if (c->status) cudaFree(c->status);
+    delete c;
+}
+
+const char* me_last_error(const me_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int me_estimate(me_ctx* c, const uint8_t* cur, const uint8_t* ref, int w, int h, int block, int range, int algo,
+                int16_t* mv, uint32_t* sad, uint16_t* nsp, void* stream)
+{
+    if (!c) return ME_ERR_ARG;
+    me_frame_desc d{cur, ref, w, h, w, range, mv, sad, nsp};
+    int rc = validate_batch(c, &d, 1, block, algo);
+    if (rc != ME_OK) return rc;
+    return run_batch(c, &d, 1, block, algo, pick_shape(c, algo, block, range, w, h), (cudaStream_t)stream);
+}
+
+int me_estimate_batch(me_ctx* c, const me_frame_desc* descs, int n, int block, int algo, void* stream)
+{
+    if (!c) return ME_ERR_ARG;
+    int rc = validate_batch(c, descs, n, block, algo);
+    if (rc != ME_OK) return rc;
+    int mr = 1, mw = 0, mh = 0;
+    for (int i = 0; i < n; ++i) { mr = std::max(mr, descs[i].range); mw = std::max(mw, descs[i].w); mh = std::max(mh, descs[i].h); }
+    return run_batch(c, descs, n, block, algo, pick_shape(c, algo, block, mr, mw, mh), (cudaStream_t)stream);
+}
+
+int me_graph_create(me_ctx* c, const me_frame_desc* descs, int n, int block, int algo, me_graph** out)
+{
+    if (!c || !out) return ME_ERR_ARG;
+    *out = nullptr;
+    int rc = validate_batch(c, descs, n, block, algo);
+    if (rc != ME_OK) return rc;
+    int mr = 1, mw = 0, mh = 0;
+    for (int i = 0; i < n; ++i) { mr = std::max(mr, descs[i].range); mw = std::max(mw, descs[i].w); mh = std::max(mh, descs[i].h); }
+    const Shape s = pick_shape(c, algo, block, mr, mw, mh);
+    std::vector<FrameDev> table(n);
+    int max_range = 1;
+    const int ntiles = build_table(descs, n, block, s, algo == ME_ALGO_FS, table.data(), &max_range);
+    me_graph* g = new me_graph();
+    g->ctx = c;
+    const size_t bytes = kHeadBytes + sizeof(FrameDev) * (size_t)n;
+    cudaError_t e = cudaMalloc(&g->dev, bytes);
+    if (e != cudaSuccess) { delete g; return fail(c, ME_ERR_NOMEM, "cudaMalloc of a graph table failed"); }
+    e = cudaMemcpy(reinterpret_cast<char*>(g->dev) + kHeadBytes, table.data(), sizeof(FrameDev) * n,
+                   cudaMemcpyHostToDevice);
+    cudaStream_t cs = nullptr;
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t le = launch_search(c, g->dev, n, ntiles, block, algo, max_range, s, cs);
+        e = cudaStreamEndCapture(cs, &g->graph);
+        if (le != cudaSuccess) e = le;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+    if (cs) cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
+        me_graph_free(g);
+        return cuda_fail(c, e, "graph capture");
+    }
+    *out = g;
+    return ME_OK;
+}
+
+int me_graph_launch(me_ctx* c, me_graph* g, void* stream)
+{
+    if (!c || !g) return ME_ERR_ARG;
+    cudaError_t e = cudaGraphLaunch(g->exec, (cudaStream_t)stream);
+    return e == cudaSuccess ? ME_OK : cuda_fail(c, e, "cudaGraphLaunch");
+}
+
+void me_graph_free(me_graph* g)
+{
+    if (!g) return;
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    if (g->dev) cudaFree(g->dev);
+    delete g;
+}
+
+int me_eval_batch(me_ctx* c, const me_eval_desc* d, int n, int block, uint64_t* sums, void* stream)
+{
+    if (!c) return ME_ERR_ARG;
+    if (!d || n <= 0 || !sums) return fail(c, ME_ERR_ARG, "descs and sums must not be NULL, n positive");
+    if (!aligned(sums, 8)) return fail(c, ME_ERR_ARG, "sums must be 8-byte aligned");
+    if (n > 65535) return fail(c, ME_ERR_ARG, "at most 65535 frames per evaluation batch");
+    int max_blocks = 0;
+    for (int i = 0; i < n; ++i) {
+        int rc = check_frame(c, d[i].cur, d[i].ref, d[i].w, d[i].h, d[i].pitch, block, 1, d[i].mv, d[i].mv,
+                             d[i].nsp);
+        if (rc != ME_OK) return rc;
+        if (d[i].mv_fs && !aligned(d[i].mv_fs, 4)) return fail(c, ME_ERR_ARG, "mv_fs must be 4-byte aligned");
+        max_blocks = std::max(max_blocks, (d[i].w / block) * (d[i].h / block));
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = kHeadBytes + sizeof(EvalDev) * (size_t)n;
+    Slot* slot = nullptr;
+    int rc = take_slot(c, bytes, &slot);
+    if (rc != ME_OK) return rc;
+    EvalDev* table = reinterpret_cast<EvalDev*>(reinterpret_cast<char*>(slot->host) + kHeadBytes);
+    for (int i = 0; i < n; ++i) {
+        EvalDev f{};
+        f.cur = d[i].cur; f.ref = d[i].ref; f.mv = d[i].mv; f.mv_fs = d[i].mv_fs; f.nsp = d[i].nsp;
+        f.w = d[i].w; f.h = d[i].h; f.pitch = d[i].pitch; f.nbx = d[i].w / block; f.nby = d[i].h / block;
+        table[i] = f;
+    }
+    cudaError_t e = cudaMemcpyAsync(slot->dev, slot->host, bytes, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(sums, 0, sizeof(uint64_t) * ME_NSUMS * (size_t)n, st);
+    if (e == cudaSuccess)
+        e = me::launch_eval(reinterpret_cast<const EvalDev*>(reinterpret_cast<char*>(slot->dev) + kHeadBytes), n,
+                            block, max_blocks, reinterpret_cast<unsigned long long*>(sums), st);
+    if (e == cudaSuccess) e = cudaEventRecord(slot->done, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "evaluation launch");
+    slot->used = true;
+    return ME_OK;
+}
+
+int me_eval(me_ctx* c, const uint8_t* cur, const uint8_t* ref, int w, int h, int block, const int16_t* mv,
+            const int16_t* mv_fs, const uint16_t* nsp, uint64_t* sums, void* stream)
+{
+    me_eval_desc d{cur, ref, w, h, w, mv, mv_fs, nsp};
+    return me_eval_batch(c, &d, 1, block, sums, stream);
+}
+
+int me_stats_from_sums(const uint64_t* s, me_stats* out)
+{
+    if (!s || !out) return ME_ERR_ARG;
+    const double npix = (double)s[ME_SUM_PIXELS], nb = (double)s[ME_SUM_BLOCKS];
+    if (npix <= 0.0 || nb <= 0.0) return ME_ERR_ARG;
+    out->mad = (double)s[ME_SUM_ABS] / npix;
+    out->mse = (double)s[ME_SUM_SQ] / npix;
+    out->nsp = (double)s[ME_SUM_NSP] / nb;
+    out->psnr = out->mse > 0.0 ? 10.0 * std::log10(255.0 * 255.0 / out->mse) : 100.0;
+    out->distance = s[ME_SUM_HAS_FS] ? (double)s[ME_SUM_DIST_Q24] / 16777216.0 / nb : 0.0;
+    out->probability = s[ME_SUM_HAS_FS] ? (double)s[ME_SUM_EQUAL] / nb : 0.0;
+    return ME_OK;
+}
+
+int me_tune(me_ctx* c, const uint8_t* cur, const uint8_t* ref, int w, int h, int block, int range, int algo,
+            int16_t* mv, uint32_t* sad, uint16_t* nsp, int* chosen, void* stream)
+{
+    if (!c) return ME_ERR_ARG;
+    me_frame_desc d{cur, ref, w, h, w, range, mv, sad, nsp};
+    int rc = validate_batch(c, &d, 1, block, algo);
+    if (rc != ME_OK) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<Shape> cands;
+    if (algo == ME_ALGO_FS) {
+        const Shape base = default_shape(c, algo, block, range);
+        for (int tx = 2; tx <= 32; tx += 2) {
+            Shape s = base;
+            s.tx = tx;
+            if (me::fs_smem_bytes(block, range, s) <= 100 * 1024) cands.push_back(s);
+        }
+    } else {
+        const int txs[4] = {8, 16, 16, 32};
+        const int tys[4] = {8, 4, 8, 4};
+        for (int th : {64, 128}) {
+            for (int i = 0; i < 4; ++i) {
+                Shape s{txs[i], block == 8 ? tys[i] * 2 : tys[i], th, 1, 0};
+                if (me::dcds_smem_bytes(block, range, s) <= 200 * 1024) cands.push_back(s);
+            }
+        }
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    int bi = -1;
+    for (size_t i = 0; i < cands.size(); ++i) {
+        float tbest = 1e30f;
+        for (int rep = 0; rep < 4; ++rep) {
+            cudaEventRecord(e0, st);
+            rc = run_batch(c, &d, 1, block, algo, cands[i], st);
+            cudaEventRecord(e1, st);
+            if (rc != ME_OK) break;
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) tbest = std::min(tbest, ms);
+        }
+        if (rc != ME_OK) break;
+        if (tbest < best) { best = tbest; bi = (int)i; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != ME_OK) return rc;
+    if (bi < 0) return fail(c, ME_ERR_UNSUPPORTED, "no launch shape fits this configuration");
+    c->tuned[shape_key(algo, block, range, w, h)] = cands[bi];
+    if (!c->tune_path.empty()) {
+        std::ofstream f(c->tune_path, std::ios::app);
+        const Shape& s = cands[bi];
+        f << shape_key(algo, block, range, w, h) << " " << s.tx << " " << s.ty << " " << s.threads << " " << s.k
+          << "\n";
+    }
+    if (chosen) *chosen = bi;
+    // leave the outputs computed with the chosen shape
+    return run_batch(c, &d, 1, block, algo, cands[bi], st);
+}
+
+int me_absdiff_peak(me_ctx* c, int iters, double* out, int n_variants, int* used, void* stream)
+{
+    if (!c || !out || n_variants <= 0 || iters <= 0) return ME_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int threads = 256, blocks = c->num_sms * 8;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    for (int v = 0; v < n_variants; ++v) {
+        out[v] = 0.0;
+        if (v >= me::SAD_NVARIANTS) continue;
+        float best = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {
+            cudaEventRecord(e0, st);
+            cudaError_t e = me::launch_absdiff_peak(v, iters, blocks, threads, c->sink, st);
+            cudaEventRecord(e1, st);
+            if (e != cudaSuccess) { cudaEventDestroy(e0); cudaEventDestroy(e1); return cuda_fail(c, e, "absdiff peak"); }
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) best = std::min(best, ms);
+        }
+        out[v] = (double)blocks * threads * (double)iters * 128.0 / (best * 1e-3);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (used) *used = me::kSadVariant;
+    return ME_OK;
+}
+
+int me_check_status(me_ctx* c, void* stream)
+{
+    if (!c) return ME_ERR_ARG;
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamSynchronize");
+    unsigned st = 0;
+    e = cudaMemcpy(&st, c->status, sizeof(unsigned), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "status read");
+    if (st) {
+        cudaMemset(c->status, 0, sizeof(unsigned));
+        if (st & me::STATUS_TIMEOUT) return fail(c, ME_ERR_TIMEOUT, "a bounded device-side wait gave up");
+        return fail(c, ME_ERR_ARG, "a kernel rejected its input");
+    }
+    return ME_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,98 @@
+// me_internal.cuh -- definitions shared by the sm_103a kernels and the C-ABI
+// host code of libme.  Nothing here is shared with the CPU oracle.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace me {
+
+// Device-side view of one frame pair of a launch (64-byte aligned so a CTA
+// reads it with a few vector loads).
+struct __align__(64) FrameDev {
+    const uint8_t* cur;
+    const uint8_t* ref;
+    int16_t* mv;
+    uint32_t* sad;
+    uint16_t* nsp;
+    int32_t w, h, pitch, range;
+    int32_t nbx, nby;          // blocks per row / column
+    int32_t tiles_x, tiles_y;  // tiles of this frame
+    int32_t tile_base;         // first global tile index of this frame
+    int32_t pad_[1];
+};
+
+// Device-side view of one frame of an evaluation batch.
+struct __align__(64) EvalDev {
+    const uint8_t* cur;
+    const uint8_t* ref;
+    const int16_t* mv;
+    const int16_t* mv_fs;
+    const uint16_t* nsp;
+    int32_t w, h, pitch, nbx, nby;
+};
+
+// Launch shape of the search kernels.
+struct Shape {
+    int tx, ty;        // tile of tx x ty blocks staged together
+    int threads;       // threads per CTA
+    int ctas_per_sm;   // persistent grid = ctas_per_sm * SM count (0 = one CTA per tile)
+    int k;             // FS: candidate rows per thread
+};
+
+// Status bits a kernel may record (read back by me_check_status).
+enum : unsigned { STATUS_TIMEOUT = 1u, STATUS_BAD_ARG = 2u };
+
+// Bitmap of visited points: one row per dy in [-R, R], this many 32-bit
+// words per row (one bit per dx in [-R, R]).
+__host__ __device__ inline int bm_words_per_row(int max_range) { return (2 * max_range + 1 + 31) / 32; }
+
+// ---------------------------------------------------------------------------
+// 4-byte SIMD sum of absolute differences, accumulated.  Several encodings of
+// the same arithmetic; the byte-absdiff microbenchmark measures each and the
+// kernels are instantiated with the fastest (kSadVariant).
+// ---------------------------------------------------------------------------
+enum { SAD_VSADU4 = 0, SAD_PTX_ADD = 1, SAD_DP4A = 2, SAD_MINMAX = 3, SAD_NVARIANTS = 4 };
+
+template <int V>
+__device__ __forceinline__ uint32_t sadacc(uint32_t a, uint32_t b, uint32_t c)
+{
+    if constexpr (V == SAD_VSADU4) {
+        return __vsadu4(a, b) + c;
+    } else if constexpr (V == SAD_PTX_ADD) {
+        uint32_t d;
+        asm("vabsdiff4.u32.u32.u32.add %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+        return d;
+    } else if constexpr (V == SAD_DP4A) {
+        return (uint32_t)__dp4a(__vabsdiffu4(a, b), 0x01010101u, c);
+    } else {
+        uint32_t d = __vsub4(__vmaxu4(a, b), __vminu4(a, b));
+        return (uint32_t)__dp4a(d, 0x01010101u, c);
+    }
+}
+
+// Variant the search kernels are compiled with (chosen by measurement).
+#ifndef ME_SAD_VARIANT
+#define ME_SAD_VARIANT 0
+#endif
+constexpr int kSadVariant = ME_SAD_VARIANT;
+
+// ---------------------------------------------------------------------------
+// Host-side launchers (each .cu file owns its kernels).
+// ---------------------------------------------------------------------------
+cudaError_t launch_dcds(const FrameDev* frames, int nframes, int ntiles, int block, int max_range,
+                        bool simplified, const Shape& s, int* head, unsigned* status, int num_sms,
+                        cudaStream_t st);
+size_t dcds_smem_bytes(int block, int max_range, const Shape& s);
+
+cudaError_t launch_fs(const FrameDev* frames, int nframes, int ntiles, int block, int max_range,
+                      const Shape& s, cudaStream_t st);
+size_t fs_smem_bytes(int block, int max_range, const Shape& s);
+
+cudaError_t launch_eval(const EvalDev* frames, int nframes, int block, int max_blocks,
+                        unsigned long long* sums, cudaStream_t st);
+
+cudaError_t launch_absdiff_peak(int variant, int iters, int blocks, int threads, unsigned* sink,
+                                cudaStream_t st);
+
+}  // namespace me

@@ -1,0 +1,204 @@
+"""Thin ctypes binding of libme (include/me.h): argument marshalling only.
+
+Every function here forwards to the C-ABI entry point of the same name;
+frames and outputs are torch CUDA tensors whose device pointers are passed
+through.  There is no fallback: if libme.so is missing or no sm_103 device is
+present the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+ME_OK, ME_ERR_ARG, ME_ERR_CUDA, ME_ERR_UNSUPPORTED, ME_ERR_TIMEOUT, ME_ERR_NOMEM = range(6)
+ME_ALGO_FS, ME_ALGO_DCDS, ME_ALGO_DCDS_S, ME_ALGO_DCDS_LEARNED = range(4)
+ME_MAX_RANGE = 32
+ME_NSUMS = 8
+ALGOS = {"fs": ME_ALGO_FS, "dcds": ME_ALGO_DCDS, "dcds_s": ME_ALGO_DCDS_S, "dcds_learned": ME_ALGO_DCDS_LEARNED}
+
+EXPORTS = ["me_init", "me_free", "me_last_error", "me_estimate", "me_estimate_batch", "me_graph_create",
+           "me_graph_launch", "me_graph_free", "me_eval", "me_eval_batch", "me_stats_from_sums", "me_tune",
+           "me_absdiff_peak", "me_check_status"]
+
+
+class MeError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libme error {code}: {msg}")
+        self.code = code
+
+
+class FrameDesc(ctypes.Structure):
+    _fields_ = [("cur", ctypes.c_void_p), ("ref", ctypes.c_void_p), ("w", ctypes.c_int32),
+                ("h", ctypes.c_int32), ("pitch", ctypes.c_int32), ("range", ctypes.c_int32),
+                ("mv", ctypes.c_void_p), ("sad", ctypes.c_void_p), ("nsp", ctypes.c_void_p)]
+
+
+class EvalDesc(ctypes.Structure):
+    _fields_ = [("cur", ctypes.c_void_p), ("ref", ctypes.c_void_p), ("w", ctypes.c_int32),
+                ("h", ctypes.c_int32), ("pitch", ctypes.c_int32), ("mv", ctypes.c_void_p),
+                ("mv_fs", ctypes.c_void_p), ("nsp", ctypes.c_void_p)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in ("mad", "mse", "nsp", "psnr", "distance", "probability")]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib_path():
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libme.so (building it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build() if build_if_missing else _build.LIB
+            if not os.path.exists(path):
+                raise FileNotFoundError(f"{path} is missing; run paper_0806_0689_gb300.build")
+            L = ctypes.CDLL(path)
+            P, I = ctypes.c_void_p, ctypes.c_int
+            L.me_init.argtypes = [ctypes.POINTER(P), I, ctypes.c_char_p]
+            L.me_free.argtypes = [P]
+            L.me_free.restype = None
+            L.me_last_error.argtypes = [P]
+            L.me_last_error.restype = ctypes.c_char_p
+            L.me_estimate.argtypes = [P, P, P, I, I, I, I, I, P, P, P, P]
+            L.me_estimate_batch.argtypes = [P, ctypes.POINTER(FrameDesc), I, I, I, P]
+            L.me_graph_create.argtypes = [P, ctypes.POINTER(FrameDesc), I, I, I, ctypes.POINTER(P)]
+            L.me_graph_launch.argtypes = [P, P, P]
+            L.me_graph_free.argtypes = [P]
+            L.me_graph_free.restype = None
+            L.me_eval.argtypes = [P, P, P, I, I, I, P, P, P, P, P]
+            L.me_eval_batch.argtypes = [P, ctypes.POINTER(EvalDesc), I, I, P, P]
+            L.me_stats_from_sums.argtypes = [P, ctypes.POINTER(Stats)]
+            L.me_tune.argtypes = [P, P, P, I, I, I, I, I, P, P, P, ctypes.POINTER(I), P]
+            L.me_absdiff_peak.argtypes = [P, I, ctypes.POINTER(ctypes.c_double), I, ctypes.POINTER(I), P]
+            L.me_check_status.argtypes = [P, P]
+            for n in EXPORTS:
+                if n not in ("me_free", "me_last_error", "me_graph_free"):
+                    getattr(L, n).restype = I
+            _lib = L
+    return _lib
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream) if hasattr(stream, "cuda_stream") else ctypes.c_void_p(stream)
+
+
+class Context:
+    """Owns one me_ctx.  Methods mirror the C-ABI entry points."""
+
+    def __init__(self, device: int = 0, tune_cache_path: str | None = None):
+        self.L = load()
+        self.h = ctypes.c_void_p()
+        rc = self.L.me_init(ctypes.byref(self.h), device,
+                            tune_cache_path.encode() if tune_cache_path else None)
+        if rc != ME_OK:
+            raise MeError(rc, "me_init failed (no sm_103 device, or CUDA unavailable)")
+
+    def close(self):
+        if self.h:
+            self.L.me_free(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != ME_OK:
+            raise MeError(rc, self.L.me_last_error(self.h).decode())
+
+    # -- search -----------------------------------------------------------
+    def me_estimate(self, cur, ref, block, rng, algo, mv, sad, nsp=None, stream=None):
+        h, w = cur.shape[-2:]
+        self._check(self.L.me_estimate(self.h, _ptr(cur), _ptr(ref), w, h, block, rng, ALGOS.get(algo, algo),
+                                       _ptr(mv), _ptr(sad), _ptr(nsp), _stream(stream)))
+
+    @staticmethod
+    def frame_descs(items):
+        """items: iterable of (cur, ref, range, mv, sad, nsp) torch tensors."""
+        items = list(items)
+        arr = (FrameDesc * len(items))()
+        for i, (cur, ref, rng, mv, sad, nsp) in enumerate(items):
+            h, w = cur.shape[-2:]
+            arr[i] = FrameDesc(cur.data_ptr(), ref.data_ptr(), w, h, cur.stride(-2), rng, mv.data_ptr(),
+                               sad.data_ptr(), None if nsp is None else nsp.data_ptr())
+        return arr
+
+    def me_estimate_batch(self, descs, block, algo, stream=None):
+        self._check(self.L.me_estimate_batch(self.h, descs, len(descs), block, ALGOS.get(algo, algo),
+                                             _stream(stream)))
+
+    def me_graph_create(self, descs, block, algo):
+        g = ctypes.c_void_p()
+        self._check(self.L.me_graph_create(self.h, descs, len(descs), block, ALGOS.get(algo, algo),
+                                           ctypes.byref(g)))
+        return g
+
+    def me_graph_launch(self, g, stream=None):
+        self._check(self.L.me_graph_launch(self.h, g, _stream(stream)))
+
+    def me_graph_free(self, g):
+        self.L.me_graph_free(g)
+
+    # -- evaluation -------------------------------------------------------
+    def me_eval(self, cur, ref, block, mv, sums, mv_fs=None, nsp=None, stream=None):
+        h, w = cur.shape[-2:]
+        self._check(self.L.me_eval(self.h, _ptr(cur), _ptr(ref), w, h, block, _ptr(mv), _ptr(mv_fs), _ptr(nsp),
+                                   _ptr(sums), _stream(stream)))
+
+    @staticmethod
+    def eval_descs(items):
+        """items: iterable of (cur, ref, mv, mv_fs, nsp) torch tensors (mv_fs, nsp may be None)."""
+        items = list(items)
+        arr = (EvalDesc * len(items))()
+        for i, (cur, ref, mv, mv_fs, nsp) in enumerate(items):
+            h, w = cur.shape[-2:]
+            arr[i] = EvalDesc(cur.data_ptr(), ref.data_ptr(), w, h, cur.stride(-2), mv.data_ptr(),
+                              None if mv_fs is None else mv_fs.data_ptr(), None if nsp is None else nsp.data_ptr())
+        return arr
+
+    def me_eval_batch(self, descs, block, sums, stream=None):
+        self._check(self.L.me_eval_batch(self.h, descs, len(descs), block, _ptr(sums), _stream(stream)))
+
+    def me_stats_from_sums(self, sums_row):
+        a = np.ascontiguousarray(np.asarray(sums_row, dtype=np.uint64))
+        st = Stats()
+        self._check(self.L.me_stats_from_sums(ctypes.c_void_p(a.ctypes.data), ctypes.byref(st)))
+        return {n: getattr(st, n) for n, _ in Stats._fields_}
+
+    # -- tuning / microbenchmark / status -----------------------------------
+    def me_tune(self, cur, ref, block, rng, algo, mv, sad, nsp=None, stream=None):
+        h, w = cur.shape[-2:]
+        chosen = ctypes.c_int(-1)
+        self._check(self.L.me_tune(self.h, _ptr(cur), _ptr(ref), w, h, block, rng, ALGOS.get(algo, algo),
+                                   _ptr(mv), _ptr(sad), _ptr(nsp), ctypes.byref(chosen), _stream(stream)))
+        return chosen.value
+
+    def me_absdiff_peak(self, iters=4096, n_variants=4, stream=None):
+        out = (ctypes.c_double * n_variants)()
+        used = ctypes.c_int(-1)
+        self._check(self.L.me_absdiff_peak(self.h, iters, out, n_variants, ctypes.byref(used), _stream(stream)))
+        return list(out), used.value
+
+    def me_check_status(self, stream=None):
+        self._check(self.L.me_check_status(self.h, _stream(stream)))

@@ -1,0 +1,297 @@
+"""GPU parity: every motion vector, SAD and search-point count produced by
+the CUDA path through the C-ABI equals the CPU oracle's, bit for bit.
+
+Inputs are the seeded synthetic luma sequences (paper_0806_0689_gb300.synth)
+shaped like the paper's QCIF/CIF workloads, plus edge cases: ranges 1..32,
+single-block frames, stationary content, ragged tiles, mixed-size batches
+and the full 1080p benchmark batch (sampled blocks).
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_0806_0689_gb300 import me, synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = me.Context(0)
+    yield c
+    c.close()
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _outs(h, w, B):
+    nb = (w // B) * (h // B)
+    return (torch.full((nb, 2), -999, dtype=torch.int16, device="cuda"),
+            torch.full((nb,), -1, dtype=torch.int32, device="cuda"),
+            torch.full((nb,), -1, dtype=torch.int16, device="cuda"))
+
+
+def _host(mv, sad, nsp):
+    torch.cuda.synchronize()
+    return (mv.cpu().numpy(), sad.cpu().numpy().view(np.uint32),
+            None if nsp is None else nsp.cpu().numpy().view(np.uint16))
+
+
+def gpu_search(ctx, cur, ref, B, R, algo):
+    h, w = cur.shape
+    c, r = _dev(cur), _dev(ref)
+    mv, sad, nsp = _outs(h, w, B)
+    ctx.me_estimate(c, r, B, R, algo, mv, sad, nsp)
+    return _host(mv, sad, nsp)
+
+
+def oracle_search(cur, ref, B, R, algo):
+    if algo == "fs":
+        return oracle.fs(cur, ref, B, R)
+    return oracle.dcds(cur, ref, B, R, simplified=(algo == "dcds_s"))
+
+
+def assert_same(got, want, what=""):
+    for name, g, o in zip(("mv", "sad", "nsp"), got, want):
+        if not np.array_equal(g, o):
+            bad = np.argwhere(np.asarray(g).reshape(len(g), -1) != np.asarray(o).reshape(len(o), -1))[:5]
+            raise AssertionError(f"{what}: {name} differs at {bad.tolist()}: gpu {g[bad[:, 0]]} oracle {o[bad[:, 0]]}")
+
+
+ALGOS = ["dcds", "dcds_s", "fs"]
+
+
+@pytest.fixture(scope="module")
+def qcif():
+    # 10 frame pairs, 3 moving objects, +-7 motion (the QCIF workload)
+    return synth.workload_sequence("qcif", 11, seed=0)
+
+
+@pytest.fixture(scope="module")
+def cif():
+    return synth.workload_sequence("cif", 5, seed=1000)
+
+
+@pytest.mark.parametrize("algo", ALGOS)
+def test_qcif_sequence_bit_exact(ctx, qcif, algo):
+    for t in range(1, len(qcif)):
+        got = gpu_search(ctx, qcif[t], qcif[t - 1], 16, 7, algo)
+        assert_same(got, oracle_search(qcif[t], qcif[t - 1], 16, 7, algo), f"pair {t}")
+
+
+@pytest.mark.parametrize("B", [16, 8])
+@pytest.mark.parametrize("R", [7, 15])
+@pytest.mark.parametrize("algo", ALGOS)
+def test_cif_bit_exact(ctx, cif, B, R, algo):
+    for t in (1, 3):
+        got = gpu_search(ctx, cif[t], cif[t - 1], B, R, algo)
+        assert_same(got, oracle_search(cif[t], cif[t - 1], B, R, algo), f"pair {t} B{B} R{R}")
+
+
+@pytest.mark.parametrize("R", [1, 2, 3, 16, 31, 32])
+@pytest.mark.parametrize("B", [16, 8])
+@pytest.mark.parametrize("algo", ALGOS)
+def test_range_edges(ctx, R, B, algo):
+    # large motion so that searches reach the window edge
+    seq = synth.sequence(112, 80, 3, seed=77 + R, n_objects=4, scale=(6.0, 3.0), max_motion=R)
+    got = gpu_search(ctx, seq[2], seq[1], B, R, algo)
+    assert_same(got, oracle_search(seq[2], seq[1], B, R, algo), f"R{R} B{B}")
+
+
+@pytest.mark.parametrize("w,h,B", [(16, 16, 16), (16, 8, 8), (32, 8, 8), (16, 48, 16), (48, 16, 16)])
+@pytest.mark.parametrize("algo", ALGOS)
+def test_tiny_frames(ctx, w, h, B, algo):
+    rng = np.random.default_rng(w * 100 + h)
+    cur, ref = synth.shifted_pair(rng, h, w, 1, 0)
+    ref = (ref // 4 + 100).astype(np.uint8)  # low contrast: SAD ties occur
+    got = gpu_search(ctx, cur, ref, B, 7, algo)
+    assert_same(got, oracle_search(cur, ref, B, 7, algo), f"{w}x{h}")
+
+
+@pytest.mark.parametrize("algo", ["dcds", "dcds_s"])
+def test_stationary_closed_form(ctx, algo):
+    rng = np.random.default_rng(4)
+    f = synth.textured_frame(rng, 48, 64)
+    mv, sad, nsp = gpu_search(ctx, f, f, 16, 7, algo)
+    assert (mv == 0).all() and (sad == 0).all()
+    # HCSP points whose block stays inside the frame
+    hcsp = oracle.hcsp_offsets()
+    for k in range(len(nsp)):
+        i, j = k % 4, k // 4
+        want = sum(1 for dx, dy in hcsp if 0 <= i * 16 + dx <= 48 and 0 <= j * 16 + dy <= 32)
+        assert nsp[k] == want
+
+
+@pytest.mark.parametrize("sx,sy", [(1, 0), (0, 1), (2, 0), (-2, 0), (0, -1), (5, -3)])
+def test_global_shift(ctx, sx, sy):
+    rng = np.random.default_rng(12)
+    cur, ref = synth.shifted_pair(rng, 96, 128, sx, sy)
+    for algo in ALGOS:
+        assert_same(gpu_search(ctx, cur, ref, 16, 7, algo), oracle_search(cur, ref, 16, 7, algo), algo)
+
+
+def _batch(ctx, frames_list, B, algo, rngs):
+    """frames_list: list of (cur, ref) numpy pairs.  Returns list of outputs."""
+    keep, items = [], []
+    for (cur, ref), R in zip(frames_list, rngs):
+        h, w = cur.shape
+        c, r = _dev(cur), _dev(ref)
+        mv, sad, nsp = _outs(h, w, B)
+        keep.append((c, r, mv, sad, nsp))
+        items.append((c, r, R, mv, sad, nsp))
+    descs = me.Context.frame_descs(items)
+    return keep, descs
+
+
+def test_batch_mixed_sizes_matches_oracle(ctx):
+    pairs, rngs = [], []
+    for name, seed, R in (("qcif", 2000, 16), ("cif", 2002, 16), ("qcif", 2001, 7), ("720p", 2004, 16),
+                          ("cif", 2003, 5)):
+        s = synth.workload_sequence(name, 3, seed=seed, max_motion=R)
+        pairs += [(s[1], s[0]), (s[2], s[1])]
+        rngs += [R, R]
+    for algo in ALGOS:
+        keep, descs = _batch(ctx, pairs, 16, algo, rngs)
+        ctx.me_estimate_batch(descs, 16, algo)
+        torch.cuda.synchronize()
+        for (cur, ref), R, (c, r, mv, sad, nsp) in zip(pairs, rngs, keep):
+            got = _host(mv, sad, nsp)
+            if algo == "fs" and cur.shape[1] > 400:
+                idx = np.random.default_rng(0).choice(len(got[1]), 200, replace=False)
+                want = oracle.fs_blocks(cur, ref, 16, R, idx)
+                got = tuple(g[idx] for g in got)
+            else:
+                want = oracle_search(cur, ref, 16, R, algo)
+            assert_same(got, want, f"{algo} {cur.shape} R{R}")
+
+
+def test_graph_replay_and_determinism(ctx, cif):
+    pairs = [(cif[t], cif[t - 1]) for t in range(1, 5)]
+    keep, descs = _batch(ctx, pairs, 16, "dcds", [16] * 4)
+    g = ctx.me_graph_create(descs, 16, "dcds")
+    try:
+        results = []
+        for rep in range(3):
+            for (_, _, mv, sad, nsp) in keep:
+                mv.fill_(-7); sad.fill_(-1); nsp.fill_(-1)
+            ctx.me_graph_launch(g)
+            torch.cuda.synchronize()
+            results.append([_host(mv, sad, nsp) for (_, _, mv, sad, nsp) in keep])
+        for rep in (1, 2):
+            for a, b in zip(results[0], results[rep]):
+                assert_same(a, b, "replay")
+        for (cur, ref), got in zip(pairs, results[0]):
+            assert_same(got, oracle.dcds(cur, ref, 16, 16), "graph vs oracle")
+    finally:
+        ctx.me_graph_free(g)
+
+
+def test_full_1080p_batch_sampled(ctx):
+    """The benchmark's workload and launch path (captured batch of 1080p
+    pairs, 16x16, +-16): sampled blocks against the oracle, and the
+    invariants on every block."""
+    seq = synth.workload_sequence("1080p", 9, seed=1, max_motion=16)
+    pairs = [(seq[t], seq[t - 1]) for t in range(1, len(seq))]
+    rs = np.random.default_rng(5)
+    for algo in ("dcds", "fs"):
+        keep, descs = _batch(ctx, pairs, 16, algo, [16] * len(pairs))
+        g = ctx.me_graph_create(descs, 16, algo)
+        ctx.me_graph_launch(g)
+        torch.cuda.synchronize()
+        ctx.me_graph_free(g)
+        for (cur, ref), (c, r, mv, sad, nsp) in zip(pairs, keep):
+            got = _host(mv, sad, nsp)
+            idx = np.sort(rs.choice(len(got[1]), 96, replace=False))
+            idx[:4] = [0, 119, len(got[1]) - 120, len(got[1]) - 1]  # frame corners
+            want = (oracle.fs_blocks if algo == "fs" else oracle.dcds_blocks)(cur, ref, 16, 16, idx)
+            assert_same(tuple(x[idx] for x in got), want, f"{algo} 1080p")
+            assert (np.abs(got[0]) <= 16).all()
+            if algo == "fs":
+                assert (got[2] <= 33 * 33).all() and (got[2] >= 17 * 17).all()
+
+
+def test_eval_matches_oracle(ctx, cif):
+    B, R = 16, 7
+    for t in (1, 2):
+        cur, ref = cif[t], cif[t - 1]
+        fs_out = oracle.fs(cur, ref, B, R)
+        dc_out = oracle.dcds(cur, ref, B, R)
+        want = oracle.evaluate(cur, ref, B, dc_out[0], fs_out[0], dc_out[2])
+        sums = torch.zeros(me.ME_NSUMS, dtype=torch.int64, device="cuda")
+        ctx.me_eval(_dev(cur), _dev(ref), B, _dev(dc_out[0]), sums, mv_fs=_dev(fs_out[0]),
+                    nsp=_dev(dc_out[2].view(np.int16)))
+        torch.cuda.synchronize()
+        got = ctx.me_stats_from_sums(sums.cpu().numpy().view(np.uint64))
+        for k in ("mad", "mse", "nsp", "probability"):
+            assert got[k] == want[k], k
+        assert abs(got["psnr"] - want["psnr"]) < 1e-9
+        assert abs(got["distance"] - want["distance"]) < 1e-7
+
+
+def test_eval_batch_per_frame(ctx, qcif):
+    B, R = 16, 7
+    items, wants, keep = [], [], []
+    for t in range(1, 5):
+        cur, ref = qcif[t], qcif[t - 1]
+        mv, _, nsp = oracle.dcds(cur, ref, B, R)
+        wants.append(oracle.evaluate(cur, ref, B, mv, None, nsp))
+        k = (_dev(cur), _dev(ref), _dev(mv), None, _dev(nsp.view(np.int16)))
+        keep.append(k)
+        items.append(k)
+    sums = torch.zeros((len(items), me.ME_NSUMS), dtype=torch.int64, device="cuda")
+    ctx.me_eval_batch(me.Context.eval_descs(items), B, sums)
+    torch.cuda.synchronize()
+    arr = sums.cpu().numpy().view(np.uint64)
+    for i, want in enumerate(wants):
+        got = ctx.me_stats_from_sums(arr[i])
+        assert got["mse"] == want["mse"] and got["nsp"] == want["nsp"] and got["mad"] == want["mad"]
+
+
+def test_invalid_arguments_rejected(ctx):
+    L, h = ctx.L, ctx.h
+    f = torch.zeros((64, 64), dtype=torch.uint8, device="cuda")
+    mv, sad, nsp = _outs(64, 64, 16)
+    P = lambda t, off=0: ctypes.c_void_p(t.data_ptr() + off)
+    s = ctypes.c_void_p(0)
+    ok = L.me_estimate(h, P(f), P(f), 64, 64, 16, 7, 1, P(mv), P(sad), P(nsp), s)
+    assert ok == me.ME_OK
+    cases = [
+        (P(f), P(f), 60, 64, 16, 7, 1),   # width not a multiple of 16
+        (P(f), P(f), 64, 60, 16, 7, 1),   # height not a multiple of the block
+        (P(f), P(f), 64, 64, 4, 7, 1),    # block size
+        (P(f), P(f), 64, 64, 16, 0, 1),   # range 0
+        (P(f), P(f), 64, 64, 16, 33, 1),  # range above 32
+        (P(f, 1), P(f), 32, 32, 16, 7, 1),  # misaligned frame
+        (None, P(f), 64, 64, 16, 7, 1),   # null frame
+        (P(f), P(f), 64, 64, 16, 7, 9),   # unknown algo
+    ]
+    for a in cases:
+        assert L.me_estimate(h, *a, P(mv), P(sad), P(nsp), s) == me.ME_ERR_ARG, a
+        assert len(L.me_last_error(h)) > 0
+    assert L.me_estimate(h, P(f), P(f), 64, 64, 16, 7, 1, None, P(sad), P(nsp), s) == me.ME_ERR_ARG
+    assert L.me_estimate(h, P(f), P(f), 64, 64, 16, 7, 3, P(mv), P(sad), P(nsp), s) == me.ME_ERR_UNSUPPORTED
+    assert L.me_estimate_batch(h, None, 0, 16, 1, s) == me.ME_ERR_ARG
+    ctx.me_check_status()
+
+
+def test_absdiff_peak(ctx):
+    rates, used = ctx.me_absdiff_peak(iters=256)
+    assert len(rates) == 4 and all(r > 1e12 for r in rates)
+    assert 0 <= used < 4
+
+
+def test_tune_keeps_parity(ctx, cif):
+    cur, ref = cif[2], cif[1]
+    for algo in ("dcds", "fs"):
+        c, r = _dev(cur), _dev(ref)
+        mv, sad, nsp = _outs(*cur.shape, 16)
+        chosen = ctx.me_tune(c, r, 16, 7, algo, mv, sad, nsp)
+        assert chosen >= 0
+        assert_same(_host(mv, sad, nsp), oracle_search(cur, ref, 16, 7, algo), f"tuned {algo}")
+        # the tuned shape is used by later calls too
+        assert_same(gpu_search(ctx, cur, ref, 16, 7, algo), oracle_search(cur, ref, 16, 7, algo), algo)
