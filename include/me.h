@@ -63,7 +63,7 @@ typedef enum me_algo {
     ME_ALGO_DCDS_LEARNED = 3 /* DCDS from a learned start proposal (not in the paper) */
 } me_algo;
 
-enum { ME_MAX_RANGE = 32, ME_MAX_INFLIGHT = 64 };
+enum { ME_MAX_RANGE = 32, ME_MAX_INFLIGHT = 64, ME_STATIC_MAX_FRAMES = 64 };
 
 /* One frame pair of a batch.  All pointers are device memory. */
 typedef struct me_frame_desc {
@@ -115,6 +115,35 @@ int me_estimate(me_ctx* ctx, const uint8_t* cur, const uint8_t* ref, int w, int 
  * call returns. */
 int me_estimate_batch(me_ctx* ctx, const me_frame_desc* descs, int n, int block, int algo,
                       void* stream);
+
+/* me_estimate_batch_noalloc: the same DCDS / DCDS^S search as
+ * me_estimate_batch, for callers that must not allocate device memory.
+ * The paper has no counterpart; this is a deployment aid.
+ *
+ * It is for code that cannot call cudaMalloc at the time it searches: a
+ * real-time video path that must not trigger the device-wide
+ * synchronisation an allocation or free can cause, a host application or
+ * plugin framework that owns all device memory through its own pool and
+ * forbids libraries from allocating, or a process running so close to the
+ * memory limit that a late allocation could fail in the middle of a stream.
+ * No context is needed (me_init allocates) and nothing is allocated, on the
+ * device or pinned on the host.
+ *
+ * The work-queue counter and descriptor table live in a fixed library-owned
+ * device array sized for ME_STATIC_MAX_FRAMES descriptors; every device that
+ * loads libme keeps it until the process exits.  n above that limit is
+ * rejected with ME_ERR_ARG.  The first call on a device looks up the array's
+ * device address (with that device current); make that first call before
+ * any stream capture.  Every call reuses the same array: calls whose work
+ * overlaps on the GPU (different streams, or different host threads on one
+ * device) race and must be serialised by the caller.  Frames and outputs are
+ * caller-owned device memory as for me_estimate_batch; `descs` is host
+ * memory read before the call returns.  algo: ME_ALGO_DCDS or
+ * ME_ALGO_DCDS_S (ME_ERR_UNSUPPORTED otherwise).  The launch shape is the
+ * library default.  Results are identical to me_estimate_batch.
+ * err (nullable) receives a message of at most err_len bytes on failure. */
+int me_estimate_batch_noalloc(const me_frame_desc* descs, int n, int block, int algo, void* stream,
+                              char* err, int err_len);
 
 /* A captured batch: the descriptor table is uploaded once and the launch
  * sequence (queue reset + search kernel) is captured in a CUDA graph that

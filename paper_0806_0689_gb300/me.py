@@ -18,12 +18,13 @@ from . import build as _build
 ME_OK, ME_ERR_ARG, ME_ERR_CUDA, ME_ERR_UNSUPPORTED, ME_ERR_TIMEOUT, ME_ERR_NOMEM = range(6)
 ME_ALGO_FS, ME_ALGO_DCDS, ME_ALGO_DCDS_S, ME_ALGO_DCDS_LEARNED = range(4)
 ME_MAX_RANGE = 32
+ME_STATIC_MAX_FRAMES = 64
 ME_NSUMS = 8
 ALGOS = {"fs": ME_ALGO_FS, "dcds": ME_ALGO_DCDS, "dcds_s": ME_ALGO_DCDS_S, "dcds_learned": ME_ALGO_DCDS_LEARNED}
 
 EXPORTS = ["me_init", "me_free", "me_last_error", "me_estimate", "me_estimate_batch", "me_graph_create",
            "me_graph_launch", "me_graph_free", "me_eval", "me_eval_batch", "me_stats_from_sums", "me_tune",
-           "me_absdiff_peak", "me_check_status"]
+           "me_absdiff_peak", "me_check_status", "me_estimate_batch_noalloc"]
 
 
 class MeError(RuntimeError):
@@ -83,6 +84,7 @@ def load(build_if_missing: bool = True):
             L.me_tune.argtypes = [P, P, P, I, I, I, I, I, P, P, P, ctypes.POINTER(I), P]
             L.me_absdiff_peak.argtypes = [P, I, ctypes.POINTER(ctypes.c_double), I, ctypes.POINTER(I), P]
             L.me_check_status.argtypes = [P, P]
+            L.me_estimate_batch_noalloc.argtypes = [ctypes.POINTER(FrameDesc), I, I, I, P, ctypes.c_char_p, I]
             for n in EXPORTS:
                 if n not in ("me_free", "me_last_error", "me_graph_free"):
                     getattr(L, n).restype = I
