@@ -5,35 +5,39 @@
 // points); DCDS^S of Sec. IV-C as a compile-time variant.
 //
 // GPU mapping
-//   * A CTA owns a tile of tx x ty blocks of one frame.  The reference window
-//     the tile can reach (the tile grown by R rows and by R rounded up to 16
-//     columns) is staged once in shared memory with 16-byte loads.
-//   * One group of G = B/4 lanes searches one block; lane w keeps column w
-//     (4 pixels) of the B rows of the current block in registers.  A SAD is
-//     B unaligned 4-byte shared-memory reads per lane (two aligned words and
-//     a funnel shift), B SIMD absolute-difference accumulations and a
-//     log2(G)-step shuffle reduction.
-//   * Groups pull blocks of the tile from a shared counter, so a group that
-//     stops after the HCSP (the half-way stop) immediately takes another
-//     block.  Each group runs a flat state machine: every iteration of the
-//     warp loop first advances each group to its next unvisited candidate
-//     (pattern transitions, fetching a new block) and then evaluates one SAD
-//     for all active groups together, so the SAD code never runs diverged.
-//   * Persistent CTAs pull tiles from a global counter (the work queue), so
-//     a single launch covers any number of frames of any sizes.
-//   * Visited points: one bit per (dx, dy) of the window in a per-group
-//     shared-memory bitmap.  A point evaluated earlier always has a SAD no
-//     smaller than the current centre's (every move lowers the best SAD
-//     strictly), so skipping it leaves the path unchanged; the bitmap only
-//     decides what is counted and recomputed.
+//   * Persistent CTAs pull 128x128-pixel tiles from a global counter (the work
+//     queue over every frame pair of the launch).  For each tile the TMA unit
+//     copies the reference window (the tile grown by R rows and by R rounded
+//     up to 16 columns, zero-filled outside the frame) and the current tile
+//     into shared memory (cp.async.bulk.tensor.2d, completion on an
+//     mbarrier).  With two stages the next tile is fetched while this one is
+//     searched.
+//   * Phase A (step 1 for every block, warp-uniform): a warp takes one tile
+//     row of blocks, B/4 lanes per block, lane w holding 4-pixel column w of
+//     the block.  The five horizontal HCSP points share each reference row
+//     (three aligned words and four funnel shifts), the two vertical points
+//     reuse the neighbouring rows, so the 7 SADs cost 18 rows of reads.
+//     Blocks whose centre wins are finished (the half-way stop, Sec. III-C);
+//     the others go to a per-tile ring in shared memory.
+//   * Phase B (steps 2-4): groups of 4 lanes pull blocks from the ring and
+//     run the diamond rounds.  A round evaluates every new point of the
+//     current pattern (at most 4) at once, then applies the switching
+//     strategies.  A per-group bitmap of visited points (one bit per
+//     displacement of the +-R window) keeps points from being evaluated or
+//     counted twice.  A point evaluated earlier always has a SAD no smaller
+//     than the current centre's (every move lowers the best SAD strictly), so
+//     skipping it leaves the path unchanged.
+//   * Ties: candidates are compared in the fixed pattern order with a strict
+//     "<", so the centre and earlier points keep a tie (the oracle's order).
 #include "me_internal.cuh"
 
+#include <algorithm>
 #include <climits>
 
 namespace me {
 namespace {
 
-enum { PH_FETCH = 0, PH_HCSP = 1, PH_DDSP = 2, PH_SIDE = 3, PH_MID = 4, PH_DONE = 5 };
+enum { PH_FETCH = 0, PH_DDSP = 1, PH_SIDE = 2, PH_MID = 3, PH_DONE = 4 };
 enum { PAT_H = 0, PAT_V = 1 };
 
 // Offsets packed 6 bits each: (dx + 2) | (dy + 2) << 3, in evaluation order.
@@ -51,6 +55,7 @@ constexpr uint64_t kMidV = enc(0, -1, 0) | enc(0, 1, 1);
 
 constexpr uint32_t kUnknown = 0xfffffffeu;  // distant-point SAD not produced this round
 constexpr uint32_t kInvalid = 0xffffffffu;  // distant point outside window/frame
+constexpr uint32_t kWaitLimit = 1u << 22;   // bounded mbarrier polling (with back-off, > 1 s)
 
 __device__ __forceinline__ void decode(uint64_t code, int k, int& ox, int& oy)
 {
@@ -59,273 +64,512 @@ __device__ __forceinline__ void decode(uint64_t code, int k, int& ox, int& oy)
     oy = (int)(v >> 3) - 2;
 }
 
-template <int B, bool SIMPL>
-__global__ void __launch_bounds__(128) dcds_kernel(const FrameDev* __restrict__ frames, int nframes,
-                                                   int ntiles, int tx, int ty, int max_range, int sp,
-                                                   int* __restrict__ head)
+// ---------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
 {
-    constexpr int G = B / 4;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Poll the phase with the given parity; gives up after kWaitLimit polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
+{
+    for (uint32_t i = 0; i < kWaitLimit; ++i) {
+        if (mbar_test(bar, parity)) return true;
+        if (i > 64) __nanosleep(256);
+    }
+    return false;
+}
+
+__device__ __forceinline__ void fence_proxy_async()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// 2-D tiled TMA load of a box at element coordinates (x, y); x*1 byte must be
+// a multiple of 16 (it is: tile origins are multiples of 128, margins of 16).
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(smem_addr(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ int find_frame(const FrameDev* frames, int nframes, int t)
+{
+    int lo = 0, hi = nframes - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (frames[mid].tile_base <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__host__ __device__ inline int round128(int v) { return (v + 127) & ~127; }
+
+__host__ __device__ inline int win_bytes_max(int max_range)
+{
+    const int rxm = (max_range + 15) & ~15;
+    return round128((kTile + 2 * rxm) * (kTile + 2 * max_range));
+}
+
+// Thread 0: take tile t into stage `st`: publish its index and frame, then arm
+// the stage's mbarrier with the byte count and start the two TMA copies.  A
+// tile index past the end completes the phase with no data.
+__device__ void issue_tile(int t, const FrameDev* frames, int nframes, int ntiles, uint8_t* stage,
+                           int cur_off, uint64_t* bar, int* s_tile, int* s_frame)
+{
+    *s_tile = t;
+    if (t >= ntiles) {
+        mbar_arrive(bar);
+        return;
+    }
+    const int f = find_frame(frames, nframes, t);
+    *s_frame = f;
+    const FrameDev& F = frames[f];
+    const int lt = t - F.tile_base;
+    const int ty = lt / F.tiles_x, tx = lt - ty * F.tiles_x;
+    const int rx = (F.range + 15) & ~15;
+    const uint32_t bytes = (uint32_t)((kTile + 2 * rx) * (kTile + 2 * F.range) + kTile * kTile);
+    mbar_arrive_expect_tx(bar, bytes);
+    tma_load_2d(stage, &F.tm_ref, tx * kTile - rx, ty * kTile - F.range, bar);
+    tma_load_2d(stage + cur_off, &F.tm_cur, tx * kTile, ty * kTile, bar);
+}
+
+template <int B, bool SIMPL, int NST>
+__global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ frames, int nframes, int ntiles,
+                                                   int max_range, int* __restrict__ head,
+                                                   unsigned* __restrict__ status)
+{
     constexpr int V = kSadVariant;
-    extern __shared__ __align__(16) uint8_t smem[];
-    __shared__ int s_tile, s_next, s_frame;
+    constexpr int TXB = kTile / B;        // blocks per tile row
+    constexpr int NMB = TXB * TXB;        // blocks per tile
+    constexpr int GA = B / 4;             // phase-A lanes per block
+    constexpr int WPB = B / 4;            // 4-byte words per block row
+    constexpr int RPL = B * WPB / 4;      // phase-B rows per lane (4 lanes per block)
+    constexpr unsigned FULL = 0xffffffffu;
 
-    const int win_rows = ty * B + 2 * max_range;
-    uint8_t* win = smem;
-    const int nwr = bm_words_per_row(max_range);
-    const int bm_stride = (2 * max_range + 1) * nwr;
-    uint32_t* bm_all = reinterpret_cast<uint32_t*>(smem + (size_t)win_rows * sp);
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t s_bar[NST];
+    __shared__ int s_tile[NST], s_frame[NST];
+    __shared__ int s_ring_n, s_ring_next;
 
-    const int lane = threadIdx.x & 31;
-    const int lig = lane & (G - 1);
-    const int gid = threadIdx.x / G;
-    const unsigned gmask = ((1u << G) - 1u) << (lane & ~(G - 1));
-    uint32_t* bm = bm_all + (size_t)gid * bm_stride;
-    const int ngroups = blockDim.x / G;
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    const int cur_off = win_bytes_max(max_range);
+    const int stage_bytes = cur_off + kTile * kTile;
+    uint2* ring = reinterpret_cast<uint2*>(smem + NST * stage_bytes);
+    const int side_max = 2 * max_range + 1;
+    const int nwb = (side_max * side_max + 31) / 32;
+    uint32_t* bm_all = reinterpret_cast<uint32_t*>(ring + NMB);
 
-    for (int i = threadIdx.x; i < ngroups * bm_stride; i += blockDim.x) bm_all[i] = 0u;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    const int ngroups = blockDim.x >> 2;
 
-    for (;;) {
-        __syncthreads();  // the previous tile is finished and its bitmaps are clean
-        if (threadIdx.x == 0) {
-            const int t = atomicAdd(head, 1);
-            int f = 0;
-            if (t < ntiles) {
-                int lo = 0, hi = nframes - 1;
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (frames[mid].tile_base <= t) lo = mid; else hi = mid - 1;
-                }
-                f = lo;
-            }
-            s_tile = t;
-            s_frame = f;
-            s_next = 0;
+    for (int i = tid; i < ngroups * nwb; i += blockDim.x) bm_all[i] = 0u;
+    if (tid == 0) {
+        for (int s = 0; s < NST; ++s) mbar_init(&s_bar[s], 1);
+        fence_mbar_init();
+        issue_tile(atomicAdd(head, 1), frames, nframes, ntiles, smem, cur_off, &s_bar[0], &s_tile[0], &s_frame[0]);
+    }
+    __syncthreads();
+
+    for (int it = 0;; ++it) {
+        const int st = (NST == 2) ? (it & 1) : 0;
+        const uint32_t par = (NST == 2) ? ((it >> 1) & 1) : (it & 1);
+        if (tid == 0) { s_ring_n = 0; s_ring_next = 0; }
+        const bool ok = mbar_wait(&s_bar[st], par);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0 && status) atomicOr(status, STATUS_TIMEOUT);
+            // give an outstanding copy a bounded chance to land before exiting
+            if (tid == 0) (void)mbar_wait(&s_bar[st], par);
+            break;
         }
-        __syncthreads();
-        const int t = s_tile;
+        const int t = s_tile[st];
         if (t >= ntiles) break;
-        const FrameDev& F = frames[s_frame];
-        const int W = F.w, H = F.h, P = F.pitch, R = F.range, NBX = F.nbx;
+        uint8_t* stage = smem + st * stage_bytes;
+        if (NST == 2 && tid == 0) {
+            // stage st^1 was last read in the previous tile, which ended with a barrier
+            fence_proxy_async();
+            issue_tile(atomicAdd(head, 1), frames, nframes, ntiles, smem + (st ^ 1) * stage_bytes, cur_off,
+                       &s_bar[st ^ 1], &s_tile[st ^ 1], &s_frame[st ^ 1]);
+        }
+        const FrameDev& F = frames[s_frame[st]];
+        const int W = F.w, H = F.h, R = F.range, NBX = F.nbx, NBY = F.nby;
         const int lt = t - F.tile_base;
         const int tile_y = lt / F.tiles_x, tile_x = lt - tile_y * F.tiles_x;
-        const int bx0 = tile_x * tx, by0 = tile_y * ty;
-        const int nbx_t = min(tx, NBX - bx0), nby_t = min(ty, F.nby - by0);
-        const int nmb = nbx_t * nby_t;
+        const int bx0 = tile_x * TXB, by0 = tile_y * TXB;
         const int rx = (R + 15) & ~15;
-        const int x_lo = bx0 * B - rx, y_lo = by0 * B - R;
+        const int WP = kTile + 2 * rx;  // window row pitch
+        const uint8_t* win = stage;
+        const uint8_t* curS = stage + cur_off;
 
-        // ---- stage the reference window (zeros outside the frame) ----
-        {
-            const int cpr = (((nbx_t * B + 15) & ~15) + 2 * rx) >> 4;
-            const int win_h = nby_t * B + 2 * R;
-            const int total = cpr * win_h;
-            for (int i = threadIdx.x; i < total; i += blockDim.x) {
-                const int row = i / cpr, c = i - row * cpr;
-                const int gy = y_lo + row, gx = x_lo + (c << 4);
-                uint4 v = make_uint4(0u, 0u, 0u, 0u);
-                if (gy >= 0 && gy < H && gx >= 0 && gx < W)
-                    v = __ldg(reinterpret_cast<const uint4*>(F.ref + (size_t)gy * P + gx));
-                *reinterpret_cast<uint4*>(win + (size_t)row * sp + (c << 4)) = v;
+        // ------------------------------------------------ phase A: HCSP
+        for (int row = warp; row < TXB; row += nwarps) {
+            const int g = lane / GA, w = lane % GA;
+            const int bxg = bx0 + g, byg = by0 + row;
+            const bool exists = bxg < NBX && byg < NBY;
+            uint32_t cw[B];
+            const uint32_t* cp = reinterpret_cast<const uint32_t*>(curS + (row * B) * kTile + g * B + 4 * w);
+#pragma unroll
+            for (int r = 0; r < B; ++r) cw[r] = cp[r * (kTile / 4)];
+            const uint8_t* base = win + (row * B + R - 1) * WP + rx + g * B + 4 * w - 4;
+            uint32_t acc[7];
+#pragma unroll
+            for (int k = 0; k < 7; ++k) acc[k] = 0u;
+#pragma unroll
+            for (int jj = -1; jj <= B; ++jj) {
+                const uint32_t* rp = reinterpret_cast<const uint32_t*>(base + (jj + 1) * WP);
+                const uint32_t b = rp[1];
+                if (jj >= 0 && jj < B) {
+                    const uint32_t a = rp[0], c = rp[2];
+                    acc[0] = sadacc<V>(b, cw[jj], acc[0]);
+                    acc[1] = sadacc<V>(__funnelshift_r(a, b, 24), cw[jj], acc[1]);
+                    acc[2] = sadacc<V>(__funnelshift_r(b, c, 8), cw[jj], acc[2]);
+                    acc[5] = sadacc<V>(__funnelshift_r(a, b, 16), cw[jj], acc[5]);
+                    acc[6] = sadacc<V>(__funnelshift_r(b, c, 16), cw[jj], acc[6]);
+                }
+                if (jj + 1 >= 0 && jj + 1 < B) acc[3] = sadacc<V>(b, cw[jj + 1], acc[3]);  // (0,-1)
+                if (jj - 1 >= 0 && jj - 1 < B) acc[4] = sadacc<V>(b, cw[jj - 1], acc[4]);  // (0,+1)
+            }
+#pragma unroll
+            for (int o = 1; o < GA; o <<= 1)
+#pragma unroll
+                for (int k = 0; k < 7; ++k) acc[k] += __shfl_xor_sync(FULL, acc[k], o);
+            const int px = bxg * B, py = byg * B;
+            unsigned vmask = 0;
+#pragma unroll
+            for (int k = 0; k < 7; ++k) {
+                int ox, oy;
+                decode(kHcsp, k, ox, oy);
+                const bool v = abs(ox) <= R && abs(oy) <= R && px + ox >= 0 && px + ox <= W - B &&
+                               py + oy >= 0 && py + oy <= H - B;
+                vmask |= (unsigned)v << k;
+            }
+            int best = 0;
+            uint32_t bs = acc[0];
+#pragma unroll
+            for (int k = 1; k < 7; ++k)
+                if (((vmask >> k) & 1u) && acc[k] < bs) { best = k; bs = acc[k]; }
+            const bool leader = (w == 0) && exists;
+            if (leader && best == 0) {
+                const size_t blk = (size_t)byg * NBX + bxg;
+                *reinterpret_cast<uint32_t*>(F.mv + 2 * blk) = 0u;
+                F.sad[blk] = bs;
+                if (F.nsp) F.nsp[blk] = (uint16_t)__popc(vmask);
+            }
+            const bool cont = leader && best != 0;
+            const unsigned bal = __ballot_sync(FULL, cont);
+            if (bal) {
+                const int first = __ffs(bal) - 1;
+                int rbase = 0;
+                if (lane == first) rbase = atomicAdd(&s_ring_n, __popc(bal));
+                rbase = __shfl_sync(FULL, rbase, first);
+                if (cont) {
+                    const int rank = __popc(bal & ((1u << lane) - 1u));
+                    ring[rbase + rank] = make_uint2((uint32_t)(row * TXB + g) | ((uint32_t)best << 8) |
+                                                        ((uint32_t)__popc(vmask) << 11),
+                                                    bs);
+                }
             }
         }
         __syncthreads();
 
-        // ---- per-group search state (replicated in the G lanes) ----
-        int phase = PH_FETCH, pat = PAT_H, k = 0, nsp = 0, slot = 0;
-        int wx0 = 0, wy0 = 0, blk = 0;
-        int dxlo = 0, dxhi = 0, dylo = 0, dyhi = 0;
-        int cx = 0, cy = 0, bxp = 0, byp = 0;
-        uint32_t bsad = 0xffffffffu;
-        int tmin = INT_MAX, tmax = -1;  // bitmap rows touched (lane 0 only)
-        uint32_t ds0 = kUnknown, ds1 = kUnknown;
-        int nmid = 2;
-        uint64_t midcode = kMidH;
-        uint32_t cb[B];
-#pragma unroll
-        for (int r = 0; r < B; ++r) cb[r] = 0u;
+        // ------------------------------------------------ phase B: diamond rounds
+        {
+            const int gq = tid >> 2, l4 = lane & 3;
+            const unsigned gmask = 0xfu << (lane & ~3);
+            const int wb = l4 % WPB, rb = l4 / WPB;
+            uint32_t* bm = bm_all + gq * nwb;
+            const int side = 2 * R + 1;
+            const int nring = s_ring_n;
 
-        for (;;) {
-            bool have = false, counted = false;
-            int qx = 0, qy = 0;
-            // Advance to the next candidate; bounded by the number of
-            // transitions one step can chain (list ends, a block finish and a
-            // fetch), far below the guard.
-            for (int guard = 0; guard < 40; ++guard) {
-                if (phase == PH_DONE) break;
-                if (phase == PH_FETCH) {
-                    int m = 0;
-                    if (lig == 0) m = atomicAdd(&s_next, 1);
-                    m = __shfl_sync(gmask, m, 0, G);
-                    if (m >= nmb) { phase = PH_DONE; break; }
-                    const int bxl = m % nbx_t, byl = m / nbx_t;
-                    const int bxg = bx0 + bxl, byg = by0 + byl;
-                    const int px = bxg * B, py = byg * B;
-                    blk = byg * NBX + bxg;
-                    wx0 = bxl * B + rx;
-                    wy0 = byl * B + R;
-                    dxlo = max(-R, -px); dxhi = min(R, W - B - px);
-                    dylo = max(-R, -py); dyhi = min(R, H - B - py);
-                    const uint8_t* cp = F.cur + (size_t)py * P + px + 4 * lig;
+            int phase = PH_FETCH, pat = PAT_H, nsp = 0;
+            int cx = 0, cy = 0, bxp = 0, byp = 0;
+            uint32_t bsad = 0;
+            int dxlo = 0, dxhi = 0, dylo = 0, dyhi = 0, wx0 = 0, wy0 = 0;
+            size_t blk = 0;
+            int wmin = INT_MAX, wmax = -1;          // bitmap words touched (lane 0)
+            uint32_t ds0 = kUnknown, ds1 = kUnknown;  // distant-point SADs this round (lane 0, DCDS^S)
+            uint32_t cb[RPL];
 #pragma unroll
-                    for (int r = 0; r < B; ++r) cb[r] = __ldg(reinterpret_cast<const uint32_t*>(cp + (size_t)r * P));
-                    cx = cy = 0; bxp = byp = 0; bsad = 0xffffffffu; nsp = 0; pat = PAT_H;
-                    phase = PH_HCSP; k = 0;
-                    continue;
-                }
-                int n;
-                uint64_t code;
-                if (phase == PH_HCSP) { n = 7; code = kHcsp; }
-                else if (phase == PH_DDSP) { n = 4; code = pat ? kDdspV : kDdspH; }
-                else if (phase == PH_SIDE) { n = 2; code = (pat ? kDdspV : kDdspH) >> 12; }
-                else { n = nmid; code = midcode; }
-                if (k < n) {
-                    int ox, oy;
-                    decode(code, k, ox, oy);
-                    const int x = cx + ox, y = cy + oy;
-                    slot = k;
-                    ++k;
-                    const bool valid = x >= dxlo && x <= dxhi && y >= dylo && y <= dyhi;
-                    if (SIMPL && phase == PH_SIDE) {
-                        // recompute a distant point visited in an earlier round
-                        const uint32_t d = slot ? ds1 : ds0;
-                        if (!valid || d != kUnknown) continue;
-                        qx = x; qy = y; have = true; counted = false;
-                        break;
-                    }
-                    if (!valid) {
-                        if (SIMPL && phase == PH_DDSP && slot >= 2) { if (slot == 2) ds0 = kInvalid; else ds1 = kInvalid; }
+            for (int r = 0; r < RPL; ++r) cb[r] = 0u;
+
+            for (;;) {
+                int ncand = 0;
+                uint32_t pack = 0;     // slot indices, 4 bits each
+                uint64_t code = 0;     // offsets of the current list
+                bool counted = true;
+                // Advance each group to its next non-empty list (or to done).
+                // Bounded: a fetch plus the transitions of one round.
+                for (int guard = 0; guard < 16 && phase != PH_DONE; ++guard) {
+                    int npts = 0;
+                    if (phase == PH_FETCH) {
+                        int i = 0;
+                        if (l4 == 0) i = atomicAdd(&s_ring_next, 1);
+                        i = __shfl_sync(gmask, i, 0, 4);
+                        if (i >= nring) { phase = PH_DONE; break; }
+                        const uint2 e = ring[i];
+                        const int mb = (int)(e.x & 255u), hb = (int)((e.x >> 8) & 7u);
+                        const int bxl = mb % TXB, byl = mb / TXB;
+                        const int bxg = bx0 + bxl, byg = by0 + byl;
+                        const int px = bxg * B, py = byg * B;
+                        blk = (size_t)byg * NBX + bxg;
+                        dxlo = max(-R, -px); dxhi = min(R, W - B - px);
+                        dylo = max(-R, -py); dyhi = min(R, H - B - py);
+                        wx0 = rx + bxl * B + 4 * wb;
+                        wy0 = R + byl * B + rb * RPL;
+                        const uint32_t* cp =
+                            reinterpret_cast<const uint32_t*>(curS + (byl * B + rb * RPL) * kTile + bxl * B + 4 * wb);
+#pragma unroll
+                        for (int r = 0; r < RPL; ++r) cb[r] = cp[r * (kTile / 4)];
+                        decode(kHcsp, hb, cx, cy);
+                        bxp = cx; byp = cy; bsad = e.y;
+                        pat = (cy == 0) ? PAT_H : PAT_V;  // switching strategy one
+                        if (l4 == 0) {
+                            nsp = (int)((e.x >> 11) & 7u);
+                            // every valid HCSP point is visited
+                            for (int k = 0; k < 7; ++k) {
+                                int ox, oy;
+                                decode(kHcsp, k, ox, oy);
+                                if (ox >= dxlo && ox <= dxhi && oy >= dylo && oy <= dyhi) {
+                                    const int bit = (oy + R) * side + (ox + R);
+                                    bm[bit >> 5] |= 1u << (bit & 31);
+                                    wmin = min(wmin, bit >> 5);
+                                    wmax = max(wmax, bit >> 5);
+                                }
+                            }
+                        }
+                        phase = PH_DDSP;
+                        code = pat ? kDdspV : kDdspH;
+                        npts = 4;
+                    } else if (phase == PH_DDSP) {
+                        if (bxp == cx && byp == cy) {
+                            if (SIMPL) { phase = PH_SIDE; code = (pat ? kDdspV : kDdspH) >> 12; npts = 2; }
+                            else { phase = PH_MID; code = pat ? kMidV : kMidH; npts = 2; }
+                        } else {
+                            if (abs(bxp - cx) + abs(byp - cy) == 1) pat ^= 1;  // switching strategy two
+                            cx = bxp; cy = byp;
+                            code = pat ? kDdspV : kDdspH;
+                            npts = 4;
+                        }
+                    } else if (SIMPL && phase == PH_SIDE) {
+                        phase = PH_MID;
+                        code = pat ? kMidV : kMidH;
+                        npts = 2;
+                        // lane 0 picks the side from the distant points' SADs
+                        int pick = 3;  // both middle points
+                        if (l4 == 0 && !(ds0 == kInvalid && ds1 == kInvalid))
+                            pick = (ds0 == kInvalid) ? 2 : (ds1 == kInvalid) ? 1 : (ds1 < ds0 ? 2 : 1);
+                        pick = __shfl_sync(gmask, pick, 0, 4);
+                        if (pick != 3) { code = code >> (6 * (pick - 1)); npts = 1; }
+                    } else {  // PH_MID evaluated: step 4 done
+                        if (l4 == 0) {
+                            *reinterpret_cast<uint32_t*>(F.mv + 2 * blk) =
+                                (uint32_t)(uint16_t)bxp | ((uint32_t)(uint16_t)byp << 16);
+                            F.sad[blk] = bsad;
+                            if (F.nsp) F.nsp[blk] = (uint16_t)nsp;
+                            for (int i = wmin; i <= wmax; ++i) bm[i] = 0u;
+                            wmin = INT_MAX; wmax = -1;
+                        }
+                        phase = PH_FETCH;
                         continue;
                     }
-                    int vis = 0;
-                    if (lig == 0) {
-                        uint32_t* wp = bm + (y + R) * nwr + ((x + R) >> 5);
-                        const uint32_t bit = 1u << ((x + R) & 31);
-                        const uint32_t wv = *wp;
-                        vis = (wv & bit) != 0u;
-                        if (!vis) {
-                            *wp = wv | bit;
-                            tmin = min(tmin, y + R);
-                            tmax = max(tmax, y + R);
+                    // build the list of new points (lane 0 owns the bitmap and the count);
+                    // only the DCDS^S side list re-evaluates points without counting them
+                    counted = !(SIMPL && phase == PH_SIDE);
+                    uint32_t lst = 0;
+                    if (l4 == 0) {
+                        int n = 0;
+                        if (SIMPL && phase == PH_DDSP) { ds0 = kUnknown; ds1 = kUnknown; }
+                        for (int k = 0; k < npts; ++k) {
+                            int ox, oy;
+                            decode(code, k, ox, oy);
+                            const int x = cx + ox, y = cy + oy;
+                            const bool valid = x >= dxlo && x <= dxhi && y >= dylo && y <= dyhi;
+                            if (!valid) {
+                                if (SIMPL && phase == PH_DDSP && k >= 2) { if (k == 2) ds0 = kInvalid; else ds1 = kInvalid; }
+                                continue;
+                            }
+                            if (counted) {
+                                const int bit = (y + R) * side + (x + R);
+                                const uint32_t m = 1u << (bit & 31);
+                                const uint32_t wv = bm[bit >> 5];
+                                if (wv & m) continue;
+                                bm[bit >> 5] = wv | m;
+                                wmin = min(wmin, bit >> 5);
+                                wmax = max(wmax, bit >> 5);
+                                ++nsp;
+                            } else {
+                                // DCDS^S: recompute a distant point this round did not evaluate
+                                if ((k == 0 ? ds0 : ds1) != kUnknown) continue;
+                            }
+                            lst |= (uint32_t)k << (4 * n);
+                            ++n;
+                        }
+                        lst |= (uint32_t)n << 16;
+                    }
+                    lst = __shfl_sync(gmask, lst, 0, 4);
+                    ncand = (int)(lst >> 16);
+                    pack = lst & 0xffffu;
+                    if (ncand) break;
+                    // empty list: the centre stands; take the next transition
+                }
+                if (!__any_sync(FULL, phase != PH_DONE)) break;
+
+                // ---- evaluate up to 4 candidates of every active group ----
+                uint32_t sad[4] = {0u, 0u, 0u, 0u};
+                int qx[4], qy[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    int ox = 0, oy = 0;
+                    decode(code, (int)((pack >> (4 * i)) & 15u), ox, oy);
+                    qx[i] = cx + ox;
+                    qy[i] = cy + oy;
+                    if (i < ncand) {
+                        const int col = wx0 + qx[i];
+                        const uint8_t* p = win + (wy0 + qy[i]) * WP + (col & ~3);
+                        const unsigned sh = (unsigned)(col & 3) * 8u;
+                        uint32_t a0 = 0u, a1 = 0u;
+#pragma unroll
+                        for (int r = 0; r < RPL; ++r) {
+                            const uint32_t lo = *reinterpret_cast<const uint32_t*>(p + r * WP);
+                            const uint32_t hi = *reinterpret_cast<const uint32_t*>(p + r * WP + 4);
+                            if (r & 1) a1 = sadacc<V>(__funnelshift_r(lo, hi, sh), cb[r], a1);
+                            else a0 = sadacc<V>(__funnelshift_r(lo, hi, sh), cb[r], a0);
+                        }
+                        sad[i] = a0 + a1;
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    sad[i] += __shfl_xor_sync(FULL, sad[i], 1);
+                    sad[i] += __shfl_xor_sync(FULL, sad[i], 2);
+                }
+                if (ncand) {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        if (i < ncand) {
+                            if (counted && sad[i] < bsad) { bsad = sad[i]; bxp = qx[i]; byp = qy[i]; }
+                            if (SIMPL && l4 == 0) {
+                                const int slot = (int)((pack >> (4 * i)) & 15u);
+                                if (phase == PH_DDSP && slot >= 2) { if (slot == 2) ds0 = sad[i]; else ds1 = sad[i]; }
+                                else if (phase == PH_SIDE) { if (slot == 0) ds0 = sad[i]; else ds1 = sad[i]; }
+                            }
                         }
                     }
-                    vis = __shfl_sync(gmask, vis, 0, G);
-                    if (vis) continue;
-                    ++nsp;
-                    qx = x; qy = y; have = true; counted = true;
-                    break;
-                }
-                // ---- list exhausted: pattern transitions (Sec. III-B) ----
-                bool finish = false;
-                if (phase == PH_HCSP) {
-                    if (bxp == 0 && byp == 0) {
-                        finish = true;  // step 1 half-way stop
-                    } else {
-                        pat = (byp == 0) ? PAT_H : PAT_V;  // switching strategy one
-                        cx = bxp; cy = byp;
-                        phase = PH_DDSP; k = 0; ds0 = ds1 = kUnknown;
-                    }
-                } else if (phase == PH_DDSP) {
-                    if (bxp == cx && byp == cy) {
-                        k = 0;
-                        if (SIMPL) { phase = PH_SIDE; }
-                        else { phase = PH_MID; nmid = 2; midcode = pat ? kMidV : kMidH; }
-                    } else {
-                        const int ddx = bxp - cx, ddy = byp - cy;
-                        if (abs(ddx) + abs(ddy) == 1) pat ^= 1;  // switching strategy two
-                        cx = bxp; cy = byp;
-                        k = 0; ds0 = ds1 = kUnknown;
-                    }
-                } else if (SIMPL && phase == PH_SIDE) {
-                    const uint64_t mc = pat ? kMidV : kMidH;
-                    if (ds0 == kInvalid && ds1 == kInvalid) { nmid = 2; midcode = mc; }
-                    else {
-                        const int side = (ds0 == kInvalid) ? 1 : (ds1 == kInvalid) ? 0 : (ds1 < ds0 ? 1 : 0);
-                        nmid = 1; midcode = mc >> (6 * side);
-                    }
-                    phase = PH_MID; k = 0;
-                } else {
-                    finish = true;  // step 4 done
-                }
-                if (finish) {
-                    if (lig == 0) {
-                        *reinterpret_cast<uint32_t*>(F.mv + 2 * (size_t)blk) =
-                            (uint32_t)(uint16_t)bxp | ((uint32_t)(uint16_t)byp << 16);
-                        F.sad[blk] = bsad;
-                        if (F.nsp) F.nsp[blk] = (uint16_t)nsp;
-                        for (int r = tmin; r <= tmax; ++r)
-                            for (int w = 0; w < nwr; ++w) bm[r * nwr + w] = 0u;
-                        tmin = INT_MAX; tmax = -1;
-                    }
-                    phase = PH_FETCH;
                 }
             }
-            if (!__any_sync(0xffffffffu, phase != PH_DONE)) break;
-
-            // ---- one SAD per active group ----
-            uint32_t part = 0u;
-            if (have) {
-                const int col = wx0 + qx + 4 * lig;
-                const uint8_t* base = win + (size_t)(wy0 + qy) * sp + (col & ~3);
-                const unsigned sh = (unsigned)(col & 3) * 8u;
-#pragma unroll
-                for (int r = 0; r < B; ++r) {
-                    const uint32_t lo = *reinterpret_cast<const uint32_t*>(base + r * sp);
-                    const uint32_t hi = *reinterpret_cast<const uint32_t*>(base + r * sp + 4);
-                    part = sadacc<V>(__funnelshift_r(lo, hi, sh), cb[r], part);
-                }
-            }
-#pragma unroll
-            for (int o = 1; o < G; o <<= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-            if (have) {
-                if (counted && part < bsad) { bsad = part; bxp = qx; byp = qy; }
-                if (SIMPL) {
-                    if (phase == PH_DDSP && slot >= 2) { if (slot == 2) ds0 = part; else ds1 = part; }
-                    else if (phase == PH_SIDE) { if (slot == 0) ds0 = part; else ds1 = part; }
-                }
-            }
+        }
+        __syncthreads();  // every read of this stage is done
+        if (NST == 1 && tid == 0) {
+            fence_proxy_async();
+            issue_tile(atomicAdd(head, 1), frames, nframes, ntiles, smem, cur_off, &s_bar[0], &s_tile[0], &s_frame[0]);
         }
     }
 }
 
-template <int B, bool SIMPL>
-cudaError_t launch_t(const FrameDev* frames, int nframes, int ntiles, int max_range, const Shape& s,
-                     int* head, int num_sms, cudaStream_t st)
+template <int B, bool SIMPL, int NST>
+cudaError_t launch_t(const FrameDev* frames, int nframes, int ntiles, int max_range, const Shape& s, int* head,
+                     unsigned* status, int num_sms, cudaStream_t st)
 {
     const size_t smem = dcds_smem_bytes(B, max_range, s);
-    auto kern = dcds_kernel<B, SIMPL>;
+    auto kern = dcds_kernel<B, SIMPL, NST>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    int grid = ntiles;
-    if (s.ctas_per_sm > 0) grid = min(ntiles, s.ctas_per_sm * num_sms);
-    if (grid < 1) grid = 1;
-    const int rxm = (max_range + 15) & ~15;
-    const int sp = ((s.tx * B + 15) & ~15) + 2 * rxm + 16;
-    kern<<<grid, s.threads, smem, st>>>(frames, nframes, ntiles, s.tx, s.ty, max_range, sp, head);
+    int per_sm = s.ctas_per_sm;
+    if (per_sm <= 0) {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, s.threads, smem);
+        if (e != cudaSuccess) return e;
+    }
+    int grid = std::max(1, std::min(ntiles, std::max(per_sm, 1) * num_sms));
+    kern<<<grid, s.threads, smem, st>>>(frames, nframes, ntiles, max_range, head, status);
     return cudaGetLastError();
+}
+
+template <int B, bool SIMPL>
+cudaError_t launch_b(const FrameDev* frames, int nframes, int ntiles, int max_range, const Shape& s, int* head,
+                     unsigned* status, int num_sms, cudaStream_t st)
+{
+    if (s.stages == 2) return launch_t<B, SIMPL, 2>(frames, nframes, ntiles, max_range, s, head, status, num_sms, st);
+    return launch_t<B, SIMPL, 1>(frames, nframes, ntiles, max_range, s, head, status, num_sms, st);
+}
+
+template <int B, bool SIMPL, int NST>
+int occupancy_t(int max_range, const Shape& s)
+{
+    int per_sm = 0;
+    const size_t smem = dcds_smem_bytes(B, max_range, s);
+    if (cudaFuncSetAttribute(dcds_kernel<B, SIMPL, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dcds_kernel<B, SIMPL, NST>, s.threads, smem) !=
+            cudaSuccess)
+        return 0;
+    return per_sm;
 }
 
 }  // namespace
 
 size_t dcds_smem_bytes(int block, int max_range, const Shape& s)
 {
-    const int rxm = (max_range + 15) & ~15;
-    const int sp = ((s.tx * block + 15) & ~15) + 2 * rxm + 16;
-    const size_t win = (size_t)(s.ty * block + 2 * max_range) * sp;
-    const int groups = s.threads / (block / 4);
-    const size_t bm = (size_t)groups * (2 * max_range + 1) * bm_words_per_row(max_range) * 4;
-    return win + bm;
+    const int nst = s.stages == 2 ? 2 : 1;
+    const int stage = win_bytes_max(max_range) + kTile * kTile;
+    const int nmb = (kTile / block) * (kTile / block);
+    const int side = 2 * max_range + 1;
+    const int nwb = (side * side + 31) / 32;
+    return 128 + (size_t)nst * stage + (size_t)nmb * 8 + (size_t)(s.threads / 4) * nwb * 4;
+}
+
+int dcds_ctas_per_sm(int block, int max_range, bool simplified, const Shape& s)
+{
+    const bool two = s.stages == 2;
+    if (block == 16)
+        return simplified ? (two ? occupancy_t<16, true, 2>(max_range, s) : occupancy_t<16, true, 1>(max_range, s))
+                          : (two ? occupancy_t<16, false, 2>(max_range, s) : occupancy_t<16, false, 1>(max_range, s));
+    return simplified ? (two ? occupancy_t<8, true, 2>(max_range, s) : occupancy_t<8, true, 1>(max_range, s))
+                      : (two ? occupancy_t<8, false, 2>(max_range, s) : occupancy_t<8, false, 1>(max_range, s));
 }
 
 cudaError_t launch_dcds(const FrameDev* frames, int nframes, int ntiles, int block, int max_range,
-                        bool simplified, const Shape& s, int* head, unsigned* /*status*/, int num_sms,
+                        bool simplified, const Shape& s, int* head, unsigned* status, int num_sms,
                         cudaStream_t st)
 {
-    if (block == 16) {
-        return simplified ? launch_t<16, true>(frames, nframes, ntiles, max_range, s, head, num_sms, st)
-                          : launch_t<16, false>(frames, nframes, ntiles, max_range, s, head, num_sms, st);
-    }
-    return simplified ? launch_t<8, true>(frames, nframes, ntiles, max_range, s, head, num_sms, st)
-                      : launch_t<8, false>(frames, nframes, ntiles, max_range, s, head, num_sms, st);
+    if (s.threads != 128 && s.threads != 256) return cudaErrorInvalidValue;
+    if (block == 16)
+        return simplified ? launch_b<16, true>(frames, nframes, ntiles, max_range, s, head, status, num_sms, st)
+                          : launch_b<16, false>(frames, nframes, ntiles, max_range, s, head, status, num_sms, st);
+    return simplified ? launch_b<8, true>(frames, nframes, ntiles, max_range, s, head, status, num_sms, st)
+                      : launch_b<8, false>(frames, nframes, ntiles, max_range, s, head, status, num_sms, st);
 }
 
 }  // namespace me

@@ -116,10 +116,10 @@ Shape default_shape(me_ctx* c, int algo, int block, int range)
         return s;
     }
     s.threads = 128;
-    if (block == 16) { s.tx = 16; s.ty = 8; }
-    else { s.tx = 16; s.ty = 16; }
+    s.tx = s.ty = me::kTile / block;
     s.k = 0;
-    s.ctas_per_sm = 1;
+    s.ctas_per_sm = 0;  // from the occupancy of the kernel
+    s.stages = 2;
     (void)c;
     return s;
 }
@@ -129,19 +129,6 @@ Shape pick_shape(me_ctx* c, int algo, int block, int range, int w, int h)
     auto it = c->tuned.find(shape_key(algo, block, range, w, h));
     if (it != c->tuned.end()) return it->second;
     return default_shape(c, algo, block, range);
-}
-
-int persistent_ctas(me_ctx* c, int block, int max_range, bool simplified, const Shape& s)
-{
-    // occupancy of the DCDS kernel for this shape; at least one CTA per SM
-    (void)simplified;
-    const size_t smem = me::dcds_smem_bytes(block, max_range, s);
-    int per_sm = (int)((227 * 1024) / (smem + 1024));
-    const int by_threads = 2048 / s.threads;
-    per_sm = std::min(per_sm, by_threads);
-    per_sm = std::min(per_sm, 16);
-    (void)c;
-    return std::max(per_sm, 1);
 }
 
 int check_frame(me_ctx* c, const uint8_t* cur, const uint8_t* ref, int w, int h, int pitch, int block,
@@ -190,7 +177,8 @@ int take_slot(me_ctx* c, size_t bytes, Slot** out)
     return ME_OK;
 }
 
-// Fill the device-side table (tiles per frame) into `table`; returns tiles.
+// Fill the device-side table (tiles per frame, TMA maps for DCDS) into
+// `table`; returns the number of tiles, or -1 if a tensor map is rejected.
 int build_table(const me_frame_desc* d, int n, int block, const Shape& s, bool fs, FrameDev* table,
                 int* max_range)
 {
@@ -208,8 +196,14 @@ int build_table(const me_frame_desc* d, int n, int block, const Shape& s, bool f
         f.range = d[i].range;
         f.nbx = d[i].w / block;
         f.nby = d[i].h / block;
-        f.tiles_x = (f.nbx + s.tx - 1) / s.tx;
-        f.tiles_y = fs ? f.nby : (f.nby + s.ty - 1) / s.ty;
+        if (fs) {
+            f.tiles_x = (f.nbx + s.tx - 1) / s.tx;
+            f.tiles_y = f.nby;
+        } else {
+            f.tiles_x = (f.w + me::kTile - 1) / me::kTile;
+            f.tiles_y = (f.h + me::kTile - 1) / me::kTile;
+            if (!me::encode_frame_maps(f)) return -1;
+        }
         f.tile_base = tiles;
         tiles += f.tiles_x * f.tiles_y;
         mr = std::max(mr, f.range);
@@ -244,9 +238,7 @@ cudaError_t launch_search(me_ctx* c, void* dev, int n, int ntiles, int block, in
     if (algo == ME_ALGO_FS) return me::launch_fs(table, n, ntiles, block, max_range, s, st);
     cudaError_t e = cudaMemsetAsync(head, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
-    Shape t = s;
-    t.ctas_per_sm = persistent_ctas(c, block, max_range, algo == ME_ALGO_DCDS_S, s);
-    return me::launch_dcds(table, n, ntiles, block, max_range, algo == ME_ALGO_DCDS_S, t, head, c->status,
+    return me::launch_dcds(table, n, ntiles, block, max_range, algo == ME_ALGO_DCDS_S, s, head, c->status,
                            c->num_sms, st);
 }
 
@@ -259,6 +251,7 @@ int run_batch(me_ctx* c, const me_frame_desc* d, int n, int block, int algo, con
     FrameDev* table = reinterpret_cast<FrameDev*>(reinterpret_cast<char*>(slot->host) + kHeadBytes);
     int max_range = 1;
     const int ntiles = build_table(d, n, block, s, algo == ME_ALGO_FS, table, &max_range);
+    if (ntiles < 0) return fail(c, ME_ERR_CUDA, "cuTensorMapEncodeTiled rejected a frame description");
     cudaError_t e = cudaMemcpyAsync(slot->dev, slot->host, bytes, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "descriptor upload");
     e = launch_search(c, slot->dev, n, ntiles, block, algo, max_range, s, st);
@@ -275,14 +268,14 @@ void load_tune_cache(me_ctx* c)
     std::ifstream f(c->tune_path);
     std::string line;
     while (std::getline(f, line)) {
-        // algo block range WxH tx ty threads k
+        // algo block range WxH tx ty threads k stages
         std::istringstream is(line);
-        int algo, block, range, tx, ty, th, k;
+        int algo, block, range, tx, ty, th, k, stages;
         std::string wh;
-        if (is >> algo >> block >> range >> wh >> tx >> ty >> th >> k) {
+        if (is >> algo >> block >> range >> wh >> tx >> ty >> th >> k >> stages) {
             int w = 0, h = 0;
             if (sscanf(wh.c_str(), "%dx%d", &w, &h) == 2) {
-                Shape s{tx, ty, th, 0, k};
+                Shape s{tx, ty, th, 0, k, stages};
                 c->tuned[shape_key(algo, block, range, w, h)] = s;
             }
         }
@@ -364,6 +357,7 @@ int me_graph_create(me_ctx* c, const me_frame_desc* descs, int n, int block, int
     std::vector<FrameDev> table(n);
     int max_range = 1;
     const int ntiles = build_table(descs, n, block, s, algo == ME_ALGO_FS, table.data(), &max_range);
+    if (ntiles < 0) return fail(c, ME_ERR_CUDA, "cuTensorMapEncodeTiled rejected a frame description");
     me_graph* g = new me_graph();
     g->ctx = c;
     const size_t bytes = kHeadBytes + sizeof(FrameDev) * (size_t)n;
@@ -480,12 +474,12 @@ int me_tune(me_ctx* c, const uint8_t* cur, const uint8_t* ref, int w, int h, int
             if (me::fs_smem_bytes(block, range, s) <= 100 * 1024) cands.push_back(s);
         }
     } else {
-        const int txs[4] = {8, 16, 16, 32};
-        const int tys[4] = {8, 4, 8, 4};
-        for (int th : {64, 128}) {
-            for (int i = 0; i < 4; ++i) {
-                Shape s{txs[i], block == 8 ? tys[i] * 2 : tys[i], th, 1, 0};
-                if (me::dcds_smem_bytes(block, range, s) <= 200 * 1024) cands.push_back(s);
+        for (int th : {128, 256}) {
+            for (int stages : {1, 2}) {
+                Shape s = default_shape(c, algo, block, range);
+                s.threads = th;
+                s.stages = stages;
+                if (me::dcds_smem_bytes(block, range, s) <= 220 * 1024) cands.push_back(s);
             }
         }
     }
@@ -518,7 +512,7 @@ int me_tune(me_ctx* c, const uint8_t* cur, const uint8_t* ref, int w, int h, int
         std::ofstream f(c->tune_path, std::ios::app);
         const Shape& s = cands[bi];
         f << shape_key(algo, block, range, w, h) << " " << s.tx << " " << s.ty << " " << s.threads << " " << s.k
-          << "\n";
+          << " " << s.stages << "\n";
     }
     if (chosen) *chosen = bi;
     // leave the outputs computed with the chosen shape

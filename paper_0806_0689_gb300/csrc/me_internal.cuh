@@ -2,14 +2,22 @@
 // host code of libme.  Nothing here is shared with the CPU oracle.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 namespace me {
 
-// Device-side view of one frame pair of a launch (64-byte aligned so a CTA
-// reads it with a few vector loads).
+// Pixel size of the square tiles the DCDS kernel stages with TMA.
+constexpr int kTile = 128;
+
+// Device-side view of one frame pair of a launch.  The two tensor maps
+// describe the frames for the TMA unit (DCDS only): the reference window of
+// a tile (box (kTile + 2*rx) x (kTile + 2*R), rx = R rounded up to 16) and
+// the current tile (box kTile x kTile).
 struct __align__(64) FrameDev {
+    CUtensorMap tm_ref;
+    CUtensorMap tm_cur;
     const uint8_t* cur;
     const uint8_t* ref;
     int16_t* mv;
@@ -21,6 +29,10 @@ struct __align__(64) FrameDev {
     int32_t tile_base;         // first global tile index of this frame
     int32_t pad_[1];
 };
+
+// Encode the two tensor maps of `f` (its pointers, sizes and range must be
+// set).  Host code; returns false if the driver rejects the description.
+bool encode_frame_maps(FrameDev& f);
 
 // Device-side view of one frame of an evaluation batch.
 struct __align__(64) EvalDev {
@@ -34,10 +46,11 @@ struct __align__(64) EvalDev {
 
 // Launch shape of the search kernels.
 struct Shape {
-    int tx, ty;        // tile of tx x ty blocks staged together
+    int tx, ty;        // FS: a tile is tx blocks of one block row (ty unused)
     int threads;       // threads per CTA
-    int ctas_per_sm;   // persistent grid = ctas_per_sm * SM count (0 = one CTA per tile)
+    int ctas_per_sm;   // persistent grid = ctas_per_sm * SM count (0 = occupancy)
     int k;             // FS: candidate rows per thread
+    int stages;        // DCDS: 1 = load each tile when needed, 2 = prefetch the next tile
 };
 
 // Status bits a kernel may record (read back by me_check_status).
@@ -84,6 +97,7 @@ cudaError_t launch_dcds(const FrameDev* frames, int nframes, int ntiles, int blo
                         bool simplified, const Shape& s, int* head, unsigned* status, int num_sms,
                         cudaStream_t st);
 size_t dcds_smem_bytes(int block, int max_range, const Shape& s);
+int dcds_ctas_per_sm(int block, int max_range, bool simplified, const Shape& s);
 
 cudaError_t launch_fs(const FrameDev* frames, int nframes, int ntiles, int block, int max_range,
                       const Shape& s, cudaStream_t st);

@@ -88,9 +88,10 @@ extern "C" int me_estimate_batch_noalloc(const me_frame_desc* d, int n, int bloc
 
     me::Shape s{};
     s.threads = 128;
-    s.tx = 16;
-    s.ty = block == 16 ? 8 : 16;
+    s.tx = s.ty = me::kTile / block;
     s.k = 0;
+    s.stages = 2;
+    s.ctas_per_sm = 0;
 
     Chunk chunk;
     int tiles = 0, max_range = 1;
@@ -109,8 +110,10 @@ extern "C" int me_estimate_batch_noalloc(const me_frame_desc* d, int n, int bloc
         f.cur = x.cur; f.ref = x.ref; f.mv = x.mv; f.sad = x.sad; f.nsp = x.nsp;
         f.w = x.w; f.h = x.h; f.pitch = x.pitch; f.range = x.range;
         f.nbx = x.w / block; f.nby = x.h / block;
-        f.tiles_x = (f.nbx + s.tx - 1) / s.tx;
-        f.tiles_y = (f.nby + s.ty - 1) / s.ty;
+        f.tiles_x = (x.w + me::kTile - 1) / me::kTile;
+        f.tiles_y = (x.h + me::kTile - 1) / me::kTile;
+        if (!me::encode_frame_maps(f))
+            return set_err(err, err_len, ME_ERR_CUDA, "cuTensorMapEncodeTiled rejected a frame description");
         f.tile_base = tiles;
         tiles += f.tiles_x * f.tiles_y;
         max_range = std::max(max_range, x.range);
@@ -134,7 +137,6 @@ extern "C" int me_estimate_batch_noalloc(const me_frame_desc* d, int n, int bloc
         e = cudaGetLastError();
         if (e != cudaSuccess) return set_err(err, err_len, ME_ERR_CUDA, cudaGetErrorString(e));
     }
-    s.ctas_per_sm = 1;
     e = me::launch_dcds(reinterpret_cast<const me::FrameDev*>(scratch + kHeadBytes), n, tiles, block, max_range,
                         algo == ME_ALGO_DCDS_S, s, reinterpret_cast<int*>(scratch), nullptr, g_dev[dev].num_sms, st);
     if (e != cudaSuccess) return set_err(err, err_len, ME_ERR_CUDA, cudaGetErrorString(e));
