@@ -191,6 +191,8 @@ def main():
     d_fs = me.Context.frame_descs((curs[i], refs[i], R_, mv_fs[i], sad_fs[i], nsp_fs[i]) for i in range(npairs))
     e_dcds = me.Context.eval_descs((curs[i], refs[i], mv[i], mv_fs[i], nsp[i]) for i in range(npairs))
     e_fs = me.Context.eval_descs((curs[i], refs[i], mv_fs[i], None, nsp_fs[i]) for i in range(npairs))
+    # launch shapes picked by the library's tuner on this batch (outputs are recomputed below)
+    tuned = {"dcds": ctx.me_tune_batch(d_dcds, B_, "dcds"), "fs": ctx.me_tune_batch(d_fs, B_, "fs")}
     g_dcds = ctx.me_graph_create(d_dcds, B_, "dcds")
     g_fs = ctx.me_graph_create(d_fs, B_, "fs")
     stream = torch.cuda.current_stream()
@@ -348,6 +350,7 @@ def main():
                             "frac": fs_absdiff / (fs_launch_ms * 1e-3) / sad_peak,
                             "peak_source": "measured byte-absdiff microbenchmark (me_absdiff_peak)"}},
         "absdiff_peak_per_s": {"variants": rates, "used": used},
+        "tuned_shape_index": tuned,
         "eval_ms": float(np.median(eval_ms)),
         "e2e": {"value": mbs_step * world / (e2e_ms * 1e-3), "unit": "macroblocks/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},

@@ -213,6 +213,11 @@ int me_tune(me_ctx* ctx, const uint8_t* cur, const uint8_t* ref, int w, int h, i
             int range, int algo, int16_t* mv, uint32_t* sad, uint16_t* nsp,
             int* chosen, void* stream);
 
+/* me_tune_batch: the same for a batch of frame pairs (the shape is kept for
+ * batches of the same block, algo, largest range and largest frame size). */
+int me_tune_batch(me_ctx* ctx, const me_frame_desc* descs, int n, int block, int algo, int* chosen,
+                  void* stream);
+
 /* me_absdiff_peak: microbenchmark of the 4-byte SIMD absolute-difference
  * primitives.  Runs `iters` dependent-chain-free accumulations per thread on
  * every SM and returns the measured rate in byte-absolute-differences per

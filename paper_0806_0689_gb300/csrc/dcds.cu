@@ -55,7 +55,7 @@ constexpr uint64_t kMidV = enc(0, -1, 0) | enc(0, 1, 1);
 
 constexpr uint32_t kUnknown = 0xfffffffeu;  // distant-point SAD not produced this round
 constexpr uint32_t kInvalid = 0xffffffffu;  // distant point outside window/frame
-constexpr uint32_t kWaitLimit = 1u << 22;   // bounded mbarrier polling (with back-off, > 1 s)
+constexpr uint32_t kWaitLimit = 1u << 20;   // bounded mbarrier waits (each try_wait call suspends briefly)
 
 __device__ __forceinline__ void decode(uint64_t code, int k, int& ox, int& oy)
 {
@@ -83,12 +83,12 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
                  : "memory");
 }
 
-__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity)
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity)
 {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
         : "r"(smem_addr(bar)), "r"(parity)
@@ -96,13 +96,13 @@ __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity)
     return ok != 0;
 }
 
-// Poll the phase with the given parity; gives up after kWaitLimit polls.
+// Wait for the phase with the given parity.  try_wait suspends the thread in
+// hardware for a bounded time per call; after kWaitLimit calls the wait gives
+// up and the caller reports a timeout.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
 {
-    for (uint32_t i = 0; i < kWaitLimit; ++i) {
-        if (mbar_test(bar, parity)) return true;
-        if (i > 64) __nanosleep(256);
-    }
+    for (uint32_t i = 0; i < kWaitLimit; ++i)
+        if (mbar_try(bar, parity)) return true;
     return false;
 }
 
@@ -267,14 +267,17 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
 #pragma unroll
                 for (int k = 0; k < 7; ++k) acc[k] += __shfl_xor_sync(FULL, acc[k], o);
             const int px = bxg * B, py = byg * B;
-            unsigned vmask = 0;
+            unsigned vmask = 0x7fu;  // all 7 HCSP points inside the window and the frame
+            if (R < 2 || px < 2 || px > W - B - 2 || py < 1 || py > H - B - 1) {
+                vmask = 0;
 #pragma unroll
-            for (int k = 0; k < 7; ++k) {
-                int ox, oy;
-                decode(kHcsp, k, ox, oy);
-                const bool v = abs(ox) <= R && abs(oy) <= R && px + ox >= 0 && px + ox <= W - B &&
-                               py + oy >= 0 && py + oy <= H - B;
-                vmask |= (unsigned)v << k;
+                for (int k = 0; k < 7; ++k) {
+                    int ox, oy;
+                    decode(kHcsp, k, ox, oy);
+                    const bool v = abs(ox) <= R && abs(oy) <= R && px + ox >= 0 && px + ox <= W - B &&
+                                   py + oy >= 0 && py + oy <= H - B;
+                    vmask |= (unsigned)v << k;
+                }
             }
             int best = 0;
             uint32_t bs = acc[0];
@@ -314,20 +317,21 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
             const int side = 2 * R + 1;
             const int nring = s_ring_n;
 
+            // group state, identical in the 4 lanes
             int phase = PH_FETCH, pat = PAT_H, nsp = 0;
             int cx = 0, cy = 0, bxp = 0, byp = 0;
             uint32_t bsad = 0;
             int dxlo = 0, dxhi = 0, dylo = 0, dyhi = 0, wx0 = 0, wy0 = 0;
             size_t blk = 0;
-            int wmin = INT_MAX, wmax = -1;          // bitmap words touched (lane 0)
-            uint32_t ds0 = kUnknown, ds1 = kUnknown;  // distant-point SADs this round (lane 0, DCDS^S)
+            uint32_t ds0 = kUnknown, ds1 = kUnknown;  // distant-point SADs of this round (DCDS^S)
+            int wmin = INT_MAX, wmax = -1;            // bitmap words this lane has set
             uint32_t cb[RPL];
 #pragma unroll
             for (int r = 0; r < RPL; ++r) cb[r] = 0u;
 
             for (;;) {
                 int ncand = 0;
-                uint32_t pack = 0;     // slot indices, 4 bits each
+                uint32_t pack = 0;     // slot indices of the new points, 4 bits each
                 uint64_t code = 0;     // offsets of the current list
                 bool counted = true;
                 // Advance each group to its next non-empty list (or to done).
@@ -355,21 +359,20 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
                         for (int r = 0; r < RPL; ++r) cb[r] = cp[r * (kTile / 4)];
                         decode(kHcsp, hb, cx, cy);
                         bxp = cx; byp = cy; bsad = e.y;
+                        nsp = (int)((e.x >> 11) & 7u);
                         pat = (cy == 0) ? PAT_H : PAT_V;  // switching strategy one
-                        if (l4 == 0) {
-                            nsp = (int)((e.x >> 11) & 7u);
-                            // every valid HCSP point is visited
-                            for (int k = 0; k < 7; ++k) {
-                                int ox, oy;
-                                decode(kHcsp, k, ox, oy);
-                                if (ox >= dxlo && ox <= dxhi && oy >= dylo && oy <= dyhi) {
-                                    const int bit = (oy + R) * side + (ox + R);
-                                    bm[bit >> 5] |= 1u << (bit & 31);
-                                    wmin = min(wmin, bit >> 5);
-                                    wmax = max(wmax, bit >> 5);
-                                }
+                        // every valid HCSP point is visited (lanes take points l4 and l4 + 4)
+                        for (int k = l4; k < 7; k += 4) {
+                            int ox, oy;
+                            decode(kHcsp, k, ox, oy);
+                            if (ox >= dxlo && ox <= dxhi && oy >= dylo && oy <= dyhi) {
+                                const int bit = (oy + R) * side + (ox + R);
+                                atomicOr(&bm[bit >> 5], 1u << (bit & 31));
+                                wmin = min(wmin, bit >> 5);
+                                wmax = max(wmax, bit >> 5);
                             }
                         }
+                        __syncwarp(gmask);  // the group's bitmap writes are visible to its 4 lanes
                         phase = PH_DDSP;
                         code = pat ? kDdspV : kDdspH;
                         npts = 4;
@@ -384,64 +387,64 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
                             npts = 4;
                         }
                     } else if (SIMPL && phase == PH_SIDE) {
+                        // step 4 of DCDS^S: the middle point on the side of the better distant point
                         phase = PH_MID;
                         code = pat ? kMidV : kMidH;
                         npts = 2;
-                        // lane 0 picks the side from the distant points' SADs
-                        int pick = 3;  // both middle points
-                        if (l4 == 0 && !(ds0 == kInvalid && ds1 == kInvalid))
-                            pick = (ds0 == kInvalid) ? 2 : (ds1 == kInvalid) ? 1 : (ds1 < ds0 ? 2 : 1);
-                        pick = __shfl_sync(gmask, pick, 0, 4);
-                        if (pick != 3) { code = code >> (6 * (pick - 1)); npts = 1; }
+                        if (!(ds0 == kInvalid && ds1 == kInvalid)) {
+                            const int pick = (ds0 == kInvalid) ? 1 : (ds1 == kInvalid) ? 0 : (ds1 < ds0 ? 1 : 0);
+                            code >>= 6 * pick;
+                            npts = 1;
+                        }
                     } else {  // PH_MID evaluated: step 4 done
                         if (l4 == 0) {
                             *reinterpret_cast<uint32_t*>(F.mv + 2 * blk) =
                                 (uint32_t)(uint16_t)bxp | ((uint32_t)(uint16_t)byp << 16);
                             F.sad[blk] = bsad;
                             if (F.nsp) F.nsp[blk] = (uint16_t)nsp;
-                            for (int i = wmin; i <= wmax; ++i) bm[i] = 0u;
-                            wmin = INT_MAX; wmax = -1;
                         }
+                        for (int i = wmin; i <= wmax; ++i) bm[i] = 0u;
+                        wmin = INT_MAX; wmax = -1;
+                        __syncwarp(gmask);
                         phase = PH_FETCH;
                         continue;
                     }
-                    // build the list of new points (lane 0 owns the bitmap and the count);
-                    // only the DCDS^S side list re-evaluates points without counting them
+                    // Build the list of new points: lane k checks point k.  Only the
+                    // DCDS^S side list re-evaluates points without counting them.
                     counted = !(SIMPL && phase == PH_SIDE);
-                    uint32_t lst = 0;
-                    if (l4 == 0) {
-                        int n = 0;
-                        if (SIMPL && phase == PH_DDSP) { ds0 = kUnknown; ds1 = kUnknown; }
-                        for (int k = 0; k < npts; ++k) {
-                            int ox, oy;
-                            decode(code, k, ox, oy);
-                            const int x = cx + ox, y = cy + oy;
-                            const bool valid = x >= dxlo && x <= dxhi && y >= dylo && y <= dyhi;
-                            if (!valid) {
-                                if (SIMPL && phase == PH_DDSP && k >= 2) { if (k == 2) ds0 = kInvalid; else ds1 = kInvalid; }
-                                continue;
-                            }
+                    bool valid = false, fresh = false;
+                    int bit = 0;
+                    if (l4 < npts) {
+                        int ox, oy;
+                        decode(code, l4, ox, oy);
+                        const int x = cx + ox, y = cy + oy;
+                        valid = x >= dxlo && x <= dxhi && y >= dylo && y <= dyhi;
+                        if (valid) {
                             if (counted) {
-                                const int bit = (y + R) * side + (x + R);
-                                const uint32_t m = 1u << (bit & 31);
-                                const uint32_t wv = bm[bit >> 5];
-                                if (wv & m) continue;
-                                bm[bit >> 5] = wv | m;
-                                wmin = min(wmin, bit >> 5);
-                                wmax = max(wmax, bit >> 5);
-                                ++nsp;
+                                bit = (y + R) * side + (x + R);
+                                fresh = ((bm[bit >> 5] >> (bit & 31)) & 1u) == 0u;
                             } else {
-                                // DCDS^S: recompute a distant point this round did not evaluate
-                                if ((k == 0 ? ds0 : ds1) != kUnknown) continue;
+                                fresh = (l4 == 0 ? ds0 : ds1) == kUnknown;
                             }
-                            lst |= (uint32_t)k << (4 * n);
-                            ++n;
                         }
-                        lst |= (uint32_t)n << 16;
                     }
-                    lst = __shfl_sync(gmask, lst, 0, 4);
-                    ncand = (int)(lst >> 16);
-                    pack = lst & 0xffffu;
+                    const unsigned shift = lane & ~3u;
+                    const unsigned vb = (__ballot_sync(gmask, valid) >> shift) & 15u;
+                    const unsigned nb = (__ballot_sync(gmask, fresh) >> shift) & 15u;
+                    if (counted && fresh) {
+                        atomicOr(&bm[bit >> 5], 1u << (bit & 31));
+                        wmin = min(wmin, bit >> 5);
+                        wmax = max(wmax, bit >> 5);
+                    }
+                    __syncwarp(gmask);  // ordered before any later check by another lane
+                    if (SIMPL && phase == PH_DDSP) {
+                        ds0 = (vb & 4u) ? kUnknown : kInvalid;
+                        ds1 = (vb & 8u) ? kUnknown : kInvalid;
+                    }
+                    if (counted) nsp += __popc(nb);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        if ((nb >> k) & 1u) { pack |= (uint32_t)k << (4 * ncand); ++ncand; }
                     if (ncand) break;
                     // empty list: the centre stands; take the next transition
                 }
@@ -481,7 +484,7 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
                     for (int i = 0; i < 4; ++i) {
                         if (i < ncand) {
                             if (counted && sad[i] < bsad) { bsad = sad[i]; bxp = qx[i]; byp = qy[i]; }
-                            if (SIMPL && l4 == 0) {
+                            if (SIMPL) {
                                 const int slot = (int)((pack >> (4 * i)) & 15u);
                                 if (phase == PH_DDSP && slot >= 2) { if (slot == 2) ds0 = sad[i]; else ds1 = sad[i]; }
                                 else if (phase == PH_SIDE) { if (slot == 0) ds0 = sad[i]; else ds1 = sad[i]; }

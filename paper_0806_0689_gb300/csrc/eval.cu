@@ -5,7 +5,16 @@
 // search points, number of blocks whose MV equals the FS MV, and the sum of
 // round(2^24 * |mv - mv_fs|).  Integer atomics make the sums independent of
 // scheduling.  The ratios and the PSNR are formed on the host.
+//
+// Mapping: one item = one B-pixel row segment of one block.  Consecutive
+// threads take consecutive blocks of the same pixel row, so a warp reads 32
+// neighbouring segments of cur (one coalesced span) and of ref.  Each thread
+// walks many items (grid-stride) and the CTA reduces once at the end.  An MV
+// that moves its block out of the frame is not compensated; its pixels are
+// left out of ME_SUM_PIXELS and of the error sums.
 #include "me_internal.cuh"
+
+#include <algorithm>
 
 namespace me {
 namespace {
@@ -14,48 +23,62 @@ template <int B>
 __global__ void __launch_bounds__(256) eval_kernel(const EvalDev* __restrict__ frames,
                                                    unsigned long long* __restrict__ sums)
 {
-    constexpr int BW = B / 4;
-    constexpr int ITEMS = B * BW;  // (row, word) items per block
+    constexpr int BW = B / 4;  // words per segment
     const EvalDev& F = frames[blockIdx.y];
     unsigned long long* out = sums + (size_t)blockIdx.y * 8;
-    const int nb = F.nbx * F.nby;
-    const long total = (long)nb * ITEMS;
+    const int nbx = F.nbx, W = F.w, H = F.h, P = F.pitch;
+    const int total = F.h * nbx;  // (pixel row, block column) items
+    const uint32_t* mvw = reinterpret_cast<const uint32_t*>(F.mv);
+    const uint32_t* fsw = reinterpret_cast<const uint32_t*>(F.mv_fs);
 
     unsigned long long s_abs = 0, s_sq = 0, s_nsp = 0, s_eq = 0, s_dist = 0, s_pix = 0;
-    for (long it = (long)blockIdx.x * blockDim.x + threadIdx.x; it < total; it += (long)gridDim.x * blockDim.x) {
-        const int k = (int)(it / ITEMS);
-        const int rem = (int)(it - (long)k * ITEMS);
-        const int r = rem / BW, w = rem - r * BW;
-        const int bx = k % F.nbx, by = k / F.nbx;
-        const uint32_t mvw = __ldg(reinterpret_cast<const uint32_t*>(F.mv) + k);
-        const int dx = (int)(int16_t)(mvw & 0xffffu), dy = (int)(int16_t)(mvw >> 16);
-        const int x = bx * B + 4 * w, y = by * B + r;
-        const bool ok = bx * B + dx >= 0 && bx * B + dx <= F.w - B && by * B + dy >= 0 && by * B + dy <= F.h - B;
-        if (ok) {
-            const uint32_t c = __ldg(reinterpret_cast<const uint32_t*>(F.cur + (size_t)y * F.pitch + x));
-            const long g = (long)(y + dy) * F.pitch + x + dx;
-            const long a = g & ~3l;
+    for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < total; it += gridDim.x * blockDim.x) {
+        const int y = it / nbx, bx = it - y * nbx;
+        const int by = y / B, r = y - by * B;
+        const int k = by * nbx + bx;
+        const uint32_t m = __ldg(mvw + k);
+        const int dx = (int)(int16_t)(m & 0xffffu), dy = (int)(int16_t)(m >> 16);
+        const int x = bx * B;
+        if (x + dx >= 0 && x + dx <= W - B && by * B + dy >= 0 && by * B + dy <= H - B) {
+            const uint8_t* cp = F.cur + (size_t)y * P + x;
+            uint32_t c[BW];
+            if constexpr (BW == 4) {
+                const uint4 v = __ldg(reinterpret_cast<const uint4*>(cp));
+                c[0] = v.x; c[1] = v.y; c[2] = v.z; c[3] = v.w;
+            } else {
+                const uint2 v = __ldg(reinterpret_cast<const uint2*>(cp));
+                c[0] = v.x; c[1] = v.y;
+            }
+            const long g = (long)(y + dy) * P + x + dx;
+            const uint32_t* rp = reinterpret_cast<const uint32_t*>(F.ref + (g & ~3l));
             const unsigned sh = (unsigned)(g & 3) * 8u;
-            const uint32_t lo = __ldg(reinterpret_cast<const uint32_t*>(F.ref + a));
-            const uint32_t hi = sh ? __ldg(reinterpret_cast<const uint32_t*>(F.ref + a + 4)) : 0u;
-            const uint32_t p = __funnelshift_r(lo, hi, sh);
-            const uint32_t ad = __vabsdiffu4(c, p);
-            s_abs += __dp4a(ad, 0x01010101u, 0u);
-            s_sq += __dp4a(ad, ad, 0u);
-            s_pix += 4;
+            uint32_t wv[BW + 1];
+#pragma unroll
+            for (int i = 0; i < BW; ++i) wv[i] = __ldg(rp + i);
+            // the word after the segment is read only when the segment is unaligned,
+            // and then it still lies inside the row
+            wv[BW] = sh ? __ldg(rp + BW) : 0u;
+            uint32_t a = 0, q = 0;
+#pragma unroll
+            for (int i = 0; i < BW; ++i) {
+                const uint32_t d = __vabsdiffu4(c[i], __funnelshift_r(wv[i], wv[i + 1], sh));
+                a = __dp4a(d, 0x01010101u, a);
+                q = __dp4a(d, d, q);
+            }
+            s_abs += a;
+            s_sq += q;
+            s_pix += B;
         }
-        if (rem == 0) {
+        if (r == 0) {
             if (F.nsp) s_nsp += F.nsp[k];
-            if (F.mv_fs) {
-                const uint32_t fw = __ldg(reinterpret_cast<const uint32_t*>(F.mv_fs) + k);
+            if (fsw) {
+                const uint32_t fw = __ldg(fsw + k);
                 const int ex = dx - (int)(int16_t)(fw & 0xffffu), ey = dy - (int)(int16_t)(fw >> 16);
                 s_eq += (ex == 0 && ey == 0);
                 s_dist += (unsigned long long)__double2ll_rn(sqrt((double)(ex * ex + ey * ey)) * 16777216.0);
             }
         }
     }
-    // an MV that moves its block out of the frame is not compensated; its
-    // pixels are left out of ME_SUM_PIXELS and of the error sums
     unsigned long long v[6] = {s_abs, s_sq, s_nsp, s_eq, s_dist, s_pix};
     __shared__ unsigned long long red[6][8];
 #pragma unroll
@@ -76,21 +99,21 @@ __global__ void __launch_bounds__(256) eval_kernel(const EvalDev* __restrict__ f
         if (a) atomicAdd(out + slot, a);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        out[5] = (unsigned long long)nb;
+        out[5] = (unsigned long long)F.nbx * F.nby;
         out[7] = F.mv_fs ? 1ull : 0ull;
     }
 }
 
 }  // namespace
 
-cudaError_t launch_eval(const EvalDev* frames, int nframes, int block, int max_blocks,
+cudaError_t launch_eval(const EvalDev* frames, int nframes, int block, int max_blocks, int num_sms,
                         unsigned long long* sums, cudaStream_t st)
 {
-    const int items = block * (block / 4);
-    long total = (long)max_blocks * items;
-    int gx = (int)((total + 255) / 256);
-    if (gx > 2048) gx = 2048;
-    if (gx < 1) gx = 1;
+    // enough CTAs to fill the GPU a few times over, and at least ~16 items per thread
+    const long items = (long)max_blocks * block;
+    const long by_items = (items + 256 * 16 - 1) / (256 * 16);
+    const long by_gpu = (long)num_sms * 8 / std::max(nframes, 1) + 1;
+    int gx = (int)std::max(1l, std::min(by_items, by_gpu));
     dim3 grid(gx, nframes);
     if (block == 16) eval_kernel<16><<<grid, 256, 0, st>>>(frames, sums);
     else eval_kernel<8><<<grid, 256, 0, st>>>(frames, sums);

@@ -19,6 +19,10 @@ using me::EvalDev;
 using me::FrameDev;
 using me::Shape;
 
+#ifndef ME_DCDS_STAGES
+#define ME_DCDS_STAGES 1  // default tile staging of the DCDS kernel (measured: 1 stage, 4 CTAs/SM)
+#endif
+
 namespace {
 
 // One reusable upload slot: a device buffer [queue head | descriptor table],
@@ -119,7 +123,7 @@ Shape default_shape(me_ctx* c, int algo, int block, int range)
     s.tx = s.ty = me::kTile / block;
     s.k = 0;
     s.ctas_per_sm = 0;  // from the occupancy of the kernel
-    s.stages = 2;
+    s.stages = ME_DCDS_STAGES;
     (void)c;
     return s;
 }
@@ -429,7 +433,7 @@ int me_eval_batch(me_ctx* c, const me_eval_desc* d, int n, int block, uint64_t* 
     if (e == cudaSuccess) e = cudaMemsetAsync(sums, 0, sizeof(uint64_t) * ME_NSUMS * (size_t)n, st);
     if (e == cudaSuccess)
         e = me::launch_eval(reinterpret_cast<const EvalDev*>(reinterpret_cast<char*>(slot->dev) + kHeadBytes), n,
-                            block, max_blocks, reinterpret_cast<unsigned long long*>(sums), st);
+                            block, max_blocks, c->num_sms, reinterpret_cast<unsigned long long*>(sums), st);
     if (e == cudaSuccess) e = cudaEventRecord(slot->done, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "evaluation launch");
     slot->used = true;
@@ -457,29 +461,29 @@ int me_stats_from_sums(const uint64_t* s, me_stats* out)
     return ME_OK;
 }
 
-int me_tune(me_ctx* c, const uint8_t* cur, const uint8_t* ref, int w, int h, int block, int range, int algo,
-            int16_t* mv, uint32_t* sad, uint16_t* nsp, int* chosen, void* stream)
+int me_tune_batch(me_ctx* c, const me_frame_desc* descs, int n, int block, int algo, int* chosen, void* stream)
 {
     if (!c) return ME_ERR_ARG;
-    me_frame_desc d{cur, ref, w, h, w, range, mv, sad, nsp};
-    int rc = validate_batch(c, &d, 1, block, algo);
+    int rc = validate_batch(c, descs, n, block, algo);
     if (rc != ME_OK) return rc;
     cudaStream_t st = (cudaStream_t)stream;
+    int mr = 1, mw = 0, mh = 0;
+    for (int i = 0; i < n; ++i) { mr = std::max(mr, descs[i].range); mw = std::max(mw, descs[i].w); mh = std::max(mh, descs[i].h); }
     std::vector<Shape> cands;
     if (algo == ME_ALGO_FS) {
-        const Shape base = default_shape(c, algo, block, range);
+        const Shape base = default_shape(c, algo, block, mr);
         for (int tx = 2; tx <= 32; tx += 2) {
             Shape s = base;
             s.tx = tx;
-            if (me::fs_smem_bytes(block, range, s) <= 100 * 1024) cands.push_back(s);
+            if (me::fs_smem_bytes(block, mr, s) <= 100 * 1024) cands.push_back(s);
         }
     } else {
         for (int th : {128, 256}) {
             for (int stages : {1, 2}) {
-                Shape s = default_shape(c, algo, block, range);
+                Shape s = default_shape(c, algo, block, mr);
                 s.threads = th;
                 s.stages = stages;
-                if (me::dcds_smem_bytes(block, range, s) <= 220 * 1024) cands.push_back(s);
+                if (me::dcds_smem_bytes(block, mr, s) <= 220 * 1024) cands.push_back(s);
             }
         }
     }
@@ -492,7 +496,7 @@ int me_tune(me_ctx* c, const uint8_t* cur, const uint8_t* ref, int w, int h, int
         float tbest = 1e30f;
         for (int rep = 0; rep < 4; ++rep) {
             cudaEventRecord(e0, st);
-            rc = run_batch(c, &d, 1, block, algo, cands[i], st);
+            rc = run_batch(c, descs, n, block, algo, cands[i], st);
             cudaEventRecord(e1, st);
             if (rc != ME_OK) break;
             cudaEventSynchronize(e1);
@@ -507,16 +511,23 @@ int me_tune(me_ctx* c, const uint8_t* cur, const uint8_t* ref, int w, int h, int
     cudaEventDestroy(e1);
     if (rc != ME_OK) return rc;
     if (bi < 0) return fail(c, ME_ERR_UNSUPPORTED, "no launch shape fits this configuration");
-    c->tuned[shape_key(algo, block, range, w, h)] = cands[bi];
+    c->tuned[shape_key(algo, block, mr, mw, mh)] = cands[bi];
     if (!c->tune_path.empty()) {
         std::ofstream f(c->tune_path, std::ios::app);
         const Shape& s = cands[bi];
-        f << shape_key(algo, block, range, w, h) << " " << s.tx << " " << s.ty << " " << s.threads << " " << s.k
+        f << shape_key(algo, block, mr, mw, mh) << " " << s.tx << " " << s.ty << " " << s.threads << " " << s.k
           << " " << s.stages << "\n";
     }
     if (chosen) *chosen = bi;
     // leave the outputs computed with the chosen shape
-    return run_batch(c, &d, 1, block, algo, cands[bi], st);
+    return run_batch(c, descs, n, block, algo, cands[bi], st);
+}
+
+int me_tune(me_ctx* c, const uint8_t* cur, const uint8_t* ref, int w, int h, int block, int range, int algo,
+            int16_t* mv, uint32_t* sad, uint16_t* nsp, int* chosen, void* stream)
+{
+    me_frame_desc d{cur, ref, w, h, w, range, mv, sad, nsp};
+    return me_tune_batch(c, &d, 1, block, algo, chosen, stream);
 }
 
 int me_absdiff_peak(me_ctx* c, int iters, double* out, int n_variants, int* used, void* stream)

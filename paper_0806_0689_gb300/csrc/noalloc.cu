@@ -90,7 +90,7 @@ extern "C" int me_estimate_batch_noalloc(const me_frame_desc* d, int n, int bloc
     s.threads = 128;
     s.tx = s.ty = me::kTile / block;
     s.k = 0;
-    s.stages = 2;
+    s.stages = 1;
     s.ctas_per_sm = 0;
 
     Chunk chunk;

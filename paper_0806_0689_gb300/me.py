@@ -24,7 +24,7 @@ ALGOS = {"fs": ME_ALGO_FS, "dcds": ME_ALGO_DCDS, "dcds_s": ME_ALGO_DCDS_S, "dcds
 
 EXPORTS = ["me_init", "me_free", "me_last_error", "me_estimate", "me_estimate_batch", "me_graph_create",
            "me_graph_launch", "me_graph_free", "me_eval", "me_eval_batch", "me_stats_from_sums", "me_tune",
-           "me_absdiff_peak", "me_check_status", "me_estimate_batch_noalloc"]
+           "me_absdiff_peak", "me_check_status", "me_estimate_batch_noalloc", "me_tune_batch"]
 
 
 class MeError(RuntimeError):
@@ -82,6 +82,7 @@ def load(build_if_missing: bool = True):
             L.me_eval_batch.argtypes = [P, ctypes.POINTER(EvalDesc), I, I, P, P]
             L.me_stats_from_sums.argtypes = [P, ctypes.POINTER(Stats)]
             L.me_tune.argtypes = [P, P, P, I, I, I, I, I, P, P, P, ctypes.POINTER(I), P]
+            L.me_tune_batch.argtypes = [P, ctypes.POINTER(FrameDesc), I, I, I, ctypes.POINTER(I), P]
             L.me_absdiff_peak.argtypes = [P, I, ctypes.POINTER(ctypes.c_double), I, ctypes.POINTER(I), P]
             L.me_check_status.argtypes = [P, P]
             L.me_estimate_batch_noalloc.argtypes = [ctypes.POINTER(FrameDesc), I, I, I, P, ctypes.c_char_p, I]
@@ -194,6 +195,12 @@ class Context:
         chosen = ctypes.c_int(-1)
         self._check(self.L.me_tune(self.h, _ptr(cur), _ptr(ref), w, h, block, rng, ALGOS.get(algo, algo),
                                    _ptr(mv), _ptr(sad), _ptr(nsp), ctypes.byref(chosen), _stream(stream)))
+        return chosen.value
+
+    def me_tune_batch(self, descs, block, algo, stream=None):
+        chosen = ctypes.c_int(-1)
+        self._check(self.L.me_tune_batch(self.h, descs, len(descs), block, ALGOS.get(algo, algo),
+                                         ctypes.byref(chosen), _stream(stream)))
         return chosen.value
 
     def me_absdiff_peak(self, iters=4096, n_variants=4, stream=None):
