@@ -224,10 +224,15 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
             issue_tile(atomicAdd(head, 1), frames, nframes, ntiles, smem + (st ^ 1) * stage_bytes, cur_off,
                        &s_bar[st ^ 1], &s_tile[st ^ 1], &s_frame[st ^ 1]);
         }
-        const FrameDev& F = frames[s_frame[st]];
-        const int W = F.w, H = F.h, R = F.range, NBX = F.nbx, NBY = F.nby;
-        const int lt = t - F.tile_base;
-        const int tile_y = lt / F.tiles_x, tile_x = lt - tile_y * F.tiles_x;
+        // descriptor fields in registers: the output stores below cannot alias them
+        const FrameDev* Fp = frames + s_frame[st];
+        const int W = Fp->w, H = Fp->h, R = Fp->range, NBX = Fp->nbx, NBY = Fp->nby;
+        uint32_t* __restrict__ out_mv = reinterpret_cast<uint32_t*>(Fp->mv);
+        uint32_t* __restrict__ out_sad = Fp->sad;
+        uint16_t* __restrict__ out_nsp = Fp->nsp;
+        const int lt = t - Fp->tile_base;
+        const int txs = Fp->tiles_x;
+        const int tile_y = lt / txs, tile_x = lt - tile_y * txs;
         const int bx0 = tile_x * TXB, by0 = tile_y * TXB;
         const int rx = (R + 15) & ~15;
         const int WP = kTile + 2 * rx;  // window row pitch
@@ -287,9 +292,9 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
             const bool leader = (w == 0) && exists;
             if (leader && best == 0) {
                 const size_t blk = (size_t)byg * NBX + bxg;
-                *reinterpret_cast<uint32_t*>(F.mv + 2 * blk) = 0u;
-                F.sad[blk] = bs;
-                if (F.nsp) F.nsp[blk] = (uint16_t)__popc(vmask);
+                out_mv[blk] = 0u;
+                out_sad[blk] = bs;
+                if (out_nsp) out_nsp[blk] = (uint16_t)__popc(vmask);
             }
             const bool cont = leader && best != 0;
             const unsigned bal = __ballot_sync(FULL, cont);
@@ -309,16 +314,21 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
         __syncthreads();
 
         // ------------------------------------------------ phase B: diamond rounds
+        // Every iteration runs one round for every group of the warp, in
+        // converged code: (1) groups without a block take the next ring entries
+        // (one atomic per warp), (2) each group builds its round's list, lane k
+        // checking point k, (3) the new points' SADs are evaluated together,
+        // (4) the switching strategies pick the next list.
         {
-            const int gq = tid >> 2, l4 = lane & 3;
-            const unsigned gmask = 0xfu << (lane & ~3);
+            const int gq = tid >> 2, l4 = lane & 3, lead = lane & ~3;
             const int wb = l4 % WPB, rb = l4 / WPB;
             uint32_t* bm = bm_all + gq * nwb;
             const int side = 2 * R + 1;
             const int nring = s_ring_n;
 
             // group state, identical in the 4 lanes
-            int phase = PH_FETCH, pat = PAT_H, nsp = 0;
+            int act = 0;  // 0: needs a block, 1: searching, 2: done
+            int phase = PH_DDSP, pat = PAT_H, nsp = 0, pick = -1;
             int cx = 0, cy = 0, bxp = 0, byp = 0;
             uint32_t bsad = 0;
             int dxlo = 0, dxhi = 0, dylo = 0, dyhi = 0, wx0 = 0, wy0 = 0;
@@ -329,157 +339,142 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
 #pragma unroll
             for (int r = 0; r < RPL; ++r) cb[r] = 0u;
 
-            for (;;) {
-                int ncand = 0;
-                uint32_t pack = 0;     // slot indices of the new points, 4 bits each
-                uint64_t code = 0;     // offsets of the current list
-                bool counted = true;
-                // Advance each group to its next non-empty list (or to done).
-                // Bounded: a fetch plus the transitions of one round.
-                for (int guard = 0; guard < 16 && phase != PH_DONE; ++guard) {
-                    int npts = 0;
-                    if (phase == PH_FETCH) {
-                        int i = 0;
-                        if (l4 == 0) i = atomicAdd(&s_ring_next, 1);
-                        i = __shfl_sync(gmask, i, 0, 4);
-                        if (i >= nring) { phase = PH_DONE; break; }
-                        const uint2 e = ring[i];
-                        const int mb = (int)(e.x & 255u), hb = (int)((e.x >> 8) & 7u);
-                        const int bxl = mb % TXB, byl = mb / TXB;
-                        const int bxg = bx0 + bxl, byg = by0 + byl;
-                        const int px = bxg * B, py = byg * B;
-                        blk = (size_t)byg * NBX + bxg;
-                        dxlo = max(-R, -px); dxhi = min(R, W - B - px);
-                        dylo = max(-R, -py); dyhi = min(R, H - B - py);
-                        wx0 = rx + bxl * B + 4 * wb;
-                        wy0 = R + byl * B + rb * RPL;
-                        const uint32_t* cp =
-                            reinterpret_cast<const uint32_t*>(curS + (byl * B + rb * RPL) * kTile + bxl * B + 4 * wb);
-#pragma unroll
-                        for (int r = 0; r < RPL; ++r) cb[r] = cp[r * (kTile / 4)];
-                        decode(kHcsp, hb, cx, cy);
-                        bxp = cx; byp = cy; bsad = e.y;
-                        nsp = (int)((e.x >> 11) & 7u);
-                        pat = (cy == 0) ? PAT_H : PAT_V;  // switching strategy one
-                        // every valid HCSP point is visited (lanes take points l4 and l4 + 4)
-                        for (int k = l4; k < 7; k += 4) {
-                            int ox, oy;
-                            decode(kHcsp, k, ox, oy);
-                            if (ox >= dxlo && ox <= dxhi && oy >= dylo && oy <= dyhi) {
-                                const int bit = (oy + R) * side + (ox + R);
-                                atomicOr(&bm[bit >> 5], 1u << (bit & 31));
-                                wmin = min(wmin, bit >> 5);
-                                wmax = max(wmax, bit >> 5);
-                            }
-                        }
-                        __syncwarp(gmask);  // the group's bitmap writes are visible to its 4 lanes
-                        phase = PH_DDSP;
-                        code = pat ? kDdspV : kDdspH;
-                        npts = 4;
-                    } else if (phase == PH_DDSP) {
-                        if (bxp == cx && byp == cy) {
-                            if (SIMPL) { phase = PH_SIDE; code = (pat ? kDdspV : kDdspH) >> 12; npts = 2; }
-                            else { phase = PH_MID; code = pat ? kMidV : kMidH; npts = 2; }
+            for (int iter = 0;; ++iter) {
+                // ---- (1) fetch: one atomic for all groups of the warp that need a block ----
+                const unsigned need = __ballot_sync(FULL, act == 0 && l4 == 0);
+                if (need) {
+                    const int first = __ffs(need) - 1;
+                    int base = 0;
+                    if (lane == first) base = atomicAdd(&s_ring_next, __popc(need));
+                    base = __shfl_sync(FULL, base, first);
+                    int idx = base + __popc(need & ((1u << lane) - 1u));
+                    idx = __shfl_sync(FULL, idx, lead);
+                    if (act == 0) {
+                        if (idx >= nring) {
+                            act = 2;
                         } else {
-                            if (abs(bxp - cx) + abs(byp - cy) == 1) pat ^= 1;  // switching strategy two
-                            cx = bxp; cy = byp;
-                            code = pat ? kDdspV : kDdspH;
-                            npts = 4;
-                        }
-                    } else if (SIMPL && phase == PH_SIDE) {
-                        // step 4 of DCDS^S: the middle point on the side of the better distant point
-                        phase = PH_MID;
-                        code = pat ? kMidV : kMidH;
-                        npts = 2;
-                        if (!(ds0 == kInvalid && ds1 == kInvalid)) {
-                            const int pick = (ds0 == kInvalid) ? 1 : (ds1 == kInvalid) ? 0 : (ds1 < ds0 ? 1 : 0);
-                            code >>= 6 * pick;
-                            npts = 1;
-                        }
-                    } else {  // PH_MID evaluated: step 4 done
-                        if (l4 == 0) {
-                            *reinterpret_cast<uint32_t*>(F.mv + 2 * blk) =
-                                (uint32_t)(uint16_t)bxp | ((uint32_t)(uint16_t)byp << 16);
-                            F.sad[blk] = bsad;
-                            if (F.nsp) F.nsp[blk] = (uint16_t)nsp;
-                        }
-                        for (int i = wmin; i <= wmax; ++i) bm[i] = 0u;
-                        wmin = INT_MAX; wmax = -1;
-                        __syncwarp(gmask);
-                        phase = PH_FETCH;
-                        continue;
-                    }
-                    // Build the list of new points: lane k checks point k.  Only the
-                    // DCDS^S side list re-evaluates points without counting them.
-                    counted = !(SIMPL && phase == PH_SIDE);
-                    bool valid = false, fresh = false;
-                    int bit = 0;
-                    if (l4 < npts) {
-                        int ox, oy;
-                        decode(code, l4, ox, oy);
-                        const int x = cx + ox, y = cy + oy;
-                        valid = x >= dxlo && x <= dxhi && y >= dylo && y <= dyhi;
-                        if (valid) {
-                            if (counted) {
-                                bit = (y + R) * side + (x + R);
-                                fresh = ((bm[bit >> 5] >> (bit & 31)) & 1u) == 0u;
-                            } else {
-                                fresh = (l4 == 0 ? ds0 : ds1) == kUnknown;
+                            const uint2 e = ring[idx];
+                            const int mb = (int)(e.x & 255u), hb = (int)((e.x >> 8) & 7u);
+                            const int bxl = mb % TXB, byl = mb / TXB;
+                            const int bxg = bx0 + bxl, byg = by0 + byl;
+                            const int px = bxg * B, py = byg * B;
+                            blk = (size_t)byg * NBX + bxg;
+                            dxlo = max(-R, -px); dxhi = min(R, W - B - px);
+                            dylo = max(-R, -py); dyhi = min(R, H - B - py);
+                            wx0 = rx + bxl * B + 4 * wb;
+                            wy0 = R + byl * B + rb * RPL;
+                            const uint32_t* cp = reinterpret_cast<const uint32_t*>(
+                                curS + (byl * B + rb * RPL) * kTile + bxl * B + 4 * wb);
+#pragma unroll
+                            for (int r = 0; r < RPL; ++r) cb[r] = cp[r * (kTile / 4)];
+                            decode(kHcsp, hb, cx, cy);
+                            bxp = cx; byp = cy; bsad = e.y;
+                            nsp = (int)((e.x >> 11) & 7u);
+                            pat = (cy == 0) ? PAT_H : PAT_V;  // switching strategy one
+                            phase = PH_DDSP;
+                            pick = -1;
+                            act = 1;
+                            // every valid HCSP point is visited (lanes take points l4 and l4 + 4)
+                            for (int k = l4; k < 7; k += 4) {
+                                int ox, oy;
+                                decode(kHcsp, k, ox, oy);
+                                if (ox >= dxlo && ox <= dxhi && oy >= dylo && oy <= dyhi) {
+                                    const int bit = (oy + R) * side + (ox + R);
+                                    atomicOr(&bm[bit >> 5], 1u << (bit & 31));
+                                    wmin = min(wmin, bit >> 5);
+                                    wmax = max(wmax, bit >> 5);
+                                }
                             }
                         }
                     }
-                    const unsigned shift = lane & ~3u;
-                    const unsigned vb = (__ballot_sync(gmask, valid) >> shift) & 15u;
-                    const unsigned nb = (__ballot_sync(gmask, fresh) >> shift) & 15u;
-                    if (counted && fresh) {
-                        atomicOr(&bm[bit >> 5], 1u << (bit & 31));
-                        wmin = min(wmin, bit >> 5);
-                        wmax = max(wmax, bit >> 5);
-                    }
-                    __syncwarp(gmask);  // ordered before any later check by another lane
-                    if (SIMPL && phase == PH_DDSP) {
-                        ds0 = (vb & 4u) ? kUnknown : kInvalid;
-                        ds1 = (vb & 8u) ? kUnknown : kInvalid;
-                    }
-                    if (counted) nsp += __popc(nb);
-#pragma unroll
-                    for (int k = 0; k < 4; ++k)
-                        if ((nb >> k) & 1u) { pack |= (uint32_t)k << (4 * ncand); ++ncand; }
-                    if (ncand) break;
-                    // empty list: the centre stands; take the next transition
+                    __syncwarp();  // bitmap initialisation visible to the whole group
                 }
-                if (!__any_sync(FULL, phase != PH_DONE)) break;
+                if (!__any_sync(FULL, act != 2)) break;
 
-                // ---- evaluate up to 4 candidates of every active group ----
+                // ---- (2) this round's list: lane k checks point k ----
+                uint64_t code;
+                int npts;
+                if (phase == PH_DDSP) { code = pat ? kDdspV : kDdspH; npts = 4; }
+                else if (SIMPL && phase == PH_SIDE) { code = (pat ? kDdspV : kDdspH) >> 12; npts = 2; }
+                else {
+                    code = pat ? kMidV : kMidH;
+                    npts = 2;
+                    if (SIMPL && pick >= 0) { code >>= 6 * pick; npts = 1; }
+                }
+                const bool counted = !(SIMPL && phase == PH_SIDE);
+                bool valid = false, fresh = false;
+                int bit = 0;
+                if (act == 1 && l4 < npts) {
+                    int ox, oy;
+                    decode(code, l4, ox, oy);
+                    const int x = cx + ox, y = cy + oy;
+                    valid = x >= dxlo && x <= dxhi && y >= dylo && y <= dyhi;
+                    if (valid) {
+                        if (counted) {
+                            bit = (y + R) * side + (x + R);
+                            fresh = ((bm[bit >> 5] >> (bit & 31)) & 1u) == 0u;
+                        } else {
+                            fresh = (l4 == 0 ? ds0 : ds1) == kUnknown;
+                        }
+                    }
+                }
+                const unsigned vb = (__ballot_sync(FULL, valid) >> lead) & 15u;
+                const unsigned nb = (__ballot_sync(FULL, fresh) >> lead) & 15u;
+                if (counted && fresh) {
+                    atomicOr(&bm[bit >> 5], 1u << (bit & 31));
+                    wmin = min(wmin, bit >> 5);
+                    wmax = max(wmax, bit >> 5);
+                }
+                if (SIMPL && phase == PH_DDSP) {
+                    ds0 = (vb & 4u) ? kUnknown : kInvalid;
+                    ds1 = (vb & 8u) ? kUnknown : kInvalid;
+                }
+                if (counted) nsp += __popc(nb);
+                int ncand = 0;
+                uint32_t pack = 0;  // slot indices of the new points, 4 bits each
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if ((nb >> k) & 1u) { pack |= (uint32_t)k << (4 * ncand); ++ncand; }
+
+                // ---- (3) evaluate the new points (two at a time, all groups together) ----
                 uint32_t sad[4] = {0u, 0u, 0u, 0u};
                 int qx[4], qy[4];
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
                     int ox = 0, oy = 0;
-                    decode(code, (int)((pack >> (4 * i)) & 15u), ox, oy);
-                    qx[i] = cx + ox;
+                    if (i < ncand) decode(code, (int)((pack >> (4 * i)) & 15u), ox, oy);
+                    qx[i] = cx + ox;  // unused slots read the centre: a valid address
                     qy[i] = cy + oy;
-                    if (i < ncand) {
-                        const int col = wx0 + qx[i];
-                        const uint8_t* p = win + (wy0 + qy[i]) * WP + (col & ~3);
-                        const unsigned sh = (unsigned)(col & 3) * 8u;
-                        uint32_t a0 = 0u, a1 = 0u;
+                }
+                const bool more = __any_sync(FULL, ncand > 2);
 #pragma unroll
-                        for (int r = 0; r < RPL; ++r) {
-                            const uint32_t lo = *reinterpret_cast<const uint32_t*>(p + r * WP);
-                            const uint32_t hi = *reinterpret_cast<const uint32_t*>(p + r * WP + 4);
-                            if (r & 1) a1 = sadacc<V>(__funnelshift_r(lo, hi, sh), cb[r], a1);
-                            else a0 = sadacc<V>(__funnelshift_r(lo, hi, sh), cb[r], a0);
-                        }
-                        sad[i] = a0 + a1;
+                for (int half = 0; half < 2; ++half) {
+                    if (half == 1 && !more) break;
+                    const int i0 = 2 * half;
+                    const int c0 = wx0 + qx[i0], c1 = wx0 + qx[i0 + 1];
+                    const uint8_t* p0 = win + (wy0 + qy[i0]) * WP + (c0 & ~3);
+                    const uint8_t* p1 = win + (wy0 + qy[i0 + 1]) * WP + (c1 & ~3);
+                    const unsigned s0 = (unsigned)(c0 & 3) * 8u, s1 = (unsigned)(c1 & 3) * 8u;
+                    uint32_t a0 = 0u, a1 = 0u;
+#pragma unroll
+                    for (int r = 0; r < RPL; ++r) {
+                        const uint32_t l0 = *reinterpret_cast<const uint32_t*>(p0 + r * WP);
+                        const uint32_t h0 = *reinterpret_cast<const uint32_t*>(p0 + r * WP + 4);
+                        const uint32_t l1 = *reinterpret_cast<const uint32_t*>(p1 + r * WP);
+                        const uint32_t h1 = *reinterpret_cast<const uint32_t*>(p1 + r * WP + 4);
+                        a0 = sadacc<V>(__funnelshift_r(l0, h0, s0), cb[r], a0);
+                        a1 = sadacc<V>(__funnelshift_r(l1, h1, s1), cb[r], a1);
                     }
+                    a0 += __shfl_xor_sync(FULL, a0, 1);
+                    a1 += __shfl_xor_sync(FULL, a1, 1);
+                    a0 += __shfl_xor_sync(FULL, a0, 2);
+                    a1 += __shfl_xor_sync(FULL, a1, 2);
+                    sad[i0] = a0;
+                    sad[i0 + 1] = a1;
                 }
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    sad[i] += __shfl_xor_sync(FULL, sad[i], 1);
-                    sad[i] += __shfl_xor_sync(FULL, sad[i], 2);
-                }
-                if (ncand) {
+
+                // ---- (4) best point of the list, then switching strategies (Sec. III-B) ----
+                if (act == 1) {
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
                         if (i < ncand) {
@@ -491,7 +486,30 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
                             }
                         }
                     }
+                    if (phase == PH_DDSP) {
+                        if (bxp == cx && byp == cy) {
+                            phase = SIMPL ? PH_SIDE : PH_MID;  // the centre won: step 4 next
+                        } else {
+                            if (abs(bxp - cx) + abs(byp - cy) == 1) pat ^= 1;  // switching strategy two
+                            cx = bxp; cy = byp;
+                        }
+                    } else if (SIMPL && phase == PH_SIDE) {
+                        // DCDS^S: the middle point on the side of the better distant point
+                        phase = PH_MID;
+                        pick = (ds0 == kInvalid && ds1 == kInvalid) ? -1
+                             : (ds0 == kInvalid) ? 1 : (ds1 == kInvalid) ? 0 : (ds1 < ds0 ? 1 : 0);
+                    } else {  // step 4 evaluated: the block is done
+                        if (l4 == 0) {
+                            out_mv[blk] = (uint32_t)(uint16_t)bxp | ((uint32_t)(uint16_t)byp << 16);
+                            out_sad[blk] = bsad;
+                            if (out_nsp) out_nsp[blk] = (uint16_t)nsp;
+                        }
+                        for (int i = wmin; i <= wmax; ++i) bm[i] = 0u;
+                        wmin = INT_MAX; wmax = -1;
+                        act = 0;
+                    }
                 }
+                __syncwarp();  // bitmap updates and clears are ordered before the next round
             }
         }
         __syncthreads();  // every read of this stage is done
@@ -509,6 +527,8 @@ cudaError_t launch_t(const FrameDev* frames, int nframes, int ntiles, int max_ra
     const size_t smem = dcds_smem_bytes(B, max_range, s);
     auto kern = dcds_kernel<B, SIMPL, NST>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     int per_sm = s.ctas_per_sm;
     if (per_sm <= 0) {
@@ -535,6 +555,8 @@ int occupancy_t(int max_range, const Shape& s)
     const size_t smem = dcds_smem_bytes(B, max_range, s);
     if (cudaFuncSetAttribute(dcds_kernel<B, SIMPL, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess ||
+        cudaFuncSetAttribute(dcds_kernel<B, SIMPL, NST>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dcds_kernel<B, SIMPL, NST>, s.threads, smem) !=
             cudaSuccess)
         return 0;

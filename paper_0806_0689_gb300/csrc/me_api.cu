@@ -20,7 +20,10 @@ using me::FrameDev;
 using me::Shape;
 
 #ifndef ME_DCDS_STAGES
-#define ME_DCDS_STAGES 1  // default tile staging of the DCDS kernel (measured: 1 stage, 4 CTAs/SM)
+#define ME_DCDS_STAGES 1     // default tile staging of the DCDS kernel
+#endif
+#ifndef ME_DCDS_THREADS
+#define ME_DCDS_THREADS 128  // default CTA size of the DCDS kernel
 #endif
 
 namespace {
@@ -119,7 +122,7 @@ Shape default_shape(me_ctx* c, int algo, int block, int range)
         s.tx = bt;
         return s;
     }
-    s.threads = 128;
+    s.threads = ME_DCDS_THREADS;
     s.tx = s.ty = me::kTile / block;
     s.k = 0;
     s.ctas_per_sm = 0;  // from the occupancy of the kernel

@@ -15,7 +15,7 @@ constexpr int kTile = 128;
 // describe the frames for the TMA unit (DCDS only): the reference window of
 // a tile (box (kTile + 2*rx) x (kTile + 2*R), rx = R rounded up to 16) and
 // the current tile (box kTile x kTile).
-struct __align__(64) FrameDev {
+struct __align__(128) FrameDev {
     CUtensorMap tm_ref;
     CUtensorMap tm_cur;
     const uint8_t* cur;
