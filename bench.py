@@ -37,7 +37,7 @@ WORKLOAD = f"1080p {W_}x{H_} luma, 16x16 blocks, range +-16, {NPAIRS} independen
 def _args():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=400)
+    p.add_argument("--steps", type=int, default=3000)
     p.add_argument("--warmup", type=int, default=10)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--pairs", type=int, default=NPAIRS)
@@ -69,7 +69,7 @@ def _oracle_worker(args):
     return n, time.perf_counter() - t0
 
 
-def cpu_baseline(seconds_hint=12.0):
+def cpu_baseline(seconds_hint=20.0):
     """Time the CPU oracle (as it stands) on a bounded sample of the same
     workload: whole 1080p pairs, DCDS + evaluation, one process per core."""
     import multiprocessing as mp
@@ -89,6 +89,29 @@ def cpu_baseline(seconds_hint=12.0):
                       f"{mbs} macroblocks in {busy:.1f} s (wall {wall:.1f} s)"}
 
 
+# ---------------------------------------------------------------- ncu traffic
+
+def _kernel_rev():
+    import hashlib
+    src = os.path.join(ROOT, "paper_0806_0689_gb300", "csrc", "dcds.cu")
+    return hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
+
+
+def _profiled_traffic(npairs):
+    """dram bytes (read + write) of one DCDS launch from the committed ncu
+    summary, scaled to this batch; None once dcds.cu has changed since the
+    counters were taken."""
+    import re
+    try:
+        txt = open(os.path.join(ROOT, "profiles", "dcds_kernel_1080p.md")).read()
+    except OSError:
+        return None
+    m = re.search(r"traffic_bytes_per_launch:\s*(\d+)\s+pairs:\s*(\d+)\s+dcds_cu_sha1:\s*([0-9a-f]+)", txt)
+    if not m or m.group(3) != _kernel_rev():
+        return None
+    return int(m.group(1)) * npairs / int(m.group(2))
+
+
 # ---------------------------------------------------------------- clocks
 
 class Clocks:
@@ -101,7 +124,7 @@ class Clocks:
         self.dev = dev
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(dev), f"--query-gpu={self.FIELDS}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "50"],
                                       stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.p = None
@@ -317,13 +340,7 @@ def main():
     fs_launch_ms = float(np.median(fs_ms))
     fs_absdiff = float(np.sum(nsp_fs.cpu().numpy().view(np.uint16).astype(np.float64))) * B_ * B_
     dcds_absdiff = nsp_mean * nb * npairs * B_ * B_
-    traffic = None
-    try:
-        prof = json.load(open(os.path.join(ROOT, "profiles", "dcds_traffic.json")))
-        if prof.get("kernel_rev") == "dcds-v1":
-            traffic = prof["bytes_per_launch_1080p_%dpairs" % npairs]
-    except Exception:
-        pass
+    traffic = _profiled_traffic(npairs)
 
     line = {
         "metric": "DCDS macroblocks/s at 1080p on 1 GB300; search pts/MB and PSNR vs FS & plain",
