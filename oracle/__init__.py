@@ -76,6 +76,19 @@ def _load():
             lib.oracle_eval_frame.argtypes = [P, P, I, I, I, I, P, P, P, P]
             lib.oracle_hcsp_offsets.restype = None
             lib.oracle_hcsp_offsets.argtypes = [P]
+            lib.oracle_search_from.restype = I
+            lib.oracle_search_from.argtypes = [BDM_FN, P, I, I, I, I, I, I, I, I, I, P]
+            lib.oracle_dcds_block_from.restype = I
+            lib.oracle_dcds_block_from.argtypes = [P, P, I, I, I, I, I, I, I, I, I, I, P]
+            lib.oracle_dcds_from_starts.restype = I
+            lib.oracle_dcds_from_starts.argtypes = [P, P, I, I, I, I, I, P, P, P, P]
+            lib.oracle_cnn_nparams.restype = I
+            lib.oracle_cnn_features.restype = None
+            lib.oracle_cnn_features.argtypes = [P, P, I, I, I, I, I, P, P, P]
+            lib.oracle_cnn_forward.restype = None
+            lib.oracle_cnn_forward.argtypes = [P, P, P, P]
+            lib.oracle_cnn_loss_grad.restype = ctypes.c_double
+            lib.oracle_cnn_loss_grad.argtypes = [P, P, P, I, I, I, P]
             _lib = lib
     return _lib
 
@@ -176,6 +189,125 @@ def search(bdm, rng, dx_lim=(-10**6, 10**6), dy_lim=(-10**6, 10**6), simplified=
     if rc:
         raise MemoryError("oracle_search failed")
     return int(out[0]), int(out[1]), int(out[2]), int(out[3])
+
+
+def search_from(bdm, rng, start=(0, 0), prior_v=False, dx_lim=(-10**6, 10**6), dy_lim=(-10**6, 10**6),
+                simplified=False):
+    """DCDS from a proposed start: the better of the origin and ``start`` (the
+    origin on a tie) centres the first pattern, the HCSP or (prior_v) its
+    transpose; then DCDS steps 2-4.  Returns (mvx, mvy, bdm_at_mv, nsp)."""
+    cb = BDM_FN(lambda _u, dx, dy: int(bdm(dx, dy)))
+    out = (ctypes.c_int64 * 4)()
+    rc = _load().oracle_search_from(cb, None, rng, dx_lim[0], dx_lim[1], dy_lim[0], dy_lim[1], int(start[0]),
+                                    int(start[1]), int(bool(prior_v)), int(bool(simplified)),
+                                    ctypes.cast(out, ctypes.c_void_p))
+    if rc:
+        raise MemoryError("oracle_search_from failed")
+    return int(out[0]), int(out[1]), int(out[2]), int(out[3])
+
+
+def dcds_from_starts(cur, ref, block, rng, starts):
+    """DCDS of every block from per-block (sx, sy, prior_v) starts (int16 [nb, 3])."""
+    cur, ref = _frames(cur, ref)
+    h, w = cur.shape
+    nb = (w // block) * (h // block)
+    starts = np.ascontiguousarray(starts, dtype=np.int16).reshape(nb, 3)
+    mv = np.zeros((nb, 2), np.int16)
+    sd = np.zeros(nb, np.uint32)
+    ns = np.zeros(nb, np.uint16)
+    rc = _load().oracle_dcds_from_starts(_ptr(cur), _ptr(ref), w, h, w, block, rng, _ptr(starts), _ptr(mv),
+                                         _ptr(sd), _ptr(ns))
+    if rc:
+        raise ValueError("oracle_dcds_from_starts rejected its arguments")
+    return mv, sd, ns
+
+
+# ---------------------------------------------------------------- learned proposal
+
+def cnn_nparams():
+    return int(_load().oracle_cnn_nparams())
+
+
+def cnn_features(cur, ref, px, py, nbr=None):
+    """(x [2, 32, 32] float64, mvf [6] float64) of the 16x16 block at (px, py)."""
+    cur, ref = _frames(cur, ref)
+    h, w = cur.shape
+    x = np.zeros((2, 32, 32), np.float64)
+    mvf = np.zeros(6, np.float64)
+    nbr = None if nbr is None else np.ascontiguousarray(nbr, dtype=np.int16)
+    _load().oracle_cnn_features(_ptr(cur), _ptr(ref), w, h, w, px, py, _ptr(nbr), _ptr(x), _ptr(mvf))
+    return x, mvf
+
+
+def cnn_forward(params, x, mvf):
+    params = np.ascontiguousarray(params, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    mvf = np.ascontiguousarray(mvf, dtype=np.float64)
+    out = np.zeros(68, np.float64)
+    _load().oracle_cnn_forward(_ptr(params), _ptr(x), _ptr(mvf), _ptr(out))
+    return out
+
+
+def cnn_loss_grad(params, x, mvf, labels, grad=None):
+    """Loss of one block and its gradient (added into ``grad`` if given)."""
+    params = np.ascontiguousarray(params, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    mvf = np.ascontiguousarray(mvf, dtype=np.float64)
+    if grad is None:
+        grad = np.zeros_like(params)
+    loss = _load().oracle_cnn_loss_grad(_ptr(params), _ptr(x), _ptr(mvf), int(labels[0]), int(labels[1]),
+                                        int(labels[2]), _ptr(grad))
+    return float(loss), grad
+
+
+def cnn_start(logits, px, py, w, h, rng, block=16):
+    """Start point and direction prior chosen from logits: the argmax of the dx
+    and dy heads (ties go to the class nearest the centre, checked in the order
+    0, -1, +1, -2, +2, ...), clamped to the window and the frame; vertical
+    prior when the V logit is strictly larger."""
+    def centre_out_argmax(z):
+        best, bv = 0, z[16]
+        for a in range(1, 17):
+            for d in (-a, a):
+                if z[d + 16] > bv:
+                    best, bv = d, z[d + 16]
+        return best
+    sx = centre_out_argmax(logits[:33])
+    sy = centre_out_argmax(logits[33:66])
+    sx = max(max(-rng, -px), min(min(rng, w - block - px), sx))
+    sy = max(max(-rng, -py), min(min(rng, h - block - py), sy))
+    return sx, sy, int(logits[67] > logits[66])
+
+
+def learned_dcds(cur, ref, rng, params):
+    """Learned-start DCDS of a frame, 16x16 blocks, blocks in raster order (the
+    left, top and top-right neighbours are final before a block starts).
+    Returns (mv, sad, nsp, starts, logits)."""
+    cur, ref = _frames(cur, ref)
+    h, w = cur.shape
+    nbx, nby = w // 16, h // 16
+    nb = nbx * nby
+    mv = np.zeros((nb, 2), np.int16)
+    sd = np.zeros(nb, np.uint32)
+    ns = np.zeros(nb, np.uint16)
+    starts = np.zeros((nb, 3), np.int16)
+    logits = np.zeros((nb, 68), np.float64)
+    out = (ctypes.c_int64 * 4)()
+    L = _load()
+    for k in range(nb):
+        px, py = (k % nbx) * 16, (k // nbx) * 16
+        x, mvf = cnn_features(cur, ref, px, py, mv)
+        lg = cnn_forward(params, x, mvf)
+        logits[k] = lg
+        starts[k] = cnn_start(lg, px, py, w, h, rng)
+        rc = L.oracle_dcds_block_from(_ptr(cur), _ptr(ref), w, h, w, 16, rng, px, py, int(starts[k][0]),
+                                      int(starts[k][1]), int(starts[k][2]), ctypes.cast(out, ctypes.c_void_p))
+        if rc:
+            raise MemoryError("oracle_dcds_block_from failed")
+        mv[k] = (out[0], out[1])
+        sd[k] = out[2]
+        ns[k] = out[3]
+    return mv, sd, ns, starts, logits
 
 
 def evaluate(cur, ref, block, mv, mv_fs=None, nsp=None):

@@ -199,9 +199,17 @@ static int best_of(search_t* s, int cx, int cy, const int (*off)[2], int n,
     return best;
 }
 
+/* VCSP: the HCSP transposed (a project extension used only by the learned
+ * start when its direction prior says vertical; not in the paper). */
+static const int VCSP_[7][2] = {{0, 0}, {0, -1}, {0, 1}, {-1, 0}, {1, 0}, {0, -2}, {0, 2}};
+
 /*
  * One DCDS search over the window of `range` (Sec. III-B, steps 1-4 and the
- * two switching strategies).  `simplified` selects DCDS^S (Sec. IV-C): the
+ * two switching strategies), started from a proposal: the origin and the
+ * start point (sx, sy) are evaluated and the better one (the origin on a
+ * tie) becomes the centre of the first pattern, which is the HCSP, or its
+ * transpose when prior_v is set.  With start (0,0) and prior_v = 0 this is
+ * exactly the paper's DCDS.  `simplified` selects DCDS^S (Sec. IV-C): the
  * last step checks only the middle point on the side of the better distant
  * point.  Returns the motion vector, its BDM and the NSP in out[0..3]
  * (out[2] is the BDM truncated to 64 bits, out[3] the NSP).
@@ -212,9 +220,9 @@ static int best_of(search_t* s, int cx, int cy, const int (*off)[2], int n,
  * negative side is chosen; when both are outside, both middle points are
  * checked as in DCDS.
  */
-int oracle_search(oracle_bdm_fn bdm, void* user, int range,
-                  int dx_min, int dx_max, int dy_min, int dy_max,
-                  int simplified, int64_t* out)
+int oracle_search_from(oracle_bdm_fn bdm, void* user, int range,
+                       int dx_min, int dx_max, int dy_min, int dy_max,
+                       int sx, int sy, int prior_v, int simplified, int64_t* out)
 {
     search_t s;
     s.range = range;
@@ -226,17 +234,23 @@ int oracle_search(oracle_bdm_fn bdm, void* user, int range,
     s.nsp = 0;
     if (!s.value || !s.seen) { free(s.value); free(s.seen); return 1; }
 
-    /* Step 1: HCSP at the origin of the window. */
-    int64_t cval;
+    /* Centre of the first pattern: the origin, or the proposed start when it
+     * is strictly better. */
+    int64_t cval, sval;
     eval_point(&s, 0, 0, &cval);            /* the origin is always a candidate */
     int cx = 0, cy = 0, bx, by;
+    if ((sx != 0 || sy != 0) && eval_point(&s, sx, sy, &sval) && sval < cval) {
+        cx = sx; cy = sy; cval = sval;
+    }
+    /* Step 1: HCSP (or VCSP) at that centre. */
     int64_t bval;
-    int k = best_of(&s, 0, 0, (const int (*)[2])&HCSP_[1], 6, cval, &bx, &by, &bval);
-    int mx = 0, my = 0;
+    const int (*first)[2] = prior_v ? VCSP_ : HCSP_;
+    int k = best_of(&s, cx, cy, &first[1], 6, cval, &bx, &by, &bval);
+    int mx = cx, my = cy;
     int64_t mval = cval;
     if (k != 0) {
         /* Switching strategy one: a horizontal BMP selects HDSP, else VDSP. */
-        int pat = (by == 0) ? PAT_H : PAT_V;
+        int pat = (by == cy) ? PAT_H : PAT_V;
         cx = bx; cy = by; cval = bval;
         /* Steps 2 and 3: re-centre the directional diamond on the BMP until
          * the centre wins.  Each move strictly lowers the BDM, so this ends. */
@@ -267,6 +281,14 @@ int oracle_search(oracle_bdm_fn bdm, void* user, int range,
     out[0] = mx; out[1] = my; out[2] = mval; out[3] = s.nsp;
     free(s.value); free(s.seen);
     return 0;
+}
+
+/* The paper's DCDS: the search above from the origin with the HCSP. */
+int oracle_search(oracle_bdm_fn bdm, void* user, int range,
+                  int dx_min, int dx_max, int dy_min, int dy_max,
+                  int simplified, int64_t* out)
+{
+    return oracle_search_from(bdm, user, range, dx_min, dx_max, dy_min, dy_max, 0, 0, 0, simplified, out);
 }
 
 typedef struct {
@@ -322,6 +344,50 @@ int oracle_dcds_blocks(const uint8_t* cur, const uint8_t* ref, int w, int h, int
         if (dcds_one(cur, ref, w, h, pitch, block, range, simplified, (idx[t] % nbx) * block,
                      (idx[t] / nbx) * block, mv + 2 * (long)t, sad + t, nsp ? nsp + t : NULL)) return 1;
     }
+    return 0;
+}
+
+/* DCDS of the block at pixel (bx, by) from the start (sx, sy, prior_v),
+ * the start clamped to the window and the frame.  out = mv x, mv y, SAD, NSP. */
+int oracle_dcds_block_from(const uint8_t* cur, const uint8_t* ref, int w, int h, int pitch, int block,
+                           int range, int bx, int by, int sx, int sy, int prior_v, int64_t* out)
+{
+    int lo_x = -bx > -range ? -bx : -range, hi_x = w - block - bx < range ? w - block - bx : range;
+    int lo_y = -by > -range ? -by : -range, hi_y = h - block - by < range ? h - block - by : range;
+    sx = sx < lo_x ? lo_x : (sx > hi_x ? hi_x : sx);
+    sy = sy < lo_y ? lo_y : (sy > hi_y ? hi_y : sy);
+    sad_user_t u = {cur, ref, pitch, bx, by, block};
+    return oracle_search_from(sad_cb, &u, range, -bx, w - block - bx, -by, h - block - by, sx, sy,
+                              prior_v != 0, 0, out);
+}
+
+/* DCDS of every block of a frame from per-block starts: starts[3k..3k+2] =
+ * (sx, sy, prior_v) (16x16 or 8x8 blocks; the start is clamped to the
+ * window and the frame). */
+int oracle_dcds_from_starts(const uint8_t* cur, const uint8_t* ref, int w, int h, int pitch,
+                            int block, int range, const int16_t* starts,
+                            int16_t* mv, uint32_t* sad, uint16_t* nsp)
+{
+    if (block <= 0 || w % block || h % block || range < 0) return 1;
+    int nbx = w / block, nby = h / block;
+    for (int j = 0; j < nby; ++j)
+        for (int i = 0; i < nbx; ++i) {
+            long k = (long)j * nbx + i;
+            int bx = i * block, by = j * block;
+            int lo_x = -bx > -range ? -bx : -range, hi_x = w - block - bx < range ? w - block - bx : range;
+            int lo_y = -by > -range ? -by : -range, hi_y = h - block - by < range ? h - block - by : range;
+            int sx = starts[3 * k], sy = starts[3 * k + 1];
+            sx = sx < lo_x ? lo_x : (sx > hi_x ? hi_x : sx);
+            sy = sy < lo_y ? lo_y : (sy > hi_y ? hi_y : sy);
+            sad_user_t u = {cur, ref, pitch, bx, by, block};
+            int64_t out[4];
+            if (oracle_search_from(sad_cb, &u, range, -bx, w - block - bx, -by, h - block - by,
+                                   sx, sy, starts[3 * k + 2] != 0, 0, out)) return 1;
+            mv[2 * k] = (int16_t)out[0];
+            mv[2 * k + 1] = (int16_t)out[1];
+            sad[k] = (uint32_t)out[2];
+            if (nsp) nsp[k] = (uint16_t)out[3];
+        }
     return 0;
 }
 
