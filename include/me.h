@@ -156,6 +156,59 @@ int me_graph_launch(me_ctx* ctx, me_graph* g, void* stream);
 void me_graph_free(me_graph* g);
 
 /* ---------------------------------------------------------------------- */
+/* Learned start proposal.  Not in the paper: the task adds a small CNN that  */
+/* proposes a start point and a horizontal/vertical prior for DCDS, in the    */
+/* spirit of the paper's directional conditional MVP model (Sec. II-C-2,      */
+/* Sec. II-D).  16x16 blocks only.                                            */
+/*   features: the current block centred in a zero 32x32 canvas and the      */
+/*   co-located 32x32 reference patch (clamped), both (p - 128) / 128, plus   */
+/*   the final MVs of the left, top and top-right blocks divided by 16;       */
+/*   network: 4 conv 3x3 stride 2 (32 channels, ReLU) then a linear head to  */
+/*   68 logits (dx in [-16,16], dy in [-16,16], H/V).  Convolutions run on    */
+/*   the BF16 tensor cores with FP32 accumulation.                            */
+/*   parameters (host float, this order): conv1.w [32][2][3][3], conv1.b      */
+/*   [32], conv2.w [32][32][3][3], conv2.b, conv3.w, conv3.b, conv4.w,        */
+/*   conv4.b, fc.w [68][134], fc.b [68]; fc inputs are the 128 conv-4         */
+/*   outputs in (channel, y, x) order, then the 6 neighbour scalars.          */
+/* ---------------------------------------------------------------------- */
+typedef struct me_proposal me_proposal;
+enum { ME_PROPOSAL_NPARAMS = 37532, ME_PROPOSAL_NLOGITS = 68 };
+
+/* Create (all parameters zero: the proposal is then the origin with a
+ * horizontal prior, which makes the learned search equal to DCDS) / free. */
+int me_proposal_create(me_ctx* ctx, me_proposal** out);
+void me_proposal_free(me_proposal* p);
+/* Copy ME_PROPOSAL_NPARAMS floats in / out (HOST arrays).  Setting the
+ * parameters resets the optimiser state.  Both synchronise the device. */
+int me_proposal_set_params(me_ctx* ctx, me_proposal* p, const float* params);
+int me_proposal_get_params(me_ctx* ctx, me_proposal* p, float* params);
+/* One training step over every 16x16 block of the n pairs: descs[i].mv (a
+ * DEVICE motion field, e.g. the full-search field) gives the labels (dx, dy
+ * clamped to +-16; H when |dx| >= |dy|) and the neighbour scalars.  The loss
+ * is the mean over blocks of three softmax cross-entropies.  lr > 0 applies
+ * one Adam step (beta 0.9 / 0.999); lr = 0 only computes.  *loss receives the
+ * mean loss, grad (HOST, nullable) the gradient in parameter order.  At most
+ * 65536 blocks per step.  Synchronises `stream`. */
+int me_proposal_train_step(me_ctx* ctx, me_proposal* p, const me_frame_desc* descs, int n, float lr,
+                           float* loss, float* grad, void* stream);
+/* Logits of every block of one pair (DEVICE float [nb][68]), the neighbour
+ * scalars taken from desc->mv (a DEVICE motion field). */
+int me_proposal_logits(me_ctx* ctx, me_proposal* p, const me_frame_desc* desc, float* logits, void* stream);
+/* Learned-start DCDS over n pairs: blocks run in wavefront order so that the
+ * left, top and top-right blocks are final first; the head turns their MVs
+ * and the block's conv features into a start (argmax of the dx and dy heads,
+ * ties to the class nearest 0, clamped to window and frame) and a prior (V
+ * when its logit is larger).  The origin and the start are evaluated, the
+ * better one (the origin on a tie) centres the first pattern (HCSP, or its
+ * transpose for a V prior), then DCDS steps 2-4 follow.  NSP counts every
+ * distinct point.  Outputs go to descs[i].mv / sad / nsp; starts (DEVICE
+ * int16 [total blocks][3] = sx, sy, prior; nullable) records the proposals.
+ * Waits between blocks are bounded (ME_ERR_TIMEOUT via me_check_status).
+ * Synchronises `stream`. */
+int me_estimate_learned_batch(me_ctx* ctx, me_proposal* p, const me_frame_desc* descs, int n,
+                              int16_t* starts, void* stream);
+
+/* ---------------------------------------------------------------------- */
 /* Evaluation: the six measures of Sec. IV (MAD, MSE, NSP, PSNR, distance  */
 /* to the FS motion vector, probability of finding it).                    */
 /* The device computes exact integer sums; me_stats_from_sums turns them   */

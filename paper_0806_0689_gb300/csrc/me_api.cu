@@ -3,6 +3,7 @@
 // shape tuner and the byte-absdiff microbenchmark.  All arithmetic of the
 // motion search runs in the kernels of dcds.cu, fs.cu and eval.cu.
 #include "me.h"
+#include "me_ctx.h"
 #include "me_internal.cuh"
 
 #include <algorithm>
@@ -18,6 +19,8 @@
 using me::EvalDev;
 using me::FrameDev;
 using me::Shape;
+using me::Slot;
+using me::kHeadBytes;
 
 #ifndef ME_DCDS_STAGES
 #define ME_DCDS_STAGES 1     // default tile staging of the DCDS kernel
@@ -25,41 +28,6 @@ using me::Shape;
 #ifndef ME_DCDS_THREADS
 #define ME_DCDS_THREADS 128  // default CTA size of the DCDS kernel
 #endif
-
-namespace {
-
-// One reusable upload slot: a device buffer [queue head | descriptor table],
-// its pinned host twin and an event marking the last launch that used it.
-struct Slot {
-    void* dev = nullptr;
-    void* host = nullptr;
-    size_t cap = 0;
-    cudaEvent_t done = nullptr;
-    bool used = false;
-};
-
-constexpr size_t kHeadBytes = 256;  // queue head (int) and padding before the table
-
-}  // namespace
-
-struct me_ctx {
-    int device = 0;
-    int num_sms = 0;
-    std::string err;
-    std::string tune_path;
-    std::map<std::string, Shape> tuned;
-    Slot slots[ME_MAX_INFLIGHT];
-    int next_slot = 0;
-    unsigned* status = nullptr;  // device word written by kernels
-    unsigned* sink = nullptr;    // microbenchmark sink
-};
-
-struct me_graph {
-    me_ctx* ctx = nullptr;
-    void* dev = nullptr;  // [head | table]
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-};
 
 namespace {
 

@@ -1,0 +1,63 @@
+// me_cnn.cuh -- the learned start proposal: sizes, parameter layout and the
+// host launchers of cnn.cu.  (Not in the paper; added by the task.)
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace me {
+namespace cnn {
+
+constexpr int NLOGIT = 68;   // 33 dx + 33 dy + 2 H/V
+constexpr int NFEAT = 134;   // 128 conv-4 outputs + 6 neighbour scalars
+constexpr int CH = 32;       // channels of every conv layer
+// canonical parameter offsets
+constexpr int P_W1 = 0, P_B1 = P_W1 + CH * 2 * 9;
+constexpr int P_W2 = P_B1 + CH, P_B2 = P_W2 + CH * CH * 9;
+constexpr int P_W3 = P_B2 + CH, P_B3 = P_W3 + CH * CH * 9;
+constexpr int P_W4 = P_B3 + CH, P_B4 = P_W4 + CH * CH * 9;
+constexpr int P_FW = P_B4 + CH, P_FB = P_FW + NLOGIT * NFEAT;
+constexpr int NPARAMS = P_FB + NLOGIT;  // 37532
+// per layer: input side and channels, GEMM K (padded)
+constexpr int LAYERS = 4;
+constexpr int HIN[LAYERS] = {32, 16, 8, 4};
+constexpr int CIN[LAYERS] = {2, CH, CH, CH};
+constexpr int KP[LAYERS] = {32, 288, 288, 288};
+constexpr int PW[LAYERS] = {P_W1, P_W2, P_W3, P_W4};
+constexpr int PB[LAYERS] = {P_B1, P_B2, P_B3, P_B4};
+
+enum { GEMM_STORE = 0, GEMM_ATOMIC = 1, GEMM_BIAS_RELU = 2 };
+
+cudaError_t gemm(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, float* C, int ldc, int M,
+                 int N, int K, int splits, int mode, const float* bias, __nv_bfloat16* out_bf16, cudaStream_t st);
+cudaError_t im2col(const __nv_bfloat16* in, int n, int hin, int cin, int kp, __nv_bfloat16* cols, cudaStream_t st);
+cudaError_t col2im(const float* dcols, int n, int hin, int cin, int kp, float* din, cudaStream_t st);
+cudaError_t transpose(const __nv_bfloat16* in, int rows, int ncols, int ld_in, __nv_bfloat16* out, int rows_pad,
+                      cudaStream_t st);
+cudaError_t relu_back(const float* da, const __nv_bfloat16* a, long rows, __nv_bfloat16* dz, float* dbias,
+                      cudaStream_t st);
+cudaError_t head_fwd(const __nv_bfloat16* a4, const float* mvf, int n, const float* fw, const float* fb,
+                     float* logits, cudaStream_t st);
+cudaError_t loss(const float* logits, const int* labels, int n, float scale, float* dlogits, double* loss_sum,
+                 cudaStream_t st);
+cudaError_t head_bwd(const float* dlogits, const __nv_bfloat16* a4, const float* mvf, int n, const float* fw,
+                     float* gfw, float* gfb, float* da4, cudaStream_t st);
+cudaError_t pack_weights(const float* p, int cin, int kp, __nv_bfloat16* w, cudaStream_t st);
+cudaError_t unpack_wgrad(const float* gw, int cin, int kp, float* g, cudaStream_t st);
+cudaError_t adam(float* p, const float* g, float* m, float* v, int n, float lr, int step, cudaStream_t st);
+
+// One frame pair as the proposal kernels see it (16x16 blocks).
+struct PropFrame {
+    const uint8_t* cur;
+    const uint8_t* ref;
+    const int16_t* nbr;  // motion field for the neighbour scalars (and labels in training)
+    int16_t* mv;         // outputs of the learned search
+    uint32_t* sad;
+    uint16_t* nsp;
+    int32_t w, h, pitch, range, nbx, nby, base;  // base: index of the frame's first block
+    int32_t pad_;
+};
+
+}  // namespace cnn
+}  // namespace me

@@ -1,0 +1,668 @@
+// proposal.cu -- the learned start proposal for DCDS (not in the paper; the
+// task adds it): features, training step, inference and the learned-start
+// search.
+//
+// Features of a 16x16 block at (px, py): the current block centred in a zero
+// 32x32 canvas, the 32x32 reference patch at the same origin (coordinates
+// clamped to the frame), both as (p - 128) / 128; and the final MVs of the
+// left, top and top-right blocks divided by 16 (zero where absent).
+//
+// Training labels come from a motion field (the full-search field computed
+// by this library): dx, dy clamped to +-16 (classes 0..32) and H/V = 0 when
+// |mvx| >= |mvy|, else 1.  The neighbour scalars use the same field.
+//
+// Learned-start search: blocks are processed in wavefront order (t = bx + 2 by)
+// so that the left, top and top-right blocks are final first.  Per block, one
+// warp waits for those three (acquire loads, bounded), runs the head on the
+// precomputed conv-4 features and the neighbours' MVs, picks the start (argmax
+// of the dx and dy heads, ties to the class nearest the centre) and the prior
+// (V when its logit is larger), and searches: the origin and the start are
+// evaluated, the better one (the origin on a tie) centres the first pattern
+// (the HCSP, or its transpose for a vertical prior), then DCDS steps 2-4.
+#include "me.h"
+#include "me_cnn.cuh"
+#include "me_ctx.h"
+
+#include <algorithm>
+#include <climits>
+#include <cstring>
+#include <vector>
+
+using namespace me::cnn;
+
+struct me_proposal {
+    me_ctx* ctx = nullptr;
+    float* p = nullptr;  // canonical parameters (device)
+    float* g = nullptr;  // gradient
+    float* m = nullptr;  // Adam moments
+    float* v = nullptr;
+    __nv_bfloat16* w[LAYERS] = {nullptr, nullptr, nullptr, nullptr};  // GEMM-layout weights
+    int step = 0;
+    uint8_t* ws = nullptr;  // workspace
+    size_t ws_cap = 0;
+    PropFrame* frames = nullptr;  // device frame table
+    int frames_cap = 0;
+    int* order = nullptr;  // wavefront order
+    long order_cap = 0;
+};
+
+namespace {
+
+constexpr int kChunk = 2048;  // samples per trunk pass at inference
+
+int fail(me_ctx* c, int code, const std::string& msg)
+{
+    if (c) c->err = msg;
+    return code;
+}
+
+int cuda_fail(me_ctx* c, cudaError_t e, const char* what)
+{
+    return fail(c, ME_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// ------------------------------------------------------------------ device helpers
+__device__ __forceinline__ int find_frame(const PropFrame* fr, int nframes, long gid)
+{
+    int lo = 0, hi = nframes - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (fr[mid].base <= gid) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// features of samples [s0, s0 + n): x NHWC [n][32][32][2] bf16, mvf [n][6], labels [n][3]
+__global__ void feat_kernel(const PropFrame* __restrict__ fr, int nframes, long s0, int n,
+                            __nv_bfloat16* __restrict__ x, float* __restrict__ mvf, int* __restrict__ labels)
+{
+    const long total = (long)n * 1024;
+    for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+        const long s = idx >> 10;
+        const int pix = (int)(idx & 1023), i = pix >> 5, j = pix & 31;
+        const long gid = s0 + s;
+        const PropFrame& F = fr[find_frame(fr, nframes, gid)];
+        const int k = (int)(gid - F.base);
+        const int bx = k % F.nbx, by = k / F.nbx;
+        const int px = bx * 16, py = by * 16;
+        float v0 = 0.f;
+        if (i >= 8 && i < 24 && j >= 8 && j < 24)
+            v0 = ((float)F.cur[(size_t)(py + i - 8) * F.pitch + (px + j - 8)] - 128.f) * (1.f / 128.f);
+        const int yy = min(max(py + i - 8, 0), F.h - 1), xx = min(max(px + j - 8, 0), F.w - 1);
+        const float v1 = ((float)F.ref[(size_t)yy * F.pitch + xx] - 128.f) * (1.f / 128.f);
+        x[idx * 2] = __float2bfloat16_rn(v0);
+        x[idx * 2 + 1] = __float2bfloat16_rn(v1);
+        if (pix == 0) {
+            const int nbdx[3] = {-1, 0, 1}, nbdy[3] = {0, -1, -1};
+            for (int q = 0; q < 3; ++q) {
+                const int ax = bx + nbdx[q], ay = by + nbdy[q];
+                float vx = 0.f, vy = 0.f;
+                if (F.nbr && ax >= 0 && ax < F.nbx && ay >= 0) {
+                    const int m = ay * F.nbx + ax;
+                    vx = F.nbr[2 * m] * (1.f / 16.f);
+                    vy = F.nbr[2 * m + 1] * (1.f / 16.f);
+                }
+                mvf[s * 6 + 2 * q] = vx;
+                mvf[s * 6 + 2 * q + 1] = vy;
+            }
+            if (labels) {
+                int mx = 0, my = 0;
+                if (F.nbr) { mx = F.nbr[2 * k]; my = F.nbr[2 * k + 1]; }
+                labels[s * 3] = min(max(mx, -16), 16) + 16;
+                labels[s * 3 + 1] = min(max(my, -16), 16) + 16;
+                labels[s * 3 + 2] = (abs(mx) >= abs(my)) ? 0 : 1;
+            }
+        }
+    }
+}
+
+__global__ void copy_rows_kernel(const __nv_bfloat16* __restrict__ src, long n, __nv_bfloat16* __restrict__ dst)
+{
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
+
+// ------------------------------------------------------------------ learned-start search
+__device__ __forceinline__ int ld_acquire(const int* p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(int* p, int v)
+{
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+constexpr uint32_t kSpinLimit = 1u << 22;
+
+struct WarpBlock {
+    const uint8_t* ref;
+    int pitch, px, py, dxlo, dxhi, dylo, dyhi, R;
+    uint32_t c0, c1;  // this lane's 8 current pixels (row lane/2, half lane%2)
+};
+
+// SAD of the block at displacement (qx, qy): every lane returns the total
+__device__ __forceinline__ uint32_t warp_sad(const WarpBlock& b, int qx, int qy, int lane)
+{
+    const int r = lane >> 1, hh = lane & 1;
+    const long g = (long)(b.py + qy + r) * b.pitch + b.px + qx + 8 * hh;
+    const uint32_t* wp = reinterpret_cast<const uint32_t*>(b.ref + (g & ~3l));
+    const unsigned sh = (unsigned)(g & 3) * 8u;
+    const uint32_t w0 = __ldg(wp), w1 = __ldg(wp + 1);
+    const uint32_t w2 = sh ? __ldg(wp + 2) : 0u;  // inside the row whenever the segment is unaligned
+    uint32_t s = me::sadacc<me::kSadVariant>(__funnelshift_r(w0, w1, sh), b.c0, 0u);
+    s = me::sadacc<me::kSadVariant>(__funnelshift_r(w1, w2, sh), b.c1, s);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
+// Visit (qx, qy): false if outside the window/frame or visited before;
+// otherwise marks it, counts it and returns its SAD in *v.
+__device__ __forceinline__ bool visit(const WarpBlock& b, uint32_t* bm, int& wmin, int& wmax, int& nsp, int qx,
+                                      int qy, uint32_t* v, int lane)
+{
+    if (qx < b.dxlo || qx > b.dxhi || qy < b.dylo || qy > b.dyhi) return false;
+    const int bit = (qy + b.R) * (2 * b.R + 1) + (qx + b.R);
+    int seen = 0;
+    if (lane == 0) {
+        const uint32_t w = bm[bit >> 5], m = 1u << (bit & 31);
+        seen = (w & m) != 0u;
+        if (!seen) {
+            bm[bit >> 5] = w | m;
+            wmin = min(wmin, bit >> 5);
+            wmax = max(wmax, bit >> 5);
+        }
+    }
+    seen = __shfl_sync(0xffffffffu, seen, 0);
+    if (seen) return false;
+    ++nsp;
+    *v = warp_sad(b, qx, qy, lane);
+    return true;
+}
+
+__constant__ int8_t kFirstH[6][2] = {{-1, 0}, {1, 0}, {0, -1}, {0, 1}, {-2, 0}, {2, 0}};  // HCSP
+__constant__ int8_t kFirstV[6][2] = {{0, -1}, {0, 1}, {-1, 0}, {1, 0}, {0, -2}, {0, 2}};  // its transpose
+__constant__ int8_t kDd[2][4][2] = {{{0, -1}, {0, 1}, {-2, 0}, {2, 0}}, {{-1, 0}, {1, 0}, {0, -2}, {0, 2}}};
+__constant__ int8_t kMid[2][2][2] = {{{-1, 0}, {1, 0}}, {{0, -1}, {0, 1}}};
+
+__global__ void __launch_bounds__(256) learned_dcds_kernel(const PropFrame* __restrict__ fr, int nframes,
+                                                           const int* __restrict__ order, int total,
+                                                           const __nv_bfloat16* __restrict__ a4,
+                                                           const float* __restrict__ fw, const float* __restrict__ fb,
+                                                           int* __restrict__ done, int* __restrict__ counter,
+                                                           int16_t* __restrict__ starts, unsigned* __restrict__ status,
+                                                           int max_range)
+{
+    extern __shared__ uint32_t bm_all[];
+    __shared__ float s_logit[8][NLOGIT];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int side_max = 2 * max_range + 1;
+    const int nwb = (side_max * side_max + 31) / 32;
+    uint32_t* bm = bm_all + warp * nwb;
+    for (int i = lane; i < nwb; i += 32) bm[i] = 0u;
+    __syncwarp();
+    int wmin = INT_MAX, wmax = -1;
+    for (;;) {
+        int idx = 0;
+        if (lane == 0) idx = atomicAdd(counter, 1);
+        idx = __shfl_sync(0xffffffffu, idx, 0);
+        if (idx >= total) break;
+        const int gid = order[idx];
+        const PropFrame& F = fr[find_frame(fr, nframes, gid)];
+        const int k = gid - F.base;
+        const int bx = k % F.nbx, by = k / F.nbx;
+        // ---- wait until the causal neighbours are final ----
+        const int nbdx[3] = {-1, 0, 1}, nbdy[3] = {0, -1, -1};
+        float mvx = 0.f, mvy = 0.f;
+        bool late = false;
+        if (lane < 3) {
+            const int ax = bx + nbdx[lane], ay = by + nbdy[lane];
+            if (ax >= 0 && ax < F.nbx && ay >= 0) {
+                const int nk = ay * F.nbx + ax;
+                uint32_t it = 0;
+                while (ld_acquire(done + F.base + nk) == 0) {
+                    if (++it > kSpinLimit) { late = true; break; }
+                    __nanosleep(64);
+                }
+                if (!late) {
+                    const uint32_t m = __ldcg(reinterpret_cast<const uint32_t*>(F.mv) + nk);
+                    mvx = (float)(int16_t)(m & 0xffffu) * (1.f / 16.f);
+                    mvy = (float)(int16_t)(m >> 16) * (1.f / 16.f);
+                }
+            }
+        }
+        if (__any_sync(0xffffffffu, late) && lane == 0 && status) atomicOr(status, me::STATUS_TIMEOUT);
+        float mvf[6];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            mvf[2 * q] = __shfl_sync(0xffffffffu, mvx, q);
+            mvf[2 * q + 1] = __shfl_sync(0xffffffffu, mvy, q);
+        }
+        // ---- head: logits from the conv-4 features and the neighbours ----
+        const __nv_bfloat16* af = a4 + (size_t)gid * 128;
+        for (int o = lane; o < NLOGIT; o += 32) {
+            const float* wr = fw + (size_t)o * NFEAT;
+            float acc = fb[o];
+            for (int f = 0; f < 128; ++f) acc += wr[f] * __bfloat162float(af[(f & 3) * 32 + (f >> 2)]);
+#pragma unroll
+            for (int q = 0; q < 6; ++q) acc += wr[128 + q] * mvf[q];
+            s_logit[warp][o] = acc;
+        }
+        __syncwarp();
+        const int R = F.range, px = bx * 16, py = by * 16;
+        WarpBlock b;
+        b.ref = F.ref; b.pitch = F.pitch; b.px = px; b.py = py; b.R = R;
+        b.dxlo = max(-R, -px); b.dxhi = min(R, F.w - 16 - px);
+        b.dylo = max(-R, -py); b.dyhi = min(R, F.h - 16 - py);
+        {
+            const uint32_t* cp = reinterpret_cast<const uint32_t*>(F.cur + (size_t)(py + (lane >> 1)) * F.pitch + px +
+                                                                   8 * (lane & 1));
+            b.c0 = __ldg(cp);
+            b.c1 = __ldg(cp + 1);
+        }
+        int sx = 0, sy = 0, pv = 0;
+        {
+            // argmax with ties to the class nearest the centre: 0, -1, +1, -2, +2, ...
+            const float* z = s_logit[warp];
+            float bvx = z[16], bvy = z[33 + 16];
+            for (int a = 1; a <= 16; ++a) {
+                if (z[16 - a] > bvx) { bvx = z[16 - a]; sx = -a; }
+                if (z[16 + a] > bvx) { bvx = z[16 + a]; sx = a; }
+                if (z[49 - a] > bvy) { bvy = z[49 - a]; sy = -a; }
+                if (z[49 + a] > bvy) { bvy = z[49 + a]; sy = a; }
+            }
+            pv = z[67] > z[66] ? 1 : 0;
+            sx = min(max(sx, b.dxlo), b.dxhi);
+            sy = min(max(sy, b.dylo), b.dyhi);
+        }
+        __syncwarp();  // s_logit is reused by the next block of this warp
+        // ---- search ----
+        int nsp = 0;
+        uint32_t v = 0, cval = 0;
+        visit(b, bm, wmin, wmax, nsp, 0, 0, &cval, lane);  // the origin is always a candidate
+        int cx = 0, cy = 0;
+        if ((sx != 0 || sy != 0) && visit(b, bm, wmin, wmax, nsp, sx, sy, &v, lane) && v < cval) {
+            cx = sx; cy = sy; cval = v;
+        }
+        int bxp = cx, byp = cy;
+        uint32_t bsad = cval;
+        for (int i = 0; i < 6; ++i) {
+            const int qx = cx + (pv ? kFirstV[i][0] : kFirstH[i][0]);
+            const int qy = cy + (pv ? kFirstV[i][1] : kFirstH[i][1]);
+            if (visit(b, bm, wmin, wmax, nsp, qx, qy, &v, lane) && v < bsad) { bsad = v; bxp = qx; byp = qy; }
+        }
+        if (bxp != cx || byp != cy) {
+            int pat = (byp == cy) ? 0 : 1;  // switching strategy one
+            cx = bxp; cy = byp;
+            for (int guard = 0; guard < 4 * side_max * side_max; ++guard) {
+                for (int i = 0; i < 4; ++i) {
+                    const int qx = cx + kDd[pat][i][0], qy = cy + kDd[pat][i][1];
+                    if (visit(b, bm, wmin, wmax, nsp, qx, qy, &v, lane) && v < bsad) { bsad = v; bxp = qx; byp = qy; }
+                }
+                if (bxp == cx && byp == cy) break;
+                if (abs(bxp - cx) + abs(byp - cy) == 1) pat ^= 1;  // switching strategy two
+                cx = bxp; cy = byp;
+            }
+            for (int i = 0; i < 2; ++i) {
+                const int qx = cx + kMid[pat][i][0], qy = cy + kMid[pat][i][1];
+                if (visit(b, bm, wmin, wmax, nsp, qx, qy, &v, lane) && v < bsad) { bsad = v; bxp = qx; byp = qy; }
+            }
+        }
+        if (lane == 0) {
+            reinterpret_cast<uint32_t*>(F.mv)[k] = (uint32_t)(uint16_t)bxp | ((uint32_t)(uint16_t)byp << 16);
+            F.sad[k] = bsad;
+            if (F.nsp) F.nsp[k] = (uint16_t)nsp;
+            if (starts) {
+                starts[(size_t)gid * 3] = (int16_t)sx;
+                starts[(size_t)gid * 3 + 1] = (int16_t)sy;
+                starts[(size_t)gid * 3 + 2] = (int16_t)pv;
+            }
+            for (int i = wmin; i <= wmax; ++i) bm[i] = 0u;
+            wmin = INT_MAX; wmax = -1;
+            __threadfence();
+            st_release(done + gid, 1);
+        }
+        __syncwarp();
+    }
+}
+
+inline int nblk(long n, int per = 256, int cap = 4096)
+{
+    return (int)std::max(1l, std::min((n + per - 1) / per, (long)cap));
+}
+
+// ------------------------------------------------------------------ workspace
+struct Ws {
+    __nv_bfloat16 *x, *cols[LAYERS], *a[LAYERS], *dz, *dzT, *colsT, *wT;
+    float *mvf, *logits, *dlogits, *da, *dcols, *gw;
+    int* labels;
+    double* loss_sum;
+};
+
+size_t al(size_t v) { return (v + 255) & ~size_t(255); }
+
+// lay out the workspace for n samples; train adds the backward buffers
+size_t ws_layout(uint8_t* base, int n, bool train, Ws* w)
+{
+    size_t off = 0;
+    auto take = [&](size_t bytes) { uint8_t* p = base ? base + off : nullptr; off += al(bytes); return p; };
+    const size_t N = (size_t)n;
+    const size_t rows_pad0 = (N * 256 + 31) / 32 * 32;
+    w->x = (__nv_bfloat16*)take(N * 2048 * 2);
+    w->mvf = (float*)take(N * 6 * 4);
+    w->labels = (int*)take(N * 3 * 4);
+    for (int l = 0; l < LAYERS; ++l) {
+        const size_t ho = HIN[l] / 2;
+        w->cols[l] = (__nv_bfloat16*)take((train || l == 0 ? N * ho * ho * KP[l] : (l == 1 ? N * 64 * 288 : 0)) * 2);
+        w->a[l] = (__nv_bfloat16*)take(N * ho * ho * CH * 2);
+    }
+    if (!train) {  // one shared im2col buffer at inference
+        for (int l = 1; l < LAYERS; ++l) w->cols[l] = w->cols[1];
+        w->cols[0] = w->cols[0];
+    }
+    w->logits = (float*)take(N * NLOGIT * 4);
+    w->dlogits = (float*)take(N * NLOGIT * 4);
+    w->loss_sum = (double*)take(8);
+    if (train) {
+        w->da = (float*)take(N * 8192 * 4);
+        w->dz = (__nv_bfloat16*)take(N * 8192 * 2);
+        w->dzT = (__nv_bfloat16*)take(CH * rows_pad0 * 2);
+        w->colsT = (__nv_bfloat16*)take(std::max(KP[0] * rows_pad0, (size_t)288 * ((N * 64 + 31) / 32 * 32)) * 2);
+        w->dcols = (float*)take(N * 64 * 288 * 4);
+        w->gw = (float*)take(32 * 288 * 4);
+        w->wT = (__nv_bfloat16*)take(288 * 32 * 2);
+    }
+    return off;
+}
+
+int ensure_ws(me_proposal* P, int n, bool train, Ws* w)
+{
+    const size_t need = ws_layout(nullptr, n, train, w);
+    if (P->ws_cap < need) {
+        if (P->ws) cudaFree(P->ws);
+        P->ws = nullptr;
+        P->ws_cap = 0;
+        if (cudaMalloc(&P->ws, need) != cudaSuccess) return fail(P->ctx, ME_ERR_NOMEM, "proposal workspace");
+        P->ws_cap = need;
+    }
+    ws_layout(P->ws, n, train, w);
+    return ME_OK;
+}
+
+int ensure_frames(me_proposal* P, const me_frame_desc* d, int n, bool labels_from_mv, long* total)
+{
+    me_ctx* c = P->ctx;
+    std::vector<PropFrame> t(n);
+    long base = 0;
+    for (int i = 0; i < n; ++i) {
+        if (!d[i].cur || !d[i].ref || !d[i].mv) return fail(c, ME_ERR_ARG, "cur, ref and mv must not be NULL");
+        if (d[i].w <= 0 || d[i].h <= 0 || d[i].w % 16 || d[i].h % 16 || d[i].pitch < d[i].w || d[i].pitch % 16)
+            return fail(c, ME_ERR_ARG, "the learned proposal needs 16x16 blocks: w, h multiples of 16");
+        if (d[i].range < 1 || d[i].range > ME_MAX_RANGE) return fail(c, ME_ERR_ARG, "range must be in 1..32");
+        if (((uintptr_t)d[i].mv % 4) || ((uintptr_t)d[i].sad % 4) || ((uintptr_t)d[i].nsp % 2))
+            return fail(c, ME_ERR_ARG, "mv/sad must be 4-byte aligned, nsp 2-byte aligned");
+        PropFrame f{};
+        f.cur = d[i].cur; f.ref = d[i].ref;
+        f.nbr = labels_from_mv ? d[i].mv : nullptr;
+        f.mv = d[i].mv; f.sad = d[i].sad; f.nsp = d[i].nsp;
+        f.w = d[i].w; f.h = d[i].h; f.pitch = d[i].pitch; f.range = d[i].range;
+        f.nbx = d[i].w / 16; f.nby = d[i].h / 16;
+        f.base = (int)base;
+        base += (long)f.nbx * f.nby;
+        t[i] = f;
+    }
+    if (base > INT_MAX / 2) return fail(c, ME_ERR_ARG, "too many blocks in one call");
+    if (P->frames_cap < n) {
+        if (P->frames) cudaFree(P->frames);
+        P->frames = nullptr;
+        P->frames_cap = 0;
+        if (cudaMalloc(&P->frames, sizeof(PropFrame) * n) != cudaSuccess)
+            return fail(c, ME_ERR_NOMEM, "proposal frame table");
+        P->frames_cap = n;
+    }
+    cudaError_t e = cudaMemcpy(P->frames, t.data(), sizeof(PropFrame) * n, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(c, e, "proposal frame table upload");
+    *total = base;
+    return ME_OK;
+}
+
+cudaError_t repack(me_proposal* P, cudaStream_t st)
+{
+    for (int l = 0; l < LAYERS; ++l) {
+        cudaError_t e = pack_weights(P->p + PW[l], CIN[l], KP[l], P->w[l], st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// conv trunk + head for n samples whose features are in w->x / w->mvf
+cudaError_t forward(me_proposal* P, const Ws& w, int n, bool head, cudaStream_t st)
+{
+    cudaError_t e = cudaSuccess;
+    for (int l = 0; l < LAYERS && e == cudaSuccess; ++l) {
+        const __nv_bfloat16* in = l == 0 ? w.x : w.a[l - 1];
+        const int ho = HIN[l] / 2;
+        e = im2col(in, n, HIN[l], CIN[l], KP[l], w.cols[l], st);
+        if (e == cudaSuccess)
+            e = gemm(w.cols[l], KP[l], P->w[l], KP[l], nullptr, CH, n * ho * ho, CH, KP[l], 1, GEMM_BIAS_RELU,
+                     P->p + PB[l], w.a[l], st);
+    }
+    if (e == cudaSuccess && head) e = head_fwd(w.a[3], w.mvf, n, P->p + P_FW, P->p + P_FB, w.logits, st);
+    return e;
+}
+
+cudaError_t backward(me_proposal* P, const Ws& w, int n, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(P->g, 0, sizeof(float) * NPARAMS, st);
+    if (e == cudaSuccess) e = head_bwd(w.dlogits, w.a[3], w.mvf, n, P->p + P_FW, P->g + P_FW, P->g + P_FB, w.da, st);
+    for (int l = LAYERS - 1; l >= 0 && e == cudaSuccess; --l) {
+        const int ho = HIN[l] / 2;
+        const long rows = (long)n * ho * ho;
+        const int rows_pad = (int)((rows + 31) / 32 * 32);
+        e = relu_back(w.da, w.a[l], rows, w.dz, P->g + PB[l], st);
+        if (e == cudaSuccess) e = transpose(w.dz, (int)rows, CH, CH, w.dzT, rows_pad, st);
+        if (e == cudaSuccess) e = transpose(w.cols[l], (int)rows, KP[l], KP[l], w.colsT, rows_pad, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(w.gw, 0, sizeof(float) * CH * KP[l], st);
+        if (e == cudaSuccess)
+            e = gemm(w.dzT, rows_pad, w.colsT, rows_pad, w.gw, KP[l], CH, KP[l], rows_pad,
+                     std::max(1, rows_pad / 2048), GEMM_ATOMIC, nullptr, nullptr, st);
+        if (e == cudaSuccess) e = unpack_wgrad(w.gw, CIN[l], KP[l], P->g + PW[l], st);
+        if (l > 0 && e == cudaSuccess) {
+            e = transpose(P->w[l], CH, KP[l], KP[l], w.wT, CH, st);  // W [32][KP] -> [KP][32]
+            if (e == cudaSuccess)
+                e = gemm(w.dz, CH, w.wT, CH, w.dcols, KP[l], (int)rows, KP[l], CH, 1, GEMM_STORE, nullptr, nullptr, st);
+            if (e == cudaSuccess) e = col2im(w.dcols, n, HIN[l], CIN[l], KP[l], w.da, st);
+        }
+    }
+    return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+int me_proposal_create(me_ctx* c, me_proposal** out)
+{
+    if (!c || !out) return ME_ERR_ARG;
+    *out = nullptr;
+    me_proposal* P = new me_proposal();
+    P->ctx = c;
+    bool ok = cudaMalloc(&P->p, sizeof(float) * NPARAMS) == cudaSuccess &&
+              cudaMalloc(&P->g, sizeof(float) * NPARAMS) == cudaSuccess &&
+              cudaMalloc(&P->m, sizeof(float) * NPARAMS) == cudaSuccess &&
+              cudaMalloc(&P->v, sizeof(float) * NPARAMS) == cudaSuccess;
+    for (int l = 0; l < LAYERS && ok; ++l) ok = cudaMalloc(&P->w[l], sizeof(__nv_bfloat16) * CH * KP[l]) == cudaSuccess;
+    if (ok) ok = cudaMemset(P->p, 0, sizeof(float) * NPARAMS) == cudaSuccess &&
+                 cudaMemset(P->m, 0, sizeof(float) * NPARAMS) == cudaSuccess &&
+                 cudaMemset(P->v, 0, sizeof(float) * NPARAMS) == cudaSuccess;
+    if (ok) ok = repack(P, nullptr) == cudaSuccess && cudaDeviceSynchronize() == cudaSuccess;
+    if (!ok) {
+        me_proposal_free(P);
+        return fail(c, ME_ERR_NOMEM, "proposal allocation");
+    }
+    *out = P;
+    return ME_OK;
+}
+
+void me_proposal_free(me_proposal* P)
+{
+    if (!P) return;
+    cudaFree(P->p); cudaFree(P->g); cudaFree(P->m); cudaFree(P->v);
+    for (auto* w : P->w) cudaFree(w);
+    cudaFree(P->ws); cudaFree(P->frames); cudaFree(P->order);
+    delete P;
+}
+
+int me_proposal_set_params(me_ctx* c, me_proposal* P, const float* host)
+{
+    if (!c || !P || !host) return ME_ERR_ARG;
+    cudaError_t e = cudaMemcpy(P->p, host, sizeof(float) * NPARAMS, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(P->m, 0, sizeof(float) * NPARAMS);
+    if (e == cudaSuccess) e = cudaMemset(P->v, 0, sizeof(float) * NPARAMS);
+    if (e == cudaSuccess) e = repack(P, nullptr);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    P->step = 0;
+    return e == cudaSuccess ? ME_OK : cuda_fail(c, e, "me_proposal_set_params");
+}
+
+int me_proposal_get_params(me_ctx* c, me_proposal* P, float* host)
+{
+    if (!c || !P || !host) return ME_ERR_ARG;
+    cudaError_t e = cudaMemcpy(host, P->p, sizeof(float) * NPARAMS, cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? ME_OK : cuda_fail(c, e, "me_proposal_get_params");
+}
+
+int me_proposal_train_step(me_ctx* c, me_proposal* P, const me_frame_desc* d, int n, float lr, float* loss_out,
+                           float* grad_out, void* stream)
+{
+    if (!c || !P || !d || n <= 0) return ME_ERR_ARG;
+    long total = 0;
+    int rc = ensure_frames(P, d, n, true, &total);
+    if (rc != ME_OK) return rc;
+    if (total > 65536) return fail(c, ME_ERR_ARG, "at most 65536 blocks per training step");
+    Ws w;
+    rc = ensure_ws(P, (int)total, true, &w);
+    if (rc != ME_OK) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int ns = (int)total;
+    cudaError_t e = cudaMemsetAsync(w.loss_sum, 0, sizeof(double), st);
+    if (e == cudaSuccess) {
+        feat_kernel<<<nblk((long)ns * 1024), 256, 0, st>>>(P->frames, n, 0, ns, w.x, w.mvf, w.labels);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = forward(P, w, ns, true, st);
+    if (e == cudaSuccess) e = loss(w.logits, w.labels, ns, 1.f / ns, w.dlogits, w.loss_sum, st);
+    if (e == cudaSuccess) e = backward(P, w, ns, st);
+    if (e == cudaSuccess && lr > 0.f) {
+        e = adam(P->p, P->g, P->m, P->v, NPARAMS, lr, ++P->step, st);
+        if (e == cudaSuccess) e = repack(P, st);
+    }
+    double ls = 0.0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&ls, w.loss_sum, sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && grad_out)
+        e = cudaMemcpyAsync(grad_out, P->g, sizeof(float) * NPARAMS, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "me_proposal_train_step");
+    if (loss_out) *loss_out = (float)(ls / ns);
+    return ME_OK;
+}
+
+int me_proposal_logits(me_ctx* c, me_proposal* P, const me_frame_desc* d, float* logits, void* stream)
+{
+    if (!c || !P || !d || !logits) return ME_ERR_ARG;
+    long total = 0;
+    int rc = ensure_frames(P, d, 1, true, &total);
+    if (rc != ME_OK) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    for (long s0 = 0; s0 < total; s0 += kChunk) {
+        const int ns = (int)std::min<long>(kChunk, total - s0);
+        Ws w;
+        rc = ensure_ws(P, kChunk, false, &w);
+        if (rc != ME_OK) return rc;
+        feat_kernel<<<nblk((long)ns * 1024), 256, 0, st>>>(P->frames, 1, s0, ns, w.x, w.mvf, nullptr);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = forward(P, w, ns, true, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(logits + s0 * NLOGIT, w.logits, sizeof(float) * ns * NLOGIT, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(c, e, "me_proposal_logits");
+    }
+    return ME_OK;
+}
+
+int me_estimate_learned_batch(me_ctx* c, me_proposal* P, const me_frame_desc* d, int n, int16_t* starts,
+                              void* stream)
+{
+    if (!c || !P || !d || n <= 0) return ME_ERR_ARG;
+    for (int i = 0; i < n; ++i)
+        if (!d[i].sad) return fail(c, ME_ERR_ARG, "sad must not be NULL");
+    long total = 0;
+    int rc = ensure_frames(P, d, n, false, &total);
+    if (rc != ME_OK) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    // buffers after the trunk workspace: conv-4 features, done flags, counter
+    Ws w;
+    const size_t trunk = ws_layout(nullptr, kChunk, false, &w);
+    const size_t need = al(trunk) + al((size_t)total * 128 * 2) + al((size_t)total * 4) + 256;
+    if (P->ws_cap < need) {
+        cudaFree(P->ws);
+        P->ws = nullptr;
+        P->ws_cap = 0;
+        if (cudaMalloc(&P->ws, need) != cudaSuccess) return fail(c, ME_ERR_NOMEM, "learned-search workspace");
+        P->ws_cap = need;
+    }
+    ws_layout(P->ws, kChunk, false, &w);
+    __nv_bfloat16* a4all = reinterpret_cast<__nv_bfloat16*>(P->ws + al(trunk));
+    int* done = reinterpret_cast<int*>(P->ws + al(trunk) + al((size_t)total * 128 * 2));
+    int* counter = done + ((al((size_t)total * 4)) / 4);
+    // wavefront order: t = bx + 2 by ascending, frames interleaved
+    std::vector<int> ord;
+    ord.reserve(total);
+    {
+        std::vector<PropFrame> t(n);
+        cudaMemcpy(t.data(), P->frames, sizeof(PropFrame) * n, cudaMemcpyDeviceToHost);
+        int tmax = 0;
+        for (auto& f : t) tmax = std::max(tmax, (f.nbx - 1) + 2 * (f.nby - 1));
+        for (int tt = 0; tt <= tmax; ++tt)
+            for (auto& f : t)
+                for (int by = 0; by < f.nby; ++by) {
+                    const int bx = tt - 2 * by;
+                    if (bx >= 0 && bx < f.nbx) ord.push_back(f.base + by * f.nbx + bx);
+                }
+    }
+    if (P->order_cap < total) {
+        cudaFree(P->order);
+        P->order = nullptr;
+        P->order_cap = 0;
+        if (cudaMalloc(&P->order, sizeof(int) * total) != cudaSuccess) return fail(c, ME_ERR_NOMEM, "order table");
+        P->order_cap = total;
+    }
+    cudaError_t e = cudaMemcpyAsync(P->order, ord.data(), sizeof(int) * total, cudaMemcpyHostToDevice, st);
+    for (long s0 = 0; s0 < total && e == cudaSuccess; s0 += kChunk) {
+        const int ns = (int)std::min<long>(kChunk, total - s0);
+        feat_kernel<<<nblk((long)ns * 1024), 256, 0, st>>>(P->frames, n, s0, ns, w.x, w.mvf, nullptr);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = forward(P, w, ns, false, st);
+        if (e == cudaSuccess) {
+            copy_rows_kernel<<<nblk((long)ns * 128), 256, 0, st>>>(w.a[3], (long)ns * 128, a4all + s0 * 128);
+            e = cudaGetLastError();
+        }
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(done, 0, al((size_t)total * 4) + 256, st);
+    int max_range = 1;
+    for (int i = 0; i < n; ++i) max_range = std::max(max_range, d[i].range);
+    const int side = 2 * max_range + 1;
+    const size_t smem = (size_t)8 * ((side * side + 31) / 32) * 4;
+    if (e == cudaSuccess) {
+        learned_dcds_kernel<<<c->num_sms * 4, 256, smem, st>>>(P->frames, n, P->order, (int)total, a4all, P->p + P_FW,
+                                                              P->p + P_FB, done, counter, starts, c->status, max_range);
+        e = cudaGetLastError();
+    }
+    // the host-side tables are reused by the next call: wait for this one
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e == cudaSuccess ? ME_OK : cuda_fail(c, e, "me_estimate_learned_batch");
+}
+
+}  // extern "C"

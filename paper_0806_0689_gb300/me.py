@@ -24,7 +24,11 @@ ALGOS = {"fs": ME_ALGO_FS, "dcds": ME_ALGO_DCDS, "dcds_s": ME_ALGO_DCDS_S, "dcds
 
 EXPORTS = ["me_init", "me_free", "me_last_error", "me_estimate", "me_estimate_batch", "me_graph_create",
            "me_graph_launch", "me_graph_free", "me_eval", "me_eval_batch", "me_stats_from_sums", "me_tune",
-           "me_absdiff_peak", "me_check_status", "me_estimate_batch_noalloc", "me_tune_batch"]
+           "me_absdiff_peak", "me_check_status", "me_estimate_batch_noalloc", "me_tune_batch",
+           "me_proposal_create", "me_proposal_free", "me_proposal_set_params", "me_proposal_get_params",
+           "me_proposal_train_step", "me_proposal_logits", "me_estimate_learned_batch"]
+ME_PROPOSAL_NPARAMS = 37532
+ME_PROPOSAL_NLOGITS = 68
 
 
 class MeError(RuntimeError):
@@ -86,8 +90,17 @@ def load(build_if_missing: bool = True):
             L.me_absdiff_peak.argtypes = [P, I, ctypes.POINTER(ctypes.c_double), I, ctypes.POINTER(I), P]
             L.me_check_status.argtypes = [P, P]
             L.me_estimate_batch_noalloc.argtypes = [ctypes.POINTER(FrameDesc), I, I, I, P, ctypes.c_char_p, I]
+            L.me_proposal_create.argtypes = [P, ctypes.POINTER(P)]
+            L.me_proposal_free.argtypes = [P]
+            L.me_proposal_free.restype = None
+            L.me_proposal_set_params.argtypes = [P, P, P]
+            L.me_proposal_get_params.argtypes = [P, P, P]
+            L.me_proposal_train_step.argtypes = [P, P, ctypes.POINTER(FrameDesc), I, ctypes.c_float,
+                                                 ctypes.POINTER(ctypes.c_float), P, P]
+            L.me_proposal_logits.argtypes = [P, P, ctypes.POINTER(FrameDesc), P, P]
+            L.me_estimate_learned_batch.argtypes = [P, P, ctypes.POINTER(FrameDesc), I, P, P]
             for n in EXPORTS:
-                if n not in ("me_free", "me_last_error", "me_graph_free"):
+                if n not in ("me_free", "me_last_error", "me_graph_free", "me_proposal_free"):
                     getattr(L, n).restype = I
             _lib = L
     return _lib
@@ -209,5 +222,68 @@ class Context:
         self._check(self.L.me_absdiff_peak(self.h, iters, out, n_variants, ctypes.byref(used), _stream(stream)))
         return list(out), used.value
 
+    # -- learned start proposal ----------------------------------------------
+    def me_proposal_create(self):
+        h = ctypes.c_void_p()
+        self._check(self.L.me_proposal_create(self.h, ctypes.byref(h)))
+        return h
+
+    def me_proposal_free(self, prop):
+        self.L.me_proposal_free(prop)
+
+    def me_proposal_set_params(self, prop, params):
+        a = np.ascontiguousarray(params, dtype=np.float32)
+        assert a.size == ME_PROPOSAL_NPARAMS
+        self._check(self.L.me_proposal_set_params(self.h, prop, ctypes.c_void_p(a.ctypes.data)))
+
+    def me_proposal_get_params(self, prop):
+        a = np.zeros(ME_PROPOSAL_NPARAMS, np.float32)
+        self._check(self.L.me_proposal_get_params(self.h, prop, ctypes.c_void_p(a.ctypes.data)))
+        return a
+
+    def me_proposal_train_step(self, prop, descs, lr, want_grad=False, stream=None):
+        loss = ctypes.c_float(0.0)
+        g = np.zeros(ME_PROPOSAL_NPARAMS, np.float32) if want_grad else None
+        self._check(self.L.me_proposal_train_step(self.h, prop, descs, len(descs), lr, ctypes.byref(loss),
+                                                  None if g is None else ctypes.c_void_p(g.ctypes.data),
+                                                  _stream(stream)))
+        return (loss.value, g) if want_grad else loss.value
+
+    def me_proposal_logits(self, prop, desc, logits, stream=None):
+        self._check(self.L.me_proposal_logits(self.h, prop, desc, _ptr(logits), _stream(stream)))
+
+    def me_estimate_learned_batch(self, prop, descs, starts=None, stream=None):
+        self._check(self.L.me_estimate_learned_batch(self.h, prop, descs, len(descs), _ptr(starts),
+                                                     _stream(stream)))
+
     def me_check_status(self, stream=None):
         self._check(self.L.me_check_status(self.h, _stream(stream)))
+
+
+def proposal_init_params(seed=0):
+    """He-normal initial parameters of the proposal network (host, float32, the
+    parameter order of include/me.h)."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for cin in (2, 32, 32, 32):
+        parts.append(rng.normal(0.0, np.sqrt(2.0 / (9 * cin)), 32 * cin * 9))
+        parts.append(np.full(32, 0.01))
+    parts.append(rng.normal(0.0, np.sqrt(1.0 / 134), 68 * 134))
+    parts.append(np.zeros(68))
+    p = np.concatenate(parts).astype(np.float32)
+    assert p.size == ME_PROPOSAL_NPARAMS
+    return p
+
+
+def train_proposal(ctx, prop, descs, steps, lr=2e-3, pairs_per_step=2, seed=0):
+    """Host loop over training steps (each step runs entirely in the library's
+    kernels).  descs: FrameDesc array whose mv fields hold the label fields.
+    Returns the list of step losses."""
+    rng = np.random.default_rng(seed)
+    n = len(descs)
+    losses = []
+    for _ in range(steps):
+        pick = rng.choice(n, size=min(pairs_per_step, n), replace=False)
+        sub = (FrameDesc * len(pick))(*[descs[int(i)] for i in pick])
+        losses.append(ctx.me_proposal_train_step(prop, sub, lr))
+    return losses
