@@ -32,50 +32,74 @@ __global__ void __launch_bounds__(256) eval_kernel(const EvalDev* __restrict__ f
     const uint32_t* fsw = reinterpret_cast<const uint32_t*>(F.mv_fs);
 
     unsigned long long s_abs = 0, s_sq = 0, s_nsp = 0, s_eq = 0, s_dist = 0, s_pix = 0;
-    for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < total; it += gridDim.x * blockDim.x) {
-        const int y = it / nbx, bx = it - y * nbx;
-        const int by = y / B, r = y - by * B;
-        const int k = by * nbx + bx;
-        const uint32_t m = __ldg(mvw + k);
-        const int dx = (int)(int16_t)(m & 0xffffu), dy = (int)(int16_t)(m >> 16);
-        const int x = bx * B;
-        if (x + dx >= 0 && x + dx <= W - B && by * B + dy >= 0 && by * B + dy <= H - B) {
-            const uint8_t* cp = F.cur + (size_t)y * P + x;
-            uint32_t c[BW];
-            if constexpr (BW == 4) {
-                const uint4 v = __ldg(reinterpret_cast<const uint4*>(cp));
-                c[0] = v.x; c[1] = v.y; c[2] = v.z; c[3] = v.w;
-            } else {
-                const uint2 v = __ldg(reinterpret_cast<const uint2*>(cp));
-                c[0] = v.x; c[1] = v.y;
-            }
-            const long g = (long)(y + dy) * P + x + dx;
-            const uint32_t* rp = reinterpret_cast<const uint32_t*>(F.ref + (g & ~3l));
-            const unsigned sh = (unsigned)(g & 3) * 8u;
-            uint32_t wv[BW + 1];
+    constexpr int U = 4;  // items per thread per trip: their loads are issued together
+    const int stride = gridDim.x * blockDim.x;
+    for (int it0 = blockIdx.x * blockDim.x + threadIdx.x; it0 < total; it0 += U * stride) {
+        uint32_t m[U];
+        int yv[U], bxv[U];
 #pragma unroll
-            for (int i = 0; i < BW; ++i) wv[i] = __ldg(rp + i);
-            // the word after the segment is read only when the segment is unaligned,
-            // and then it still lies inside the row
-            wv[BW] = sh ? __ldg(rp + BW) : 0u;
-            uint32_t a = 0, q = 0;
-#pragma unroll
-            for (int i = 0; i < BW; ++i) {
-                const uint32_t d = __vabsdiffu4(c[i], __funnelshift_r(wv[i], wv[i + 1], sh));
-                a = __dp4a(d, 0x01010101u, a);
-                q = __dp4a(d, d, q);
-            }
-            s_abs += a;
-            s_sq += q;
-            s_pix += B;
+        for (int u = 0; u < U; ++u) {
+            const int it = it0 + u * stride;
+            const int itc = it < total ? it : it0;
+            yv[u] = itc / nbx;
+            bxv[u] = itc - yv[u] * nbx;
+            m[u] = __ldg(mvw + (yv[u] / B) * nbx + bxv[u]);
         }
-        if (r == 0) {
-            if (F.nsp) s_nsp += F.nsp[k];
-            if (fsw) {
-                const uint32_t fw = __ldg(fsw + k);
-                const int ex = dx - (int)(int16_t)(fw & 0xffffu), ey = dy - (int)(int16_t)(fw >> 16);
-                s_eq += (ex == 0 && ey == 0);
-                s_dist += (unsigned long long)__double2ll_rn(sqrt((double)(ex * ex + ey * ey)) * 16777216.0);
+        uint32_t c[U][BW], wv[U][BW + 1];
+        bool okv[U];
+        long gv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int y = yv[u], bx = bxv[u], by = y / B;
+            const int dx = (int)(int16_t)(m[u] & 0xffffu), dy = (int)(int16_t)(m[u] >> 16);
+            const int x = bx * B;
+            okv[u] = (it0 + u * stride < total) && x + dx >= 0 && x + dx <= W - B && by * B + dy >= 0 &&
+                     by * B + dy <= H - B;
+            gv[u] = (long)(y + dy) * P + x + dx;
+            if (okv[u]) {
+                const uint8_t* cp = F.cur + (size_t)y * P + x;
+                if constexpr (BW == 4) {
+                    const uint4 v = __ldg(reinterpret_cast<const uint4*>(cp));
+                    c[u][0] = v.x; c[u][1] = v.y; c[u][2] = v.z; c[u][3] = v.w;
+                } else {
+                    const uint2 v = __ldg(reinterpret_cast<const uint2*>(cp));
+                    c[u][0] = v.x; c[u][1] = v.y;
+                }
+                const uint32_t* rp = reinterpret_cast<const uint32_t*>(F.ref + (gv[u] & ~3l));
+#pragma unroll
+                for (int i = 0; i < BW; ++i) wv[u][i] = __ldg(rp + i);
+                // the word after the segment is read only when the segment is unaligned,
+                // and then it still lies inside the row
+                wv[u][BW] = (gv[u] & 3) ? __ldg(rp + BW) : 0u;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (it0 + u * stride >= total) continue;
+            const int y = yv[u], bx = bxv[u], by = y / B, r = y - by * B;
+            const int k = by * nbx + bx;
+            const int dx = (int)(int16_t)(m[u] & 0xffffu), dy = (int)(int16_t)(m[u] >> 16);
+            if (okv[u]) {
+                const unsigned sh = (unsigned)(gv[u] & 3) * 8u;
+                uint32_t a = 0, q = 0;
+#pragma unroll
+                for (int i = 0; i < BW; ++i) {
+                    const uint32_t d = __vabsdiffu4(c[u][i], __funnelshift_r(wv[u][i], wv[u][i + 1], sh));
+                    a = __dp4a(d, 0x01010101u, a);
+                    q = __dp4a(d, d, q);
+                }
+                s_abs += a;
+                s_sq += q;
+                s_pix += B;
+            }
+            if (r == 0) {
+                if (F.nsp) s_nsp += F.nsp[k];
+                if (fsw) {
+                    const uint32_t fw = __ldg(fsw + k);
+                    const int ex = dx - (int)(int16_t)(fw & 0xffffu), ey = dy - (int)(int16_t)(fw >> 16);
+                    s_eq += (ex == 0 && ey == 0);
+                    s_dist += (unsigned long long)__double2ll_rn(sqrt((double)(ex * ex + ey * ey)) * 16777216.0);
+                }
             }
         }
     }
@@ -111,7 +135,7 @@ cudaError_t launch_eval(const EvalDev* frames, int nframes, int block, int max_b
 {
     // enough CTAs to fill the GPU a few times over, and at least ~16 items per thread
     const long items = (long)max_blocks * block;
-    const long by_items = (items + 256 * 16 - 1) / (256 * 16);
+    const long by_items = (items + 256 * 32 - 1) / (256 * 32);
     const long by_gpu = (long)num_sms * 8 / std::max(nframes, 1) + 1;
     int gx = (int)std::max(1l, std::min(by_items, by_gpu));
     dim3 grid(gx, nframes);

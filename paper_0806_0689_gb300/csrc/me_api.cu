@@ -28,6 +28,12 @@ using me::kHeadBytes;
 #ifndef ME_DCDS_THREADS
 #define ME_DCDS_THREADS 128  // default CTA size of the DCDS kernel
 #endif
+#ifndef ME_DCDS_KERNEL
+#define ME_DCDS_KERNEL 0     // default DCDS kernel: tile-phase (the warp-specialised one is a tuner candidate)
+#endif
+#ifndef ME_DCDS_AWARPS
+#define ME_DCDS_AWARPS 4     // default A warps per CTA of the warp-specialised kernel
+#endif
 
 namespace {
 
@@ -95,6 +101,8 @@ Shape default_shape(me_ctx* c, int algo, int block, int range)
     s.k = 0;
     s.ctas_per_sm = 0;  // from the occupancy of the kernel
     s.stages = ME_DCDS_STAGES;
+    s.kernel = ME_DCDS_KERNEL;
+    s.a_warps = ME_DCDS_AWARPS;
     (void)c;
     return s;
 }
@@ -152,6 +160,23 @@ int take_slot(me_ctx* c, size_t bytes, Slot** out)
     return ME_OK;
 }
 
+// Make a DCDS item queue of at least `entries` items, zeroed at allocation
+// (the warp-specialised kernel never needs it reset).
+int ensure_queue(me_ctx* c, void** q, size_t* qcap, size_t entries)
+{
+    if (*qcap >= entries) return ME_OK;
+    if (*q) cudaFree(*q);
+    *q = nullptr;
+    *qcap = 0;
+    const size_t cap = (std::max<size_t>(entries, 4096) + 63) & ~size_t(63);
+    const size_t bytes = me::dcds_queue_bytes(cap);
+    if (cudaMalloc(q, bytes) != cudaSuccess) return fail(c, ME_ERR_NOMEM, "cudaMalloc of the DCDS queue failed");
+    cudaError_t e = cudaMemset(*q, 0, bytes);
+    if (e != cudaSuccess) return cuda_fail(c, e, "queue initialisation");
+    *qcap = cap;
+    return ME_OK;
+}
+
 // Fill the device-side table (tiles per frame, TMA maps for DCDS) into
 // `table`; returns the number of tiles, or -1 if a tensor map is rejected.
 int build_table(const me_frame_desc* d, int n, int block, const Shape& s, bool fs, FrameDev* table,
@@ -204,17 +229,28 @@ int validate_batch(me_ctx* c, const me_frame_desc* d, int n, int block, int algo
     return ME_OK;
 }
 
-// Launch the search over a table already on the device at `dev`.
-cudaError_t launch_search(me_ctx* c, void* dev, int n, int ntiles, int block, int algo, int max_range,
-                          const Shape& s, cudaStream_t st)
+// Launch the search over a table already on the device at `dev` (queue: the
+// DCDS item queue of `qcap` entries, for the warp-specialised kernel).
+cudaError_t launch_search(me_ctx* c, void* dev, void* queue, size_t qcap, int n, int ntiles, int block, int algo,
+                          int max_range, const Shape& s, cudaStream_t st)
 {
     int* head = reinterpret_cast<int*>(dev);
     const FrameDev* table = reinterpret_cast<const FrameDev*>(reinterpret_cast<char*>(dev) + kHeadBytes);
     if (algo == ME_ALGO_FS) return me::launch_fs(table, n, ntiles, block, max_range, s, st);
-    cudaError_t e = cudaMemsetAsync(head, 0, sizeof(int), st);
+    cudaError_t e = cudaMemsetAsync(head, 0, me::kCounterInts * sizeof(int), st);
     if (e != cudaSuccess) return e;
+    if (s.kernel == 1)
+        return me::launch_dcds_ws(table, n, ntiles, block, max_range, algo == ME_ALGO_DCDS_S, s, head, queue,
+                                  (int)qcap, c->status, c->num_sms, st);
     return me::launch_dcds(table, n, ntiles, block, max_range, algo == ME_ALGO_DCDS_S, s, head, c->status,
                            c->num_sms, st);
+}
+
+size_t total_blocks(const me_frame_desc* d, int n, int block)
+{
+    size_t t = 0;
+    for (int i = 0; i < n; ++i) t += (size_t)(d[i].w / block) * (d[i].h / block);
+    return t;
 }
 
 int run_batch(me_ctx* c, const me_frame_desc* d, int n, int block, int algo, const Shape& s, cudaStream_t st)
@@ -229,7 +265,11 @@ int run_batch(me_ctx* c, const me_frame_desc* d, int n, int block, int algo, con
     if (ntiles < 0) return fail(c, ME_ERR_CUDA, "cuTensorMapEncodeTiled rejected a frame description");
     cudaError_t e = cudaMemcpyAsync(slot->dev, slot->host, bytes, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "descriptor upload");
-    e = launch_search(c, slot->dev, n, ntiles, block, algo, max_range, s, st);
+    if (algo != ME_ALGO_FS && s.kernel == 1) {
+        rc = ensure_queue(c, &slot->queue, &slot->qcap, total_blocks(d, n, block));
+        if (rc != ME_OK) return rc;
+    }
+    e = launch_search(c, slot->dev, slot->queue, slot->qcap, n, ntiles, block, algo, max_range, s, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "search launch");
     e = cudaEventRecord(slot->done, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaEventRecord");
@@ -243,14 +283,14 @@ void load_tune_cache(me_ctx* c)
     std::ifstream f(c->tune_path);
     std::string line;
     while (std::getline(f, line)) {
-        // algo block range WxH tx ty threads k stages
+        // algo block range WxH tx ty threads k stages kernel a_warps
         std::istringstream is(line);
-        int algo, block, range, tx, ty, th, k, stages;
+        int algo, block, range, tx, ty, th, k, stages, kernel, aw;
         std::string wh;
-        if (is >> algo >> block >> range >> wh >> tx >> ty >> th >> k >> stages) {
+        if (is >> algo >> block >> range >> wh >> tx >> ty >> th >> k >> stages >> kernel >> aw) {
             int w = 0, h = 0;
             if (sscanf(wh.c_str(), "%dx%d", &w, &h) == 2) {
-                Shape s{tx, ty, th, 0, k, stages};
+                Shape s{tx, ty, th, 0, k, stages, kernel, aw};
                 c->tuned[shape_key(algo, block, range, w, h)] = s;
             }
         }
@@ -293,6 +333,7 @@ void me_free(me_ctx* c)
         if (s.done) cudaEventDestroy(s.done);
         if (s.dev) cudaFree(s.dev);
         if (s.host) cudaFreeHost(s.host);
+        if (s.queue) cudaFree(s.queue);
     }
     if (c->status) cudaFree(c->status);
     delete c;
@@ -341,10 +382,15 @@ int me_graph_create(me_ctx* c, const me_frame_desc* descs, int n, int block, int
     e = cudaMemcpy(reinterpret_cast<char*>(g->dev) + kHeadBytes, table.data(), sizeof(FrameDev) * n,
                    cudaMemcpyHostToDevice);
     cudaStream_t cs = nullptr;
+    size_t qcap = 0;
+    if (e == cudaSuccess && algo != ME_ALGO_FS && s.kernel == 1) {
+        rc = ensure_queue(c, &g->queue, &qcap, total_blocks(descs, n, block));
+        if (rc != ME_OK) { me_graph_free(g); return rc; }
+    }
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        cudaError_t le = launch_search(c, g->dev, n, ntiles, block, algo, max_range, s, cs);
+        cudaError_t le = launch_search(c, g->dev, g->queue, qcap, n, ntiles, block, algo, max_range, s, cs);
         e = cudaStreamEndCapture(cs, &g->graph);
         if (le != cudaSuccess) e = le;
     }
@@ -371,6 +417,7 @@ void me_graph_free(me_graph* g)
     if (g->exec) cudaGraphExecDestroy(g->exec);
     if (g->graph) cudaGraphDestroy(g->graph);
     if (g->dev) cudaFree(g->dev);
+    if (g->queue) cudaFree(g->queue);
     delete g;
 }
 
@@ -449,9 +496,17 @@ int me_tune_batch(me_ctx* c, const me_frame_desc* descs, int n, int block, int a
             if (me::fs_smem_bytes(block, mr, s) <= 100 * 1024) cands.push_back(s);
         }
     } else {
+        for (int aw : {2, 4, 6}) {
+            Shape s = default_shape(c, algo, block, mr);
+            s.kernel = 1;
+            s.threads = 256;
+            s.a_warps = aw;
+            if (me::dcds_ws_smem_bytes(block, mr, s) <= 220 * 1024) cands.push_back(s);
+        }
         for (int th : {128, 256}) {
             for (int stages : {1, 2}) {
                 Shape s = default_shape(c, algo, block, mr);
+                s.kernel = 0;
                 s.threads = th;
                 s.stages = stages;
                 if (me::dcds_smem_bytes(block, mr, s) <= 220 * 1024) cands.push_back(s);
@@ -487,7 +542,7 @@ int me_tune_batch(me_ctx* c, const me_frame_desc* descs, int n, int block, int a
         std::ofstream f(c->tune_path, std::ios::app);
         const Shape& s = cands[bi];
         f << shape_key(algo, block, mr, mw, mh) << " " << s.tx << " " << s.ty << " " << s.threads << " " << s.k
-          << " " << s.stages << "\n";
+          << " " << s.stages << " " << s.kernel << " " << s.a_warps << "\n";
     }
     if (chosen) *chosen = bi;
     // leave the outputs computed with the chosen shape

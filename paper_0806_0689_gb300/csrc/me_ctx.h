@@ -18,6 +18,8 @@ struct Slot {
     size_t cap = 0;
     cudaEvent_t done = nullptr;
     bool used = false;
+    void* queue = nullptr;  // DCDS item queue: items (16 B each) then flags (4 B each), flags zeroed
+    size_t qcap = 0;        // entries
 };
 
 constexpr size_t kHeadBytes = 256;  // queue head (int) and padding before the table
@@ -38,7 +40,8 @@ struct me_ctx {
 
 struct me_graph {
     me_ctx* ctx = nullptr;
-    void* dev = nullptr;  // [head | table]
+    void* dev = nullptr;    // [head | table]
+    void* queue = nullptr;  // DCDS item queue (items, then zeroed flags)
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
 };

@@ -50,7 +50,9 @@ struct Shape {
     int threads;       // threads per CTA
     int ctas_per_sm;   // persistent grid = ctas_per_sm * SM count (0 = occupancy)
     int k;             // FS: candidate rows per thread
-    int stages;        // DCDS: 1 = load each tile when needed, 2 = prefetch the next tile
+    int stages;        // DCDS tile-phase kernel: 1 = load each tile when needed, 2 = prefetch
+    int kernel;        // DCDS: 0 = tile-phase kernel (dcds.cu), 1 = warp-specialised kernel (dcds_ws.cu)
+    int a_warps;       // DCDS warp-specialised: warps per CTA that stage tiles and run step 1
 };
 
 // Status bits a kernel may record (read back by me_check_status).
@@ -100,6 +102,19 @@ cudaError_t launch_dcds(const FrameDev* frames, int nframes, int ntiles, int blo
                         cudaStream_t st);
 size_t dcds_smem_bytes(int block, int max_range, const Shape& s);
 int dcds_ctas_per_sm(int block, int max_range, bool simplified, const Shape& s);
+
+// Warp-specialised DCDS.  counters: kCounterInts ints, zeroed before every
+// launch.  queue: kQueueHeadWords header words (word 0: epoch), then
+// max_items flags (4 B), then max_items items (16 B); all zero when allocated,
+// never reset afterwards; one launch at a time per queue.  max_items must be a
+// multiple of 4 and at least the number of blocks of the batch.
+constexpr int kCounterInts = 8;
+constexpr int kQueueHeadWords = 64;
+inline size_t dcds_queue_bytes(size_t max_items) { return kQueueHeadWords * 4 + max_items * 20; }
+cudaError_t launch_dcds_ws(const FrameDev* frames, int nframes, int ntiles, int block, int max_range,
+                           bool simplified, const Shape& s, int* counters, void* queue, int max_items,
+                           unsigned* status, int num_sms, cudaStream_t st);
+size_t dcds_ws_smem_bytes(int block, int max_range, const Shape& s);
 
 cudaError_t launch_fs(const FrameDev* frames, int nframes, int ntiles, int block, int max_range,
                       const Shape& s, cudaStream_t st);

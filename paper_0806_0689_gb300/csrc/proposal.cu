@@ -48,7 +48,7 @@ struct me_proposal {
 
 namespace {
 
-constexpr int kChunk = 2048;  // samples per trunk pass at inference
+constexpr int kChunk = 8192;  // samples per trunk pass at inference
 
 int fail(me_ctx* c, int code, const std::string& msg)
 {

@@ -295,3 +295,61 @@ def test_tune_keeps_parity(ctx, cif):
         assert_same(_host(mv, sad, nsp), oracle_search(cur, ref, 16, 7, algo), f"tuned {algo}")
         # the tuned shape is used by later calls too
         assert_same(gpu_search(ctx, cur, ref, 16, 7, algo), oracle_search(cur, ref, 16, 7, algo), algo)
+
+
+# launch shapes as the tune cache stores them: tx ty threads k stages kernel a_warps
+DCDS_SHAPES = {
+    "tile128_s1": "8 8 128 0 1 0 4",
+    "tile128_s2": "8 8 128 0 2 0 4",
+    "tile256_s1": "8 8 256 0 1 0 4",
+    "ws256_a2": "8 8 256 0 1 1 2",
+    "ws256_a6": "8 8 256 0 1 1 6",
+    "ws128_a1": "8 8 128 0 1 1 1",
+    "ws128_a4": "8 8 128 0 1 1 4",
+}
+
+
+@pytest.mark.parametrize("shape", sorted(DCDS_SHAPES))
+def test_every_dcds_kernel_shape(tmp_path, cif, shape):
+    """Both DCDS kernels (tile-phase and warp-specialised) in every staging
+    and warp split the tuner may choose give the oracle's results; a shape is
+    forced through the tune cache file of a fresh context."""
+    cur, ref = cif[3], cif[2]
+    h, w = cur.shape
+    cases = [(16, 7, "dcds"), (8, 15, "dcds"), (16, 32, "dcds_s"), (8, 3, "dcds_s")]
+    path = tmp_path / "tune.txt"
+    path.write_text("".join(f"{me.ALGOS[a]} {B} {R} {w}x{h} {DCDS_SHAPES[shape]}\n" for B, R, a in cases))
+    c2 = me.Context(0, tune_cache_path=str(path))
+    try:
+        for B, R, algo in cases:
+            want = oracle_search(cur, ref, B, R, algo)
+            for rep in range(3):  # repeated launches reuse the slot's queue
+                assert_same(gpu_search(c2, cur, ref, B, R, algo), want, f"{shape} {algo} B{B} R{R} rep{rep}")
+        c2.me_check_status()
+    finally:
+        c2.close()
+
+
+@pytest.mark.parametrize("shape", ["ws256_a2", "tile128_s2"])
+def test_dcds_shape_graph_replays(tmp_path, qcif, shape):
+    """Graph replays of a forced shape: a mixed-size batch, replayed with
+    the outputs cleared in between, matches the oracle every time."""
+    pairs = [(qcif[t], qcif[t - 1]) for t in range(1, 4)]
+    path = tmp_path / "tune.txt"
+    path.write_text(f"{me.ALGOS['dcds']} 16 16 176x144 {DCDS_SHAPES[shape]}\n")
+    c2 = me.Context(0, tune_cache_path=str(path))
+    try:
+        keep, descs = _batch(c2, pairs, 16, "dcds", [16] * len(pairs))
+        g = c2.me_graph_create(descs, 16, "dcds")
+        try:
+            for rep in range(4):
+                for (_, _, mv, sad, nsp) in keep:
+                    mv.fill_(-7); sad.fill_(-1); nsp.fill_(-1)
+                c2.me_graph_launch(g)
+                for (cur, ref), (_, _, mv, sad, nsp) in zip(pairs, keep):
+                    assert_same(_host(mv, sad, nsp), oracle.dcds(cur, ref, 16, 16), f"{shape} replay {rep}")
+        finally:
+            c2.me_graph_free(g)
+        c2.me_check_status()
+    finally:
+        c2.close()
