@@ -58,18 +58,40 @@ std::string shape_key(int algo, int block, int range, int w, int h)
     return o.str();
 }
 
-// K (candidate rows per FS thread) wasting the fewest rows of 2R+1.
+// K (candidate rows per FS thread): the fewest thread-rows of work for the
+// 2R+1 rows of candidates, counting about three rows of fixed cost per task
+// (its current block, its key reduction); ties go to the larger K.
 int fs_pick_k(int range)
 {
-    const int ks[4] = {15, 13, 11, 8};
-    int best = 8;
-    double be = -1.0;
+    const int ks[5] = {9, 11, 13, 15, 33};
     const int n = 2 * range + 1;
+    int best = 9, bc = 1 << 30;
     for (int k : ks) {
-        const double e = (double)n / (double)(((n + k - 1) / k) * k);
-        if (e > be + 1e-9) { be = e; best = k; }
+        const int cost = ((n + k - 1) / k) * (k + 3);
+        if (cost <= bc) { bc = cost; best = k; }
     }
     return best;
+}
+
+// FS tile width: the fewest idle threads over the tasks of a tile, with two
+// CTAs per SM (shared memory <= 112 KB).
+int fs_pick_tx(int block, int range, int k)
+{
+    const int ndx = 2 * range + 1;
+    const int tpb = ndx * ((ndx + k - 1) / k);
+    Shape t{};
+    t.threads = 256;
+    t.k = k;
+    double be = -1.0;
+    int bt = 0;
+    for (int tx = 32; tx >= 2; tx -= (block == 8 ? 2 : 1)) {  // widest first: less halo per block on ties
+        t.tx = tx;
+        if (!me::fs_shape_ok(block, range, t) || me::fs_smem_bytes(block, range, t) > 112 * 1024) continue;
+        const long nt = (long)tx * tpb;
+        const double e = (double)nt / (double)(((nt + 255) / 256) * 256);
+        if (e > be + 1e-3) { be = e; bt = tx; }
+    }
+    return bt > 0 ? bt : 2;
 }
 
 Shape default_shape(me_ctx* c, int algo, int block, int range)
@@ -80,20 +102,7 @@ Shape default_shape(me_ctx* c, int algo, int block, int range)
         s.threads = 256;
         s.ty = 1;
         s.ctas_per_sm = 0;
-        // tile width: least idle threads over the tasks of a tile, shared memory <= 100 KB
-        const int ndx = 2 * range + 1;
-        const int tpb = ndx * ((ndx + s.k - 1) / s.k);
-        double be = -1.0;
-        int bt = 4;
-        for (int tx = 2; tx <= 32; tx += (block == 8 ? 2 : 1)) {
-            Shape t = s;
-            t.tx = tx;
-            if (me::fs_smem_bytes(block, range, t) > 100 * 1024) break;
-            const long nt = (long)tx * tpb;
-            const double e = (double)nt / (double)(((nt + 255) / 256) * 256);
-            if (e > be + 1e-3) { be = e; bt = tx; }
-        }
-        s.tx = bt;
+        s.tx = fs_pick_tx(block, range, s.k);
         return s;
     }
     s.threads = ME_DCDS_THREADS;
@@ -183,6 +192,8 @@ int build_table(const me_frame_desc* d, int n, int block, const Shape& s, bool f
                 int* max_range)
 {
     int tiles = 0, mr = 1;
+    for (int i = 0; i < n; ++i) mr = std::max(mr, d[i].range);
+    const me::FsGeom g = fs ? me::fs_geom(block, mr, s.tx, s.k) : me::FsGeom{};
     for (int i = 0; i < n; ++i) {
         FrameDev f{};
         f.cur = d[i].cur;
@@ -199,6 +210,7 @@ int build_table(const me_frame_desc* d, int n, int block, const Shape& s, bool f
         if (fs) {
             f.tiles_x = (f.nbx + s.tx - 1) / s.tx;
             f.tiles_y = f.nby;
+            if (!me::encode_fs_maps(f, g.nch, me::fs_rows(block, f.range, s.k), s.tx * block, block)) return -1;
         } else {
             f.tiles_x = (f.w + me::kTile - 1) / me::kTile;
             f.tiles_y = (f.h + me::kTile - 1) / me::kTile;
@@ -206,7 +218,6 @@ int build_table(const me_frame_desc* d, int n, int block, const Shape& s, bool f
         }
         f.tile_base = tiles;
         tiles += f.tiles_x * f.tiles_y;
-        mr = std::max(mr, f.range);
         table[i] = f;
     }
     *max_range = mr;
@@ -236,9 +247,9 @@ cudaError_t launch_search(me_ctx* c, void* dev, void* queue, size_t qcap, int n,
 {
     int* head = reinterpret_cast<int*>(dev);
     const FrameDev* table = reinterpret_cast<const FrameDev*>(reinterpret_cast<char*>(dev) + kHeadBytes);
-    if (algo == ME_ALGO_FS) return me::launch_fs(table, n, ntiles, block, max_range, s, st);
     cudaError_t e = cudaMemsetAsync(head, 0, me::kCounterInts * sizeof(int), st);
     if (e != cudaSuccess) return e;
+    if (algo == ME_ALGO_FS) return me::launch_fs(table, n, ntiles, block, max_range, s, head, c->status, c->num_sms, st);
     if (s.kernel == 1)
         return me::launch_dcds_ws(table, n, ntiles, block, max_range, algo == ME_ALGO_DCDS_S, s, head, queue,
                                   (int)qcap, c->status, c->num_sms, st);
@@ -490,10 +501,15 @@ int me_tune_batch(me_ctx* c, const me_frame_desc* descs, int n, int block, int a
     std::vector<Shape> cands;
     if (algo == ME_ALGO_FS) {
         const Shape base = default_shape(c, algo, block, mr);
-        for (int tx = 2; tx <= 32; tx += 2) {
-            Shape s = base;
-            s.tx = tx;
-            if (me::fs_smem_bytes(block, mr, s) <= 100 * 1024) cands.push_back(s);
+        for (int k : {9, 11, 13, 15, 33}) {
+            for (int tx = 4; tx <= 32; tx += (block == 8 ? 2 : 1)) {
+                Shape s = base;
+                s.k = k;
+                s.tx = tx;
+                // rows of work per thread: the picked k and its neighbours
+                if (k != base.k && std::abs(k - base.k) > 2) continue;
+                if (me::fs_shape_ok(block, mr, s)) cands.push_back(s);
+            }
         }
     } else {
         for (int aw : {2, 4, 6}) {

@@ -12,9 +12,9 @@ namespace me {
 constexpr int kTile = 128;
 
 // Device-side view of one frame pair of a launch.  The two tensor maps
-// describe the frames for the TMA unit (DCDS only): the reference window of
-// a tile (box (kTile + 2*rx) x (kTile + 2*R), rx = R rounded up to 16) and
-// the current tile (box kTile x kTile).
+// describe the frames for the TMA unit.  DCDS: the reference window of a
+// tile (box (kTile + 2*rx) x (kTile + 2*R), rx = R rounded up to 16) and the
+// current tile (box kTile x kTile).  FS: see encode_fs_maps.
 struct __align__(128) FrameDev {
     CUtensorMap tm_ref;
     CUtensorMap tm_cur;
@@ -116,9 +116,40 @@ cudaError_t launch_dcds_ws(const FrameDev* frames, int nframes, int ntiles, int 
                            unsigned* status, int num_sms, cudaStream_t st);
 size_t dcds_ws_smem_bytes(int block, int max_range, const Shape& s);
 
-cudaError_t launch_fs(const FrameDev* frames, int nframes, int ntiles, int block, int max_range,
-                      const Shape& s, cudaStream_t st);
+// Full search.  counter: one int zeroed before every launch (the tile counter).
+// Shape: threads 256, tx blocks per tile with tx*block <= 256 (tx even for
+// block 8), k in {9, 11, 13, 15} candidate rows per thread.
+cudaError_t launch_fs(const FrameDev* frames, int nframes, int ntiles, int block, int max_range, const Shape& s,
+                      int* counter, unsigned* status, int num_sms, cudaStream_t st);
 size_t fs_smem_bytes(int block, int max_range, const Shape& s);
+bool fs_shape_ok(int block, int max_range, const Shape& s);
+
+// Reference-window rows of an FS tile: the candidate rows rounded up to
+// whole groups of k, plus the block height.
+__host__ __device__ inline int fs_rows(int block, int range, int k)
+{
+    const int n = 2 * range + 1;
+    return ((n + k - 1) / k) * k + block - 1;
+}
+
+// Shared-memory geometry of an FS launch (for the largest range of the batch).
+struct FsGeom {
+    int nch;         // 16-byte chunks per reference window row (the TMA box's middle dimension)
+    int rwb;         // bytes per staged window row (nch * 16)
+    int rows;        // window rows
+    int raw_stride;  // bytes per staged window
+    int cur_stride;  // bytes per staged current tile
+    int ecols;       // columns of the expanded window
+    int P;           // words per row of the expanded window
+    size_t smem;     // dynamic shared memory per CTA
+};
+FsGeom fs_geom(int block, int max_range, int tx, int k);
+
+// Encode the FS tensor maps of `f`: the reference frame as a 3-D tensor
+// (16 bytes x w/16 chunks x h rows, box 16 x nch x rows) and the current
+// frame as 2-D (box cur_w x block).  Host code; false if the driver rejects
+// the description.
+bool encode_fs_maps(FrameDev& f, int nch, int rows, int cur_w, int block);
 
 cudaError_t launch_eval(const EvalDev* frames, int nframes, int block, int max_blocks, int num_sms,
                         unsigned long long* sums, cudaStream_t st);

@@ -48,4 +48,18 @@ bool encode_frame_maps(FrameDev& f)
            encode_2d(&f.tm_cur, f.cur, f.w, f.h, f.pitch, kTile, kTile);
 }
 
+bool encode_fs_maps(FrameDev& f, int nch, int rows, int cur_w, int block)
+{
+    auto fn = encode_fn();
+    if (!fn || f.w % 16) return false;
+    const cuuint64_t dims[3] = {16, (cuuint64_t)(f.w / 16), (cuuint64_t)f.h};
+    const cuuint64_t strides[2] = {16, (cuuint64_t)f.pitch};
+    const cuuint32_t box[3] = {16, (cuuint32_t)nch, (cuuint32_t)rows};
+    const cuuint32_t es[3] = {1, 1, 1};
+    const bool ok = fn(&f.tm_ref, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<uint8_t*>(f.ref), dims, strides, box,
+                       es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                       CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    return ok && encode_2d(&f.tm_cur, f.cur, f.w, f.h, f.pitch, cur_w, block);
+}
+
 }  // namespace me
