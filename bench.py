@@ -42,6 +42,7 @@ def _args():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--pairs", type=int, default=NPAIRS)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-learned", action="store_true")
     return p.parse_args()
 
 
@@ -150,6 +151,68 @@ class Clocks:
                     reasons.add(n)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- learned proposal
+
+def learned_leg(ctx, me, torch, dev, curs, refs, mv_plain, mv_fs, st_plain, nb, npairs,
+                train_seqs=60, steps=3000):
+    """Train the start proposal on full-search fields of synthetic CIF pairs
+    with the benchmark's motion statistics (seeds from 100000, disjoint from
+    the benchmark's), then run the learned-start search on the benchmark
+    batch.  Reports its throughput (one call of the C-ABI entry point, which
+    runs the CNN trunk and the wavefront search), NSP and PSNR beside plain
+    DCDS."""
+    from paper_0806_0689_gb300 import synth
+    t0 = time.perf_counter()
+    items, keep = [], []
+    for sd in range(train_seqs):
+        s = synth.workload_sequence("cif", 6, seed=100000 + sd, max_motion=R_)
+        for t in range(1, 6):
+            c = torch.from_numpy(s[t]).to(dev)
+            r = torch.from_numpy(s[t - 1]).to(dev)
+            n_cif = (352 // 16) * (288 // 16)
+            m = torch.zeros((n_cif, 2), dtype=torch.int16, device=dev)
+            sd_ = torch.zeros(n_cif, dtype=torch.int32, device=dev)
+            ns = torch.zeros(n_cif, dtype=torch.int16, device=dev)
+            keep.append((c, r, m, sd_, ns))
+            items.append((c, r, R_, m, sd_, ns))
+    descs = me.Context.frame_descs(items)
+    ctx.me_estimate_batch(descs, B_, "fs")  # labels: this library's full search
+    torch.cuda.synchronize()
+    prop = ctx.me_proposal_create()
+    ctx.me_proposal_set_params(prop, me.proposal_init_params(0))
+    losses = me.train_proposal(ctx, prop, descs, steps=steps, lr=3e-3, pairs_per_step=4)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    mv_l = torch.empty_like(mv_plain)
+    sad_l = torch.empty((npairs, nb), dtype=torch.int32, device=dev)
+    nsp_l = torch.empty((npairs, nb), dtype=torch.int16, device=dev)
+    d_l = me.Context.frame_descs((curs[i], refs[i], R_, mv_l[i], sad_l[i], nsp_l[i]) for i in range(npairs))
+    ctx.me_estimate_learned_batch(prop, d_l)  # warm-up
+    ts = []
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ctx.me_estimate_learned_batch(prop, d_l)
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    sums = torch.zeros((npairs, me.ME_NSUMS), dtype=torch.int64, device=dev)
+    e_l = me.Context.eval_descs((curs[i], refs[i], mv_l[i], mv_fs[i], nsp_l[i]) for i in range(npairs))
+    ctx.me_eval_batch(e_l, B_, sums)
+    torch.cuda.synchronize()
+    st = [ctx.me_stats_from_sums(r) for r in sums.cpu().numpy().view(np.uint64)]
+    ctx.me_proposal_free(prop)
+    mean = lambda rows, k: float(np.mean([r[k] for r in rows]))
+    ms = float(np.median(ts))
+    return {"macroblocks_per_s": npairs * nb / (ms * 1e-3), "ms_per_batch": ms,
+            "nsp_per_mb": mean(st, "nsp"), "psnr_db": mean(st, "psnr"),
+            "plain_nsp_per_mb": mean(st_plain, "nsp"), "plain_psnr_db": mean(st_plain, "psnr"),
+            "psnr_minus_plain_db": mean(st, "psnr") - mean(st_plain, "psnr"),
+            "distance_to_fs": mean(st, "distance"), "probability_fs": mean(st, "probability"),
+            "training": {"pairs": len(items), "steps": steps, "final_loss": float(np.mean(losses[-50:])),
+                         "seconds": t_train, "labels": "full-search fields from this library (CIF, seeds >= 100000)"}}
 
 
 # ---------------------------------------------------------------- reference arm
@@ -376,6 +439,8 @@ def main():
     }
     if cb is not None:
         line["cpu_baseline"] = cb
+    if not a.no_learned:
+        line["learned"] = learned_leg(ctx, me, torch, dev, curs, refs, mv, mv_fs, st_d, nb, npairs)
     ctx.me_graph_free(g_dcds)
     ctx.me_graph_free(g_fs)
     if rank == 0:

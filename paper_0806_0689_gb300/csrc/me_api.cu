@@ -253,6 +253,9 @@ cudaError_t launch_search(me_ctx* c, void* dev, void* queue, size_t qcap, int n,
     if (s.kernel == 1)
         return me::launch_dcds_ws(table, n, ntiles, block, max_range, algo == ME_ALGO_DCDS_S, s, head, queue,
                                   (int)qcap, c->status, c->num_sms, st);
+    if (s.kernel == 2)
+        return me::launch_dcds_stream(table, n, ntiles, block, max_range, algo == ME_ALGO_DCDS_S, s, head,
+                                      c->status, c->num_sms, st);
     return me::launch_dcds(table, n, ntiles, block, max_range, algo == ME_ALGO_DCDS_S, s, head, c->status,
                            c->num_sms, st);
 }
@@ -512,6 +515,15 @@ int me_tune_batch(me_ctx* c, const me_frame_desc* descs, int n, int block, int a
             }
         }
     } else {
+        for (int th : {512, 384}) {
+            for (int stages : {3, 2}) {
+                Shape s = default_shape(c, algo, block, mr);
+                s.kernel = 2;
+                s.threads = th;
+                s.stages = stages;
+                if (me::dcds_stream_smem_bytes(block, mr, s) <= 227 * 1024) cands.push_back(s);
+            }
+        }
         for (int aw : {2, 4, 6}) {
             Shape s = default_shape(c, algo, block, mr);
             s.kernel = 1;

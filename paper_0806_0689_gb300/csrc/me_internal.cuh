@@ -51,7 +51,7 @@ struct Shape {
     int ctas_per_sm;   // persistent grid = ctas_per_sm * SM count (0 = occupancy)
     int k;             // FS: candidate rows per thread
     int stages;        // DCDS tile-phase kernel: 1 = load each tile when needed, 2 = prefetch
-    int kernel;        // DCDS: 0 = tile-phase kernel (dcds.cu), 1 = warp-specialised kernel (dcds_ws.cu)
+    int kernel;        // DCDS: 0 = tile-phase (dcds.cu), 1 = warp-specialised (dcds_ws.cu), 2 = streaming (dcds_stream.cu)
     int a_warps;       // DCDS warp-specialised: warps per CTA that stage tiles and run step 1
 };
 
@@ -115,6 +115,13 @@ cudaError_t launch_dcds_ws(const FrameDev* frames, int nframes, int ntiles, int 
                            bool simplified, const Shape& s, int* counters, void* queue, int max_items,
                            unsigned* status, int num_sms, cudaStream_t st);
 size_t dcds_ws_smem_bytes(int block, int max_range, const Shape& s);
+
+// Streaming DCDS: one CTA per SM, s.stages (2 or 3) resident tiles, s.threads
+// (128..512) threads.  head: the tile counter, zeroed before every launch.
+cudaError_t launch_dcds_stream(const FrameDev* frames, int nframes, int ntiles, int block, int max_range,
+                               bool simplified, const Shape& s, int* head, unsigned* status, int num_sms,
+                               cudaStream_t st);
+size_t dcds_stream_smem_bytes(int block, int max_range, const Shape& s);
 
 // Full search.  counter: one int zeroed before every launch (the tile counter).
 // Shape: threads 256, tx blocks per tile with tx*block <= 256 (tx even for

@@ -306,6 +306,9 @@ DCDS_SHAPES = {
     "ws256_a6": "8 8 256 0 1 1 6",
     "ws128_a1": "8 8 128 0 1 1 1",
     "ws128_a4": "8 8 128 0 1 1 4",
+    "stream512_s3": "8 8 512 0 3 2 4",
+    "stream384_s2": "8 8 384 0 2 2 4",
+    "stream128_s3": "8 8 128 0 3 2 4",
 }
 
 
@@ -330,7 +333,7 @@ def test_every_dcds_kernel_shape(tmp_path, cif, shape):
         c2.close()
 
 
-@pytest.mark.parametrize("shape", ["ws256_a2", "tile128_s2"])
+@pytest.mark.parametrize("shape", ["ws256_a2", "tile128_s2", "stream512_s3"])
 def test_dcds_shape_graph_replays(tmp_path, qcif, shape):
     """Graph replays of a forced shape: a mixed-size batch, replayed with
     the outputs cleared in between, matches the oracle every time."""
