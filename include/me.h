@@ -155,6 +155,30 @@ int me_graph_create(me_ctx* ctx, const me_frame_desc* descs, int n, int block, i
 int me_graph_launch(me_ctx* ctx, me_graph* g, void* stream);
 void me_graph_free(me_graph* g);
 
+/* me_estimate_eval_batch: me_estimate_batch (DCDS or DCDS^S) with the
+ * evaluation of Sec. IV fused into the search.  The search writes mv, sad
+ * and nsp as me_estimate_batch does; in the same pass, from the tiles it has
+ * already staged, it forms for every frame i exactly the ME_NSUMS sums that
+ * me_eval_batch would compute for the resulting motion field with
+ * mv = descs[i].mv, nsp = descs[i].nsp and mv_fs = mv_fs[i], so the frames are
+ * read from memory once per step instead of twice.
+ *   mv_fs: HOST array of n DEVICE pointers to full-search fields ([nb][2]
+ *          int16, 4-byte aligned); the array or any entry may be NULL (then
+ *          ME_SUM_EQUAL and ME_SUM_DIST_Q24 are 0 and ME_SUM_HAS_FS is 0).
+ *   sums:  DEVICE uint64 [n][ME_NSUMS], 8-byte aligned, overwritten.
+ * algo other than DCDS / DCDS^S: ME_ERR_UNSUPPORTED.  Argument errors as for
+ * me_estimate_batch, plus a NULL or misaligned sums.  The tile-phase kernel
+ * runs this path whatever launch shape the tuner chose. */
+int me_estimate_eval_batch(me_ctx* ctx, const me_frame_desc* descs, const int16_t* const* mv_fs, int n,
+                           int block, int algo, uint64_t* sums, void* stream);
+
+/* me_graph_create_eval: me_graph_create for me_estimate_eval_batch (the
+ * sums are reset and refilled by every replay).  The mv_fs array is read
+ * before the call returns; the fields it points to and sums must stay
+ * allocated while the graph exists. */
+int me_graph_create_eval(me_ctx* ctx, const me_frame_desc* descs, const int16_t* const* mv_fs, int n,
+                         int block, int algo, uint64_t* sums, me_graph** out);
+
 /* ---------------------------------------------------------------------- */
 /* Learned start proposal.  Not in the paper: the task adds a small CNN that  */
 /* proposes a start point and a horizontal/vertical prior for DCDS, in the    */

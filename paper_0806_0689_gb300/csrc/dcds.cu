@@ -29,6 +29,14 @@
 //     skipping it leaves the path unchanged.
 //   * Ties: candidates are compared in the fixed pattern order with a strict
 //     "<", so the centre and earlier points keep a tie (the oracle's order).
+//   * With EVAL the measures of Sec. IV are fused in, from the staged tile,
+//     so the frames are read once: sum |e| is the SAD at the final MV, sum e^2
+//     takes one pass over the block at that MV (during the HCSP for blocks
+//     whose centre wins; for the others in a dense pass over the ring after
+//     the rounds, where phase B left each block's final MV, SAD and count),
+//     the MV is compared with the full-search MV, and each warp adds its
+//     tile sums to the frame's eight counters with integer atomics -- the
+//     same sums the evaluation kernel computes.
 #include "dcds_common.cuh"
 
 #include <algorithm>
@@ -39,7 +47,27 @@ namespace {
 
 using namespace dcds;
 
-template <int B, bool SIMPL, int NST>
+// Sec. IV measures of one finished block into the thread's sums.
+// Sec. IV sums of one finished block into the thread's tile sums e = {ABS, SQ,
+// NSP, EQUAL, PIXELS} (32 bits hold a tile's worth) and dist.  fw: the block's
+// full-search MV.
+__device__ __forceinline__ void eval_block(int dx, int dy, uint32_t sad, uint32_t sq, int nsp, bool has_nsp,
+                                           bool has_fs, uint32_t fw, int bb, uint32_t (&e)[5],
+                                           unsigned long long& dist)
+{
+    e[0] += sad;
+    e[1] += sq;
+    if (has_nsp) e[2] += (unsigned)nsp;
+    if (has_fs) {
+        const int ex = dx - (int)(int16_t)(fw & 0xffffu), ey = dy - (int)(int16_t)(fw >> 16);
+        // most blocks find the FS vector: skip the (slow) fp64 square root for them
+        if (ex == 0 && ey == 0) e[3] += 1u;
+        else dist += (unsigned long long)__double2ll_rn(sqrt((double)(ex * ex + ey * ey)) * 16777216.0);
+    }
+    e[4] += (unsigned)bb;
+}
+
+template <int B, bool SIMPL, int NST, bool EVAL>
 __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ frames, int nframes, int ntiles,
                                                    int max_range, int* __restrict__ head,
                                                    unsigned* __restrict__ status)
@@ -69,6 +97,8 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
     const int ngroups = blockDim.x >> 2;
 
     for (int i = tid; i < ngroups * nwb; i += blockDim.x) bm_all[i] = 0u;
+    uint32_t esum[5] = {0u, 0u, 0u, 0u, 0u};  // EVAL: this tile's ABS SQ NSP EQUAL PIXELS
+    unsigned long long edist = 0ull;          // EVAL: this tile's DIST_Q24
     if (tid == 0) {
         for (int s = 0; s < NST; ++s) mbar_init(&s_bar[s], 1);
         fence_mbar_init();
@@ -102,6 +132,7 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
         uint32_t* __restrict__ out_mv = reinterpret_cast<uint32_t*>(Fp->mv);
         uint32_t* __restrict__ out_sad = Fp->sad;
         uint16_t* __restrict__ out_nsp = Fp->nsp;
+        const uint32_t* __restrict__ mv_fs = EVAL ? reinterpret_cast<const uint32_t*>(Fp->mv_fs) : nullptr;
         const int lt = t - Fp->tile_base;
         const int txs = Fp->tiles_x;
         const int tile_y = lt / txs, tile_x = lt - tile_y * txs;
@@ -116,12 +147,15 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
             const int g = lane / GA, w = lane % GA;
             const int bxg = bx0 + g, byg = by0 + row;
             const bool exists = bxg < NBX && byg < NBY;
+            uint32_t fw0 = 0u;  // the FS vector, fetched now so its latency hides behind the SADs
+            if (EVAL && mv_fs && exists && w == 0) fw0 = __ldg(mv_fs + (size_t)byg * NBX + bxg);
             uint32_t cw[B];
             const uint32_t* cp = reinterpret_cast<const uint32_t*>(curS + (row * B) * kTile + g * B + 4 * w);
 #pragma unroll
             for (int r = 0; r < B; ++r) cw[r] = cp[r * (kTile / 4)];
             const uint8_t* base = win + (row * B + R - 1) * WP + rx + g * B + 4 * w - 4;
             uint32_t acc[7];
+            uint32_t sq0 = 0u;  // sum of squared errors at (0,0), EVAL only
 #pragma unroll
             for (int k = 0; k < 7; ++k) acc[k] = 0u;
 #pragma unroll
@@ -130,6 +164,10 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
                 const uint32_t b = rp[1];
                 if (jj >= 0 && jj < B) {
                     const uint32_t a = rp[0], c = rp[2];
+                    if constexpr (EVAL) {
+                        const uint32_t d0 = __vabsdiffu4(b, cw[jj]);
+                        sq0 = __dp4a(d0, d0, sq0);
+                    }
                     acc[0] = sadacc<V>(b, cw[jj], acc[0]);
                     acc[1] = sadacc<V>(__funnelshift_r(a, b, 24), cw[jj], acc[1]);
                     acc[2] = sadacc<V>(__funnelshift_r(b, c, 8), cw[jj], acc[2]);
@@ -140,9 +178,11 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
                 if (jj - 1 >= 0 && jj - 1 < B) acc[4] = sadacc<V>(b, cw[jj - 1], acc[4]);  // (0,+1)
             }
 #pragma unroll
-            for (int o = 1; o < GA; o <<= 1)
+            for (int o = 1; o < GA; o <<= 1) {
 #pragma unroll
                 for (int k = 0; k < 7; ++k) acc[k] += __shfl_xor_sync(FULL, acc[k], o);
+                if constexpr (EVAL) sq0 += __shfl_xor_sync(FULL, sq0, o);
+            }
             const int px = bxg * B, py = byg * B;
             unsigned vmask = 0x7fu;  // all 7 HCSP points inside the window and the frame
             if (R < 2 || px < 2 || px > W - B - 2 || py < 1 || py > H - B - 1) {
@@ -167,6 +207,9 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
                 out_mv[blk] = 0u;
                 out_sad[blk] = bs;
                 if (out_nsp) out_nsp[blk] = (uint16_t)__popc(vmask);
+                if constexpr (EVAL)
+                    eval_block(0, 0, bs, sq0, __popc(vmask), out_nsp != nullptr, mv_fs != nullptr, fw0, B * B, esum,
+                               edist);
             }
             const bool cont = leader && best != 0;
             const unsigned bal = __ballot_sync(FULL, cont);
@@ -205,6 +248,7 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
             uint32_t bsad = 0;
             int dxlo = 0, dxhi = 0, dylo = 0, dyhi = 0, wx0 = 0, wy0 = 0;
             size_t blk = 0;
+            int ridx = 0, rmb = 0;                    // EVAL: the block's ring entry and tile position
             uint32_t ds0 = kUnknown, ds1 = kUnknown;  // distant-point SADs of this round (DCDS^S)
             int wmin = INT_MAX, wmax = -1;            // bitmap words this lane has set
             uint32_t cb[RPL];
@@ -231,6 +275,8 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
                             const int bxg = bx0 + bxl, byg = by0 + byl;
                             const int px = bxg * B, py = byg * B;
                             blk = (size_t)byg * NBX + bxg;
+                            ridx = idx;
+                            rmb = mb;
                             dxlo = max(-R, -px); dxhi = min(R, W - B - px);
                             dylo = max(-R, -py); dyhi = min(R, H - B - py);
                             wx0 = rx + bxl * B + 4 * wb;
@@ -274,7 +320,7 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
                     if (SIMPL && pick >= 0) { code >>= 6 * pick; npts = 1; }
                 }
                 const bool counted = !(SIMPL && phase == PH_SIDE);
-                bool valid = false, fresh = false;
+                bool valid = false, fresh = false, fin = false;
                 int bit = 0;
                 if (act == 1 && l4 < npts) {
                     int ox, oy;
@@ -379,9 +425,74 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
                         for (int i = wmin; i <= wmax; ++i) bm[i] = 0u;
                         wmin = INT_MAX; wmax = -1;
                         act = 0;
+                        // the ring entry now holds the final result for the evaluation pass
+                        if (EVAL && l4 == 0)
+                            ring[ridx] = make_uint2((uint32_t)rmb | ((uint32_t)(bxp + 32) << 8) |
+                                                        ((uint32_t)(byp + 32) << 16),
+                                                    bsad | ((uint32_t)nsp << 16));
                     }
                 }
                 __syncwarp();  // bitmap updates and clears are ordered before the next round
+            }
+        }
+        if constexpr (EVAL) {
+            // ---- phase C: squared error of every ring block at its final MV (dense, 4 lanes per block) ----
+            __syncthreads();
+            const int nring = s_ring_n;
+            const int gq = tid >> 2, l4 = lane & 3;
+            const int wb = l4 % WPB, rb = l4 / WPB;
+            for (int base = 0; base < nring; base += ngroups) {
+                const int i = base + gq;
+                const bool ok = i < nring;
+                uint32_t q = 0u, fw = 0u, fsad = 0u;
+                int dx = 0, dy = 0, fnsp = 0;
+                if (ok) {
+                    const uint2 e = ring[i];
+                    const int mb = (int)(e.x & 255u);
+                    dx = (int)((e.x >> 8) & 255u) - 32;
+                    dy = (int)((e.x >> 16) & 255u) - 32;
+                    fsad = e.y & 0xffffu;
+                    fnsp = (int)(e.y >> 16);
+                    const int bxl = mb % TXB, byl = mb / TXB;
+                    if (mv_fs && l4 == 0) fw = __ldg(mv_fs + (size_t)(by0 + byl) * NBX + bx0 + bxl);
+                    const int c0 = rx + bxl * B + 4 * wb + dx;
+                    const uint8_t* p0 = win + (R + byl * B + rb * RPL + dy) * WP + (c0 & ~3);
+                    const unsigned s0 = (unsigned)(c0 & 3) * 8u;
+                    const uint32_t* cp = reinterpret_cast<const uint32_t*>(curS + (byl * B + rb * RPL) * kTile +
+                                                                           bxl * B + 4 * wb);
+#pragma unroll
+                    for (int r = 0; r < RPL; ++r) {
+                        const uint32_t l0 = *reinterpret_cast<const uint32_t*>(p0 + r * WP);
+                        const uint32_t h0 = *reinterpret_cast<const uint32_t*>(p0 + r * WP + 4);
+                        const uint32_t d = __vabsdiffu4(__funnelshift_r(l0, h0, s0), cp[r * (kTile / 4)]);
+                        q = __dp4a(d, d, q);
+                    }
+                }
+                q += __shfl_xor_sync(FULL, q, 1);
+                q += __shfl_xor_sync(FULL, q, 2);
+                if (ok && l4 == 0)
+                    eval_block(dx, dy, fsad, q, fnsp, out_nsp != nullptr, mv_fs != nullptr, fw, B * B, esum, edist);
+            }
+            // this tile's sums: one atomic per warp and counter
+            unsigned long long* fs = Fp->sums;
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+                uint32_t v = esum[k];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+                if (lane == 0 && v) atomicAdd(fs + (k < 4 ? k : 6), (unsigned long long)v);
+                esum[k] = 0u;
+            }
+            {
+                unsigned long long v = edist;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+                if (lane == 0 && v) atomicAdd(fs + 4, v);
+                edist = 0ull;
+            }
+            if (tid == 0 && lt == 0) {
+                fs[5] = (unsigned long long)NBX * NBY;
+                fs[7] = Fp->mv_fs ? 1ull : 0ull;
             }
         }
         __syncthreads();  // every read of this stage is done
@@ -392,12 +503,12 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
     }
 }
 
-template <int B, bool SIMPL, int NST>
+template <int B, bool SIMPL, int NST, bool EVAL>
 cudaError_t launch_t(const FrameDev* frames, int nframes, int ntiles, int max_range, const Shape& s, int* head,
                      unsigned* status, int num_sms, cudaStream_t st)
 {
     const size_t smem = dcds_smem_bytes(B, max_range, s);
-    auto kern = dcds_kernel<B, SIMPL, NST>;
+    auto kern = dcds_kernel<B, SIMPL, NST, EVAL>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
@@ -414,10 +525,16 @@ cudaError_t launch_t(const FrameDev* frames, int nframes, int ntiles, int max_ra
 
 template <int B, bool SIMPL>
 cudaError_t launch_b(const FrameDev* frames, int nframes, int ntiles, int max_range, const Shape& s, int* head,
-                     unsigned* status, int num_sms, cudaStream_t st)
+                     unsigned* status, int num_sms, bool eval, cudaStream_t st)
 {
-    if (s.stages == 2) return launch_t<B, SIMPL, 2>(frames, nframes, ntiles, max_range, s, head, status, num_sms, st);
-    return launch_t<B, SIMPL, 1>(frames, nframes, ntiles, max_range, s, head, status, num_sms, st);
+    if (eval) {
+        if (s.stages == 2)
+            return launch_t<B, SIMPL, 2, true>(frames, nframes, ntiles, max_range, s, head, status, num_sms, st);
+        return launch_t<B, SIMPL, 1, true>(frames, nframes, ntiles, max_range, s, head, status, num_sms, st);
+    }
+    if (s.stages == 2)
+        return launch_t<B, SIMPL, 2, false>(frames, nframes, ntiles, max_range, s, head, status, num_sms, st);
+    return launch_t<B, SIMPL, 1, false>(frames, nframes, ntiles, max_range, s, head, status, num_sms, st);
 }
 
 template <int B, bool SIMPL, int NST>
@@ -425,12 +542,11 @@ int occupancy_t(int max_range, const Shape& s)
 {
     int per_sm = 0;
     const size_t smem = dcds_smem_bytes(B, max_range, s);
-    if (cudaFuncSetAttribute(dcds_kernel<B, SIMPL, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+    auto kern = dcds_kernel<B, SIMPL, NST, false>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared) !=
             cudaSuccess ||
-        cudaFuncSetAttribute(dcds_kernel<B, SIMPL, NST>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             cudaSharedmemCarveoutMaxShared) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dcds_kernel<B, SIMPL, NST>, s.threads, smem) !=
-            cudaSuccess)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, s.threads, smem) != cudaSuccess)
         return 0;
     return per_sm;
 }
@@ -459,14 +575,14 @@ int dcds_ctas_per_sm(int block, int max_range, bool simplified, const Shape& s)
 
 cudaError_t launch_dcds(const FrameDev* frames, int nframes, int ntiles, int block, int max_range,
                         bool simplified, const Shape& s, int* head, unsigned* status, int num_sms,
-                        cudaStream_t st)
+                        cudaStream_t st, bool eval)
 {
     if (s.threads != 128 && s.threads != 256) return cudaErrorInvalidValue;
     if (block == 16)
-        return simplified ? launch_b<16, true>(frames, nframes, ntiles, max_range, s, head, status, num_sms, st)
-                          : launch_b<16, false>(frames, nframes, ntiles, max_range, s, head, status, num_sms, st);
-    return simplified ? launch_b<8, true>(frames, nframes, ntiles, max_range, s, head, status, num_sms, st)
-                      : launch_b<8, false>(frames, nframes, ntiles, max_range, s, head, status, num_sms, st);
+        return simplified ? launch_b<16, true>(frames, nframes, ntiles, max_range, s, head, status, num_sms, eval, st)
+                          : launch_b<16, false>(frames, nframes, ntiles, max_range, s, head, status, num_sms, eval, st);
+    return simplified ? launch_b<8, true>(frames, nframes, ntiles, max_range, s, head, status, num_sms, eval, st)
+                      : launch_b<8, false>(frames, nframes, ntiles, max_range, s, head, status, num_sms, eval, st);
 }
 
 }  // namespace me

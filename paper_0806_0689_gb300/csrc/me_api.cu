@@ -188,8 +188,15 @@ int ensure_queue(me_ctx* c, void** q, size_t* qcap, size_t entries)
 
 // Fill the device-side table (tiles per frame, TMA maps for DCDS) into
 // `table`; returns the number of tiles, or -1 if a tensor map is rejected.
+// Fused evaluation of a DCDS batch: mv_fs (host array of n device pointers,
+// nullable) and the device sums [n][ME_NSUMS].
+struct EvalArgs {
+    const int16_t* const* mv_fs = nullptr;
+    uint64_t* sums = nullptr;
+};
+
 int build_table(const me_frame_desc* d, int n, int block, const Shape& s, bool fs, FrameDev* table,
-                int* max_range)
+                int* max_range, const EvalArgs* ev = nullptr)
 {
     int tiles = 0, mr = 1;
     for (int i = 0; i < n; ++i) mr = std::max(mr, d[i].range);
@@ -215,6 +222,10 @@ int build_table(const me_frame_desc* d, int n, int block, const Shape& s, bool f
             f.tiles_x = (f.w + me::kTile - 1) / me::kTile;
             f.tiles_y = (f.h + me::kTile - 1) / me::kTile;
             if (!me::encode_frame_maps(f)) return -1;
+        }
+        if (ev && ev->sums) {
+            f.sums = reinterpret_cast<unsigned long long*>(ev->sums) + (size_t)ME_NSUMS * i;
+            f.mv_fs = ev->mv_fs ? ev->mv_fs[i] : nullptr;
         }
         f.tile_base = tiles;
         tiles += f.tiles_x * f.tiles_y;
@@ -243,12 +254,23 @@ int validate_batch(me_ctx* c, const me_frame_desc* d, int n, int block, int algo
 // Launch the search over a table already on the device at `dev` (queue: the
 // DCDS item queue of `qcap` entries, for the warp-specialised kernel).
 cudaError_t launch_search(me_ctx* c, void* dev, void* queue, size_t qcap, int n, int ntiles, int block, int algo,
-                          int max_range, const Shape& s, cudaStream_t st)
+                          int max_range, const Shape& s, cudaStream_t st, const EvalArgs* ev = nullptr)
 {
     int* head = reinterpret_cast<int*>(dev);
     const FrameDev* table = reinterpret_cast<const FrameDev*>(reinterpret_cast<char*>(dev) + kHeadBytes);
     cudaError_t e = cudaMemsetAsync(head, 0, me::kCounterInts * sizeof(int), st);
     if (e != cudaSuccess) return e;
+    if (ev && ev->sums) {
+        // the fused evaluation runs in the tile-phase kernel; its sums accumulate from zero
+        e = cudaMemsetAsync(ev->sums, 0, sizeof(uint64_t) * ME_NSUMS * (size_t)n, st);
+        if (e != cudaSuccess) return e;
+        Shape t = s;
+        if (t.kernel != 0) t = default_shape(c, algo, block, max_range);
+        t.kernel = 0;
+        t.threads = 128;  // the fused variant uses more registers: small CTAs keep four per SM
+        return me::launch_dcds(table, n, ntiles, block, max_range, algo == ME_ALGO_DCDS_S, t, head, c->status,
+                               c->num_sms, st, true);
+    }
     if (algo == ME_ALGO_FS) return me::launch_fs(table, n, ntiles, block, max_range, s, head, c->status, c->num_sms, st);
     if (s.kernel == 1)
         return me::launch_dcds_ws(table, n, ntiles, block, max_range, algo == ME_ALGO_DCDS_S, s, head, queue,
@@ -267,7 +289,8 @@ size_t total_blocks(const me_frame_desc* d, int n, int block)
     return t;
 }
 
-int run_batch(me_ctx* c, const me_frame_desc* d, int n, int block, int algo, const Shape& s, cudaStream_t st)
+int run_batch(me_ctx* c, const me_frame_desc* d, int n, int block, int algo, const Shape& s, cudaStream_t st,
+              const EvalArgs* ev = nullptr)
 {
     const size_t bytes = kHeadBytes + sizeof(FrameDev) * (size_t)n;
     Slot* slot = nullptr;
@@ -275,7 +298,7 @@ int run_batch(me_ctx* c, const me_frame_desc* d, int n, int block, int algo, con
     if (rc != ME_OK) return rc;
     FrameDev* table = reinterpret_cast<FrameDev*>(reinterpret_cast<char*>(slot->host) + kHeadBytes);
     int max_range = 1;
-    const int ntiles = build_table(d, n, block, s, algo == ME_ALGO_FS, table, &max_range);
+    const int ntiles = build_table(d, n, block, s, algo == ME_ALGO_FS, table, &max_range, ev);
     if (ntiles < 0) return fail(c, ME_ERR_CUDA, "cuTensorMapEncodeTiled rejected a frame description");
     cudaError_t e = cudaMemcpyAsync(slot->dev, slot->host, bytes, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "descriptor upload");
@@ -283,7 +306,7 @@ int run_batch(me_ctx* c, const me_frame_desc* d, int n, int block, int algo, con
         rc = ensure_queue(c, &slot->queue, &slot->qcap, total_blocks(d, n, block));
         if (rc != ME_OK) return rc;
     }
-    e = launch_search(c, slot->dev, slot->queue, slot->qcap, n, ntiles, block, algo, max_range, s, st);
+    e = launch_search(c, slot->dev, slot->queue, slot->qcap, n, ntiles, block, algo, max_range, s, st, ev);
     if (e != cudaSuccess) return cuda_fail(c, e, "search launch");
     e = cudaEventRecord(slot->done, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaEventRecord");
@@ -375,18 +398,20 @@ int me_estimate_batch(me_ctx* c, const me_frame_desc* descs, int n, int block, i
     return run_batch(c, descs, n, block, algo, pick_shape(c, algo, block, mr, mw, mh), (cudaStream_t)stream);
 }
 
-int me_graph_create(me_ctx* c, const me_frame_desc* descs, int n, int block, int algo, me_graph** out)
+}  // extern "C"
+
+namespace {
+
+int graph_create(me_ctx* c, const me_frame_desc* descs, int n, int block, int algo, const EvalArgs* ev,
+                 me_graph** out)
 {
-    if (!c || !out) return ME_ERR_ARG;
-    *out = nullptr;
-    int rc = validate_batch(c, descs, n, block, algo);
-    if (rc != ME_OK) return rc;
+    int rc = ME_OK;
     int mr = 1, mw = 0, mh = 0;
     for (int i = 0; i < n; ++i) { mr = std::max(mr, descs[i].range); mw = std::max(mw, descs[i].w); mh = std::max(mh, descs[i].h); }
     const Shape s = pick_shape(c, algo, block, mr, mw, mh);
     std::vector<FrameDev> table(n);
     int max_range = 1;
-    const int ntiles = build_table(descs, n, block, s, algo == ME_ALGO_FS, table.data(), &max_range);
+    const int ntiles = build_table(descs, n, block, s, algo == ME_ALGO_FS, table.data(), &max_range, ev);
     if (ntiles < 0) return fail(c, ME_ERR_CUDA, "cuTensorMapEncodeTiled rejected a frame description");
     me_graph* g = new me_graph();
     g->ctx = c;
@@ -404,7 +429,7 @@ int me_graph_create(me_ctx* c, const me_frame_desc* descs, int n, int block, int
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        cudaError_t le = launch_search(c, g->dev, g->queue, qcap, n, ntiles, block, algo, max_range, s, cs);
+        cudaError_t le = launch_search(c, g->dev, g->queue, qcap, n, ntiles, block, algo, max_range, s, cs, ev);
         e = cudaStreamEndCapture(cs, &g->graph);
         if (le != cudaSuccess) e = le;
     }
@@ -416,6 +441,60 @@ int me_graph_create(me_ctx* c, const me_frame_desc* descs, int n, int block, int
     }
     *out = g;
     return ME_OK;
+}
+
+int validate_eval(me_ctx* c, const me_frame_desc* descs, const int16_t* const* mv_fs, int n, int algo,
+                  const uint64_t* sums)
+{
+    if (algo != ME_ALGO_DCDS && algo != ME_ALGO_DCDS_S)
+        return fail(c, ME_ERR_UNSUPPORTED, "the fused evaluation is built for DCDS and DCDS^S");
+    if (!sums || !aligned(sums, 8)) return fail(c, ME_ERR_ARG, "sums must be a non-NULL 8-byte aligned device array");
+    for (int i = 0; mv_fs && i < n; ++i)
+        if (mv_fs[i] && !aligned(mv_fs[i], 4)) return fail(c, ME_ERR_ARG, "mv_fs entries must be 4-byte aligned");
+    (void)descs;
+    return ME_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int me_graph_create(me_ctx* c, const me_frame_desc* descs, int n, int block, int algo, me_graph** out)
+{
+    if (!c || !out) return ME_ERR_ARG;
+    *out = nullptr;
+    int rc = validate_batch(c, descs, n, block, algo);
+    if (rc != ME_OK) return rc;
+    return graph_create(c, descs, n, block, algo, nullptr, out);
+}
+
+int me_graph_create_eval(me_ctx* c, const me_frame_desc* descs, const int16_t* const* mv_fs, int n, int block,
+                         int algo, uint64_t* sums, me_graph** out)
+{
+    if (!c || !out) return ME_ERR_ARG;
+    *out = nullptr;
+    int rc = validate_batch(c, descs, n, block, algo);
+    if (rc == ME_OK) rc = validate_eval(c, descs, mv_fs, n, algo, sums);
+    if (rc != ME_OK) return rc;
+    EvalArgs ev;
+    ev.mv_fs = mv_fs;
+    ev.sums = sums;
+    return graph_create(c, descs, n, block, algo, &ev, out);
+}
+
+int me_estimate_eval_batch(me_ctx* c, const me_frame_desc* descs, const int16_t* const* mv_fs, int n, int block,
+                           int algo, uint64_t* sums, void* stream)
+{
+    if (!c) return ME_ERR_ARG;
+    int rc = validate_batch(c, descs, n, block, algo);
+    if (rc == ME_OK) rc = validate_eval(c, descs, mv_fs, n, algo, sums);
+    if (rc != ME_OK) return rc;
+    int mr = 1, mw = 0, mh = 0;
+    for (int i = 0; i < n; ++i) { mr = std::max(mr, descs[i].range); mw = std::max(mw, descs[i].w); mh = std::max(mh, descs[i].h); }
+    EvalArgs ev;
+    ev.mv_fs = mv_fs;
+    ev.sums = sums;
+    return run_batch(c, descs, n, block, algo, pick_shape(c, algo, block, mr, mw, mh), (cudaStream_t)stream, &ev);
 }
 
 int me_graph_launch(me_ctx* c, me_graph* g, void* stream)

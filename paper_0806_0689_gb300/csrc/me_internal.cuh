@@ -28,6 +28,8 @@ struct __align__(128) FrameDev {
     int32_t tiles_x, tiles_y;  // tiles of this frame
     int32_t tile_base;         // first global tile index of this frame
     int32_t pad_[1];
+    const int16_t* mv_fs;      // fused evaluation: the full-search field (may be null)
+    unsigned long long* sums;  // fused evaluation: the frame's eight sums (null: no evaluation)
 };
 
 // Encode the two tensor maps of `f` (its pointers, sizes and range must be
@@ -97,9 +99,11 @@ constexpr int kSadVariant = ME_SAD_VARIANT;
 // ---------------------------------------------------------------------------
 // Host-side launchers (each .cu file owns its kernels).
 // ---------------------------------------------------------------------------
+// eval: fuse the evaluation sums of Sec. IV into the search (FrameDev::sums,
+// zeroed before the launch; FrameDev::mv_fs optional).
 cudaError_t launch_dcds(const FrameDev* frames, int nframes, int ntiles, int block, int max_range,
                         bool simplified, const Shape& s, int* head, unsigned* status, int num_sms,
-                        cudaStream_t st);
+                        cudaStream_t st, bool eval = false);
 size_t dcds_smem_bytes(int block, int max_range, const Shape& s);
 int dcds_ctas_per_sm(int block, int max_range, bool simplified, const Shape& s);
 

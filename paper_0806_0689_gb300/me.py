@@ -26,7 +26,8 @@ EXPORTS = ["me_init", "me_free", "me_last_error", "me_estimate", "me_estimate_ba
            "me_graph_launch", "me_graph_free", "me_eval", "me_eval_batch", "me_stats_from_sums", "me_tune",
            "me_absdiff_peak", "me_check_status", "me_estimate_batch_noalloc", "me_tune_batch",
            "me_proposal_create", "me_proposal_free", "me_proposal_set_params", "me_proposal_get_params",
-           "me_proposal_train_step", "me_proposal_logits", "me_estimate_learned_batch"]
+           "me_proposal_train_step", "me_proposal_logits", "me_estimate_learned_batch",
+           "me_estimate_eval_batch", "me_graph_create_eval"]
 ME_PROPOSAL_NPARAMS = 37532
 ME_PROPOSAL_NLOGITS = 68
 
@@ -168,6 +169,27 @@ class Context:
         g = ctypes.c_void_p()
         self._check(self.L.me_graph_create(self.h, descs, len(descs), block, ALGOS.get(algo, algo),
                                            ctypes.byref(g)))
+        return g
+
+    @staticmethod
+    def _fs_ptrs(mv_fs, n):
+        if mv_fs is None:
+            return None
+        arr = (ctypes.c_void_p * n)(*[None if t is None else t.data_ptr() for t in mv_fs])
+        return arr
+
+    def me_estimate_eval_batch(self, descs, mv_fs, block, algo, sums, stream=None):
+        """DCDS with the evaluation sums fused in; mv_fs: list of device
+        tensors (or None entries) or None; sums: device int64 [n][ME_NSUMS]."""
+        arr = self._fs_ptrs(mv_fs, len(descs))
+        self._check(self.L.me_estimate_eval_batch(self.h, descs, arr, len(descs), block, ALGOS.get(algo, algo),
+                                                  _ptr(sums), _stream(stream)))
+
+    def me_graph_create_eval(self, descs, mv_fs, block, algo, sums):
+        g = ctypes.c_void_p()
+        arr = self._fs_ptrs(mv_fs, len(descs))
+        self._check(self.L.me_graph_create_eval(self.h, descs, arr, len(descs), block, ALGOS.get(algo, algo),
+                                                _ptr(sums), ctypes.byref(g)))
         return g
 
     def me_graph_launch(self, g, stream=None):
