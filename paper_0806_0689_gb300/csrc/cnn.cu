@@ -114,6 +114,238 @@ __global__ void __launch_bounds__(128) gemm_kernel(const __nv_bfloat16* __restri
     }
 }
 
+// ------------------------------------------------------------------ fused trunk (inference)
+// All four convolutions for TS samples at a time, without im2col: each layer
+// is an implicit GEMM whose A fragments are gathered straight from the
+// previous layer's activations in shared memory (NHWC, a pixel padded to
+// PXW words so that the 8 output pixels of a fragment, two input pixels
+// apart, fall on 8 different bank groups), B fragments come from the
+// weights staged once per CTA, and bias + ReLU + bf16 rounding happen in the
+// epilogue.  The arithmetic per output is the im2col path's: bf16 operands,
+// fp32 accumulation, one bf16 rounding of each activation.
+constexpr int TS = 4;     // samples per trunk iteration
+constexpr int PXW = 18;   // smem words per pixel of a 32-channel activation (16 + 2 padding)
+constexpr int WRW = 148;  // smem words per weight row of layers 2-4 (144 + 4 padding)
+
+struct TrunkW {
+    const __nv_bfloat16* w[LAYERS];
+    const float* b[LAYERS];
+};
+
+__device__ __forceinline__ uint32_t pack_relu(float v0, float v1)
+{
+    const __nv_bfloat162 h = __floats2bfloat162_rn(v0 > 0.f ? v0 : 0.f, v1 > 0.f ? v1 : 0.f);
+    return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+// Output pixels of a warp's m-tiles: rows g and g + 8 (h = 0, 1) of m-tile i.
+template <int NM>
+struct Rows {
+    int s[NM][2], oy[NM][2], ox[NM][2];
+};
+
+// One 3x3 stride-2 layer with 32 input channels (implicit GEMM, K = 9 taps x 32)
+// for NM m-tiles and NN n-tiles (from n-tile n0) per warp.
+template <int HIN, int NM, int NN>
+__device__ __forceinline__ void conv32(const uint32_t* __restrict__ in, const uint32_t* __restrict__ Wl,
+                                       const Rows<NM> rw, int n0, float (&acc)[NM][NN][4], int g, int t)
+{
+#pragma unroll
+    for (int i = 0; i < NM; ++i)
+#pragma unroll
+        for (int j = 0; j < NN; ++j)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
+#pragma unroll 1
+    for (int tap = 0; tap < 9; ++tap) {
+        const int ky = tap / 3, kx = tap - 3 * ky;
+        int pix[NM][2];  // word offset of the input pixel, -1 outside (zero padding)
+#pragma unroll
+        for (int i = 0; i < NM; ++i)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int y = 2 * rw.oy[i][h] + ky - 1, x = 2 * rw.ox[i][h] + kx - 1;
+                pix[i][h] = (y >= 0 && y < HIN && x >= 0 && x < HIN) ? ((rw.s[i][h] * HIN + y) * HIN + x) * PXW : -1;
+            }
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            const int w0 = half * 8 + t;  // channel pair 2*w0 (and +8 channels)
+            uint32_t bf[NN][2];
+#pragma unroll
+            for (int j = 0; j < NN; ++j) {
+                const uint32_t* wr = Wl + (size_t)((n0 + j) * 8 + g) * WRW + tap * 16 + half * 8 + t;
+                bf[j][0] = wr[0];
+                bf[j][1] = wr[4];
+            }
+#pragma unroll
+            for (int i = 0; i < NM; ++i) {
+                uint32_t a[4];
+                a[0] = pix[i][0] >= 0 ? in[pix[i][0] + w0] : 0u;
+                a[1] = pix[i][1] >= 0 ? in[pix[i][1] + w0] : 0u;
+                a[2] = pix[i][0] >= 0 ? in[pix[i][0] + w0 + 4] : 0u;
+                a[3] = pix[i][1] >= 0 ? in[pix[i][1] + w0 + 4] : 0u;
+#pragma unroll
+                for (int j = 0; j < NN; ++j) mma_bf16(acc[i][j], a, bf[j]);
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256, 1) trunk_kernel(const __nv_bfloat16* __restrict__ x, int n, TrunkW tw,
+                                                       __nv_bfloat16* __restrict__ a4)
+{
+    extern __shared__ __align__(16) uint32_t tsm[];
+    uint32_t* Ws = tsm;                         // layers 2-4: [3][32][WRW]
+    uint32_t* X = Ws + 3 * 32 * WRW;            // [TS][32][32] pixels of 2 channels (one word)
+    uint32_t* A1 = X + TS * 1024;               // [TS][16][16][PXW]
+    uint32_t* A2 = A1 + TS * 256 * PXW;         // [TS][8][8][PXW]
+    uint32_t* A3 = A2 + TS * 64 * PXW;          // [TS][4][4][PXW]
+    __shared__ float sb[LAYERS][CH];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int g = lane >> 2, t = lane & 3;
+
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+        const uint32_t* wl = reinterpret_cast<const uint32_t*>(tw.w[l + 1]);
+        for (int i = tid; i < 32 * 144; i += blockDim.x) {
+            const int r = i / 144, k = i - r * 144;
+            Ws[(l * 32 + r) * WRW + k] = wl[i];
+        }
+    }
+#pragma unroll
+    for (int l = 0; l < LAYERS; ++l)
+        if (tid < CH) sb[l][tid] = tw.b[l][tid];
+    // layer 1 (K = 18 padded to 32): the B fragments live in registers
+    uint32_t b1[4][2][2];
+    {
+        const uint32_t* w1 = reinterpret_cast<const uint32_t*>(tw.w[0]);  // [32][16] words
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int kt = 0; kt < 2; ++kt) {
+                b1[j][kt][0] = w1[(j * 8 + g) * 16 + kt * 8 + t];
+                b1[j][kt][1] = w1[(j * 8 + g) * 16 + kt * 8 + t + 4];
+            }
+    }
+    __syncthreads();
+
+    for (int s0 = blockIdx.x * TS; s0 < n; s0 += gridDim.x * TS) {
+        const int ns = min(TS, n - s0);
+        const uint32_t* xs = reinterpret_cast<const uint32_t*>(x) + (size_t)s0 * 1024;
+        for (int i = tid; i < TS * 1024; i += blockDim.x) X[i] = (i >> 10) < ns ? xs[i] : 0u;
+        __syncthreads();
+
+        // ---- layer 1: 32x32x2 -> 16x16x32; an m-tile is one output row of 16 pixels ----
+        for (int mt = warp; mt < TS * 16; mt += 8) {
+            const int s = mt >> 4, oy = mt & 15;
+            float acc[4][4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[j][q] = 0.f;
+#pragma unroll
+            for (int kt = 0; kt < 2; ++kt) {
+                uint32_t a[4];
+#pragma unroll
+                for (int qq = 0; qq < 4; ++qq) {
+                    const int tap = kt * 8 + t + ((qq & 2) ? 4 : 0);  // k = 2*tap + c, c = 0, 1 in one word
+                    const int ox = g + ((qq & 1) ? 8 : 0);
+                    uint32_t v = 0u;
+                    if (tap < 9) {
+                        const int y = 2 * oy + tap / 3 - 1, xx = 2 * ox + tap % 3 - 1;
+                        if (y >= 0 && y < 32 && xx >= 0 && xx < 32) v = X[s * 1024 + y * 32 + xx];
+                    }
+                    a[qq] = v;
+                }
+#pragma unroll
+                for (int j = 0; j < 4; ++j) mma_bf16(acc[j], a, b1[j][kt]);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int ox = g + 8 * h, c = j * 8 + 2 * t;
+                    A1[((s * 16 + oy) * 16 + ox) * PXW + j * 4 + t] =
+                        pack_relu(acc[j][2 * h] + sb[0][c], acc[j][2 * h + 1] + sb[0][c + 1]);
+                }
+        }
+        __syncthreads();
+
+        // ---- layer 2: 16x16x32 -> 8x8x32; m-tile = two output rows; two m-tiles per warp ----
+        {
+            Rows<2> rw;
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const int mt = warp + 8 * i;  // 16 m-tiles: sample mt / 4, rows 2*(mt % 4) and +1
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    rw.s[i][h] = mt >> 2;
+                    rw.oy[i][h] = 2 * (mt & 3) + h;
+                    rw.ox[i][h] = g;
+                }
+            }
+            float acc[2][4][4];
+            conv32<16, 2, 4>(A1, Ws, rw, 0, acc, g, t);
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int c = j * 8 + 2 * t;
+                        A2[((rw.s[i][h] * 8 + rw.oy[i][h]) * 8 + rw.ox[i][h]) * PXW + j * 4 + t] =
+                            pack_relu(acc[i][j][2 * h] + sb[1][c], acc[i][j][2 * h + 1] + sb[1][c + 1]);
+                    }
+        }
+        __syncthreads();
+
+        // ---- layer 3: 8x8x32 -> 4x4x32; m-tile = one sample (16 pixels); warp = (sample, half of N) ----
+        {
+            Rows<1> rw;
+            const int s = warp & 3, nh = warp >> 2;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                rw.s[0][h] = s;
+                rw.oy[0][h] = (g >> 2) + 2 * h;  // rows g and g + 8 of the tile: pixel index r = 4 * oy + ox
+                rw.ox[0][h] = g & 3;
+            }
+            float acc[1][2][4];
+            conv32<8, 1, 2>(A2, Ws + 32 * WRW, rw, 2 * nh, acc, g, t);
+#pragma unroll
+            for (int j = 0; j < 2; ++j)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int c = (2 * nh + j) * 8 + 2 * t;
+                    A3[((s * 4 + rw.oy[0][h]) * 4 + rw.ox[0][h]) * PXW + (2 * nh + j) * 4 + t] =
+                        pack_relu(acc[0][j][2 * h] + sb[2][c], acc[0][j][2 * h + 1] + sb[2][c + 1]);
+                }
+        }
+        __syncthreads();
+
+        // ---- layer 4: 4x4x32 -> 2x2x32; one m-tile = 4 samples x 4 pixels; warp = n-tile ----
+        if (warp < 4) {
+            Rows<1> rw;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                rw.s[0][h] = (g >> 2) + 2 * h;  // row r = 4 * sample + pixel
+                rw.oy[0][h] = (g & 3) >> 1;
+                rw.ox[0][h] = g & 1;
+            }
+            float acc[1][1][4];
+            conv32<4, 1, 1>(A3, Ws + 2 * 32 * WRW, rw, warp, acc, g, t);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int s = rw.s[0][h], pix = (g & 3), c = warp * 8 + 2 * t;
+                if (s < ns) {
+                    const uint32_t v = pack_relu(acc[0][0][2 * h] + sb[3][c], acc[0][0][2 * h + 1] + sb[3][c + 1]);
+                    *reinterpret_cast<uint32_t*>(a4 + ((size_t)(s0 + s) * 4 + pix) * CH + c) = v;
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // ------------------------------------------------------------------ im2col / col2im
 // in: NHWC [n][hin][hin][cin] bf16; cols: [n*ho*ho][kp], ho = hin / 2
 __global__ void im2col_kernel(const __nv_bfloat16* __restrict__ in, int n, int hin, int cin, int kp,
@@ -370,6 +602,27 @@ cudaError_t relu_back(const float* da, const __nv_bfloat16* a, long rows, __nv_b
                       cudaStream_t st)
 {
     relu_back_kernel<<<blocks_for(rows, 8, 2048), 256, 0, st>>>(da, a, rows, dz, dbias);
+    return cudaGetLastError();
+}
+
+size_t trunk_smem_bytes()
+{
+    return sizeof(uint32_t) * ((size_t)3 * 32 * WRW + (size_t)TS * 1024 + (size_t)TS * (256 + 64 + 16) * PXW);
+}
+
+cudaError_t trunk(const __nv_bfloat16* x, int n, const __nv_bfloat16* const* w, const float* params,
+                  __nv_bfloat16* a4, int num_sms, cudaStream_t st)
+{
+    TrunkW tw;
+    for (int l = 0; l < LAYERS; ++l) {
+        tw.w[l] = w[l];
+        tw.b[l] = params + PB[l];
+    }
+    const size_t smem = trunk_smem_bytes();
+    cudaError_t e = cudaFuncSetAttribute(trunk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int groups = (n + TS - 1) / TS;
+    trunk_kernel<<<std::max(1, std::min(groups, num_sms)), 256, smem, st>>>(x, n, tw, a4);
     return cudaGetLastError();
 }
 

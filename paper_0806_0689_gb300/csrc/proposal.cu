@@ -116,12 +116,6 @@ __global__ void feat_kernel(const PropFrame* __restrict__ fr, int nframes, long 
     }
 }
 
-__global__ void copy_rows_kernel(const __nv_bfloat16* __restrict__ src, long n, __nv_bfloat16* __restrict__ dst)
-{
-    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
-        dst[i] = src[i];
-}
-
 // ------------------------------------------------------------------ learned-start search
 __device__ __forceinline__ int ld_acquire(const int* p)
 {
@@ -143,44 +137,99 @@ struct WarpBlock {
     uint32_t c0, c1;  // this lane's 8 current pixels (row lane/2, half lane%2)
 };
 
-// SAD of the block at displacement (qx, qy): every lane returns the total
-__device__ __forceinline__ uint32_t warp_sad(const WarpBlock& b, int qx, int qy, int lane)
+// Visit the points (qx[i], qy[i]) of one pattern list: a point outside the
+// window/frame or visited before is skipped; the others are marked, counted
+// and their SADs computed together (all loads issued before any reduction, so
+// the list costs one memory latency).  Returns the mask of evaluated points;
+// v[i] holds their SADs in every lane.
+template <int N>
+__device__ __forceinline__ unsigned visit_many(const WarpBlock& b, uint32_t* bm, int& wmin, int& wmax, int& nsp,
+                                               const int (&qx)[N], const int (&qy)[N], uint32_t (&v)[N], int lane)
 {
-    const int r = lane >> 1, hh = lane & 1;
-    const long g = (long)(b.py + qy + r) * b.pitch + b.px + qx + 8 * hh;
-    const uint32_t* wp = reinterpret_cast<const uint32_t*>(b.ref + (g & ~3l));
-    const unsigned sh = (unsigned)(g & 3) * 8u;
-    const uint32_t w0 = __ldg(wp), w1 = __ldg(wp + 1);
-    const uint32_t w2 = sh ? __ldg(wp + 2) : 0u;  // inside the row whenever the segment is unaligned
-    uint32_t s = me::sadacc<me::kSadVariant>(__funnelshift_r(w0, w1, sh), b.c0, 0u);
-    s = me::sadacc<me::kSadVariant>(__funnelshift_r(w1, w2, sh), b.c1, s);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    return s;
-}
-
-// Visit (qx, qy): false if outside the window/frame or visited before;
-// otherwise marks it, counts it and returns its SAD in *v.
-__device__ __forceinline__ bool visit(const WarpBlock& b, uint32_t* bm, int& wmin, int& wmax, int& nsp, int qx,
-                                      int qy, uint32_t* v, int lane)
-{
-    if (qx < b.dxlo || qx > b.dxhi || qy < b.dylo || qy > b.dyhi) return false;
-    const int bit = (qy + b.R) * (2 * b.R + 1) + (qx + b.R);
-    int seen = 0;
+    unsigned fresh = 0u;
     if (lane == 0) {
-        const uint32_t w = bm[bit >> 5], m = 1u << (bit & 31);
-        seen = (w & m) != 0u;
-        if (!seen) {
+        const int side = 2 * b.R + 1;
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            if (qx[i] < b.dxlo || qx[i] > b.dxhi || qy[i] < b.dylo || qy[i] > b.dyhi) continue;
+            const int bit = (qy[i] + b.R) * side + (qx[i] + b.R);
+            const uint32_t w = bm[bit >> 5], m = 1u << (bit & 31);
+            if (w & m) continue;
             bm[bit >> 5] = w | m;
             wmin = min(wmin, bit >> 5);
             wmax = max(wmax, bit >> 5);
+            fresh |= 1u << i;
         }
     }
-    seen = __shfl_sync(0xffffffffu, seen, 0);
-    if (seen) return false;
-    ++nsp;
-    *v = warp_sad(b, qx, qy, lane);
-    return true;
+    fresh = __shfl_sync(0xffffffffu, fresh, 0);
+    nsp += __popc(fresh);
+    const int r = lane >> 1, hh = lane & 1;
+    uint32_t w0[N], w1[N], w2[N];
+    unsigned sh[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        w0[i] = w1[i] = w2[i] = 0u;
+        sh[i] = 0u;
+        if ((fresh >> i) & 1u) {
+            const long g = (long)(b.py + qy[i] + r) * b.pitch + b.px + qx[i] + 8 * hh;
+            const uint32_t* wp = reinterpret_cast<const uint32_t*>(b.ref + (g & ~3l));
+            sh[i] = (unsigned)(g & 3) * 8u;
+            w0[i] = __ldg(wp);
+            w1[i] = __ldg(wp + 1);
+            if (sh[i]) w2[i] = __ldg(wp + 2);  // inside the row whenever the segment is unaligned
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        uint32_t t = me::sadacc<me::kSadVariant>(__funnelshift_r(w0[i], w1[i], sh[i]), b.c0, 0u);
+        v[i] = me::sadacc<me::kSadVariant>(__funnelshift_r(w1[i], w2[i], sh[i]), b.c1, t);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int i = 0; i < N; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+    return fresh;
+}
+
+// zpart[s][o] = fb[o] + sum over the 128 conv-4 features of fw[o][f] * a4, in
+// the head's order (the neighbour terms are added once the neighbours are
+// final).  A CTA of 4 x 68 threads stages the weights (transposed) once and
+// the features of 32 samples per step; thread (o, q) accumulates output o of
+// samples q, q + 4, ..., in the same order as the head kernel.
+constexpr int kZS = 32;  // samples per step
+__global__ void __launch_bounds__(4 * NLOGIT) zpart_kernel(const __nv_bfloat16* __restrict__ a4, long total,
+                                                           const float* __restrict__ fw,
+                                                           const float* __restrict__ fb, float* __restrict__ zpart)
+{
+    __shared__ float wT[128][NLOGIT];
+    __shared__ float af[kZS][129];
+    const int tid = threadIdx.x, o = tid % NLOGIT, q = tid / NLOGIT;
+    for (int i = tid; i < 128 * NLOGIT; i += blockDim.x) {
+        const int oo = i / 128, f = i - oo * 128;
+        wT[f][oo] = fw[(size_t)oo * NFEAT + f];
+    }
+    const float bias = fb[o];
+    for (long s0 = (long)blockIdx.x * kZS; s0 < total; s0 += (long)gridDim.x * kZS) {
+        __syncthreads();  // wT ready; the previous step's reads of af are done
+        for (int i = tid; i < kZS * 128; i += blockDim.x) {
+            const int ss = i >> 7, f = i & 127;
+            af[ss][f] = (s0 + ss < total) ? __bfloat162float(a4[(size_t)(s0 + ss) * 128 + (f & 3) * 32 + (f >> 2)]) : 0.f;
+        }
+        __syncthreads();
+        float acc[kZS / 4];
+#pragma unroll
+        for (int k = 0; k < kZS / 4; ++k) acc[k] = bias;
+        for (int f = 0; f < 128; ++f) {
+            const float w = wT[f][o];
+#pragma unroll
+            for (int k = 0; k < kZS / 4; ++k) acc[k] += w * af[q + 4 * k][f];
+        }
+#pragma unroll
+        for (int k = 0; k < kZS / 4; ++k) {
+            const long ss = s0 + q + 4 * k;
+            if (ss < total) zpart[ss * NLOGIT + o] = acc[k];
+        }
+    }
 }
 
 __constant__ int8_t kFirstH[6][2] = {{-1, 0}, {1, 0}, {0, -1}, {0, 1}, {-2, 0}, {2, 0}};  // HCSP
@@ -190,8 +239,8 @@ __constant__ int8_t kMid[2][2][2] = {{{-1, 0}, {1, 0}}, {{0, -1}, {0, 1}}};
 
 __global__ void __launch_bounds__(256) learned_dcds_kernel(const PropFrame* __restrict__ fr, int nframes,
                                                            const int* __restrict__ order, int total,
-                                                           const __nv_bfloat16* __restrict__ a4,
-                                                           const float* __restrict__ fw, const float* __restrict__ fb,
+                                                           const float* __restrict__ zpart,
+                                                           const float* __restrict__ fw,
                                                            int* __restrict__ done, int* __restrict__ counter,
                                                            int16_t* __restrict__ starts, unsigned* __restrict__ status,
                                                            int max_range)
@@ -214,6 +263,26 @@ __global__ void __launch_bounds__(256) learned_dcds_kernel(const PropFrame* __re
         const PropFrame& F = fr[find_frame(fr, nframes, gid)];
         const int k = gid - F.base;
         const int bx = k % F.nbx, by = k / F.nbx;
+        // ---- work that does not depend on the neighbours: the block, the origin's SAD ----
+        const int R = F.range, px = bx * 16, py = by * 16;
+        WarpBlock b;
+        b.ref = F.ref; b.pitch = F.pitch; b.px = px; b.py = py; b.R = R;
+        b.dxlo = max(-R, -px); b.dxhi = min(R, F.w - 16 - px);
+        b.dylo = max(-R, -py); b.dyhi = min(R, F.h - 16 - py);
+        {
+            const uint32_t* cp = reinterpret_cast<const uint32_t*>(F.cur + (size_t)(py + (lane >> 1)) * F.pitch + px +
+                                                                   8 * (lane & 1));
+            b.c0 = __ldg(cp);
+            b.c1 = __ldg(cp + 1);
+        }
+        int nsp = 0;
+        uint32_t cval;
+        {
+            const int qx[1] = {0}, qy[1] = {0};
+            uint32_t v[1];
+            visit_many<1>(b, bm, wmin, wmax, nsp, qx, qy, v, lane);  // the origin is always a candidate
+            cval = v[0];
+        }
         // ---- wait until the causal neighbours are final ----
         const int nbdx[3] = {-1, 0, 1}, nbdy[3] = {0, -1, -1};
         float mvx = 0.f, mvy = 0.f;
@@ -241,28 +310,18 @@ __global__ void __launch_bounds__(256) learned_dcds_kernel(const PropFrame* __re
             mvf[2 * q] = __shfl_sync(0xffffffffu, mvx, q);
             mvf[2 * q + 1] = __shfl_sync(0xffffffffu, mvy, q);
         }
-        // ---- head: logits from the conv-4 features and the neighbours ----
-        const __nv_bfloat16* af = a4 + (size_t)gid * 128;
+        // ---- head: the conv-feature part of the logits was computed for every block
+        //      beforehand (zpart = bias + conv terms, in the head's order); add the
+        //      neighbours' terms ----
+        const float* zp = zpart + (size_t)gid * NLOGIT;
         for (int o = lane; o < NLOGIT; o += 32) {
             const float* wr = fw + (size_t)o * NFEAT;
-            float acc = fb[o];
-            for (int f = 0; f < 128; ++f) acc += wr[f] * __bfloat162float(af[(f & 3) * 32 + (f >> 2)]);
+            float acc = zp[o];
 #pragma unroll
             for (int q = 0; q < 6; ++q) acc += wr[128 + q] * mvf[q];
             s_logit[warp][o] = acc;
         }
         __syncwarp();
-        const int R = F.range, px = bx * 16, py = by * 16;
-        WarpBlock b;
-        b.ref = F.ref; b.pitch = F.pitch; b.px = px; b.py = py; b.R = R;
-        b.dxlo = max(-R, -px); b.dxhi = min(R, F.w - 16 - px);
-        b.dylo = max(-R, -py); b.dyhi = min(R, F.h - 16 - py);
-        {
-            const uint32_t* cp = reinterpret_cast<const uint32_t*>(F.cur + (size_t)(py + (lane >> 1)) * F.pitch + px +
-                                                                   8 * (lane & 1));
-            b.c0 = __ldg(cp);
-            b.c1 = __ldg(cp + 1);
-        }
         int sx = 0, sy = 0, pv = 0;
         {
             // argmax with ties to the class nearest the centre: 0, -1, +1, -2, +2, ...
@@ -280,36 +339,53 @@ __global__ void __launch_bounds__(256) learned_dcds_kernel(const PropFrame* __re
         }
         __syncwarp();  // s_logit is reused by the next block of this warp
         // ---- search ----
-        int nsp = 0;
-        uint32_t v = 0, cval = 0;
-        visit(b, bm, wmin, wmax, nsp, 0, 0, &cval, lane);  // the origin is always a candidate
         int cx = 0, cy = 0;
-        if ((sx != 0 || sy != 0) && visit(b, bm, wmin, wmax, nsp, sx, sy, &v, lane) && v < cval) {
-            cx = sx; cy = sy; cval = v;
+        {
+            // the proposed start (skipped when it is the origin, visited above)
+            const int qx[1] = {sx}, qy[1] = {sy};
+            uint32_t v[1];
+            const unsigned f = visit_many<1>(b, bm, wmin, wmax, nsp, qx, qy, v, lane);
+            if ((f & 1u) && v[0] < cval) { cx = sx; cy = sy; cval = v[0]; }
         }
         int bxp = cx, byp = cy;
         uint32_t bsad = cval;
-        for (int i = 0; i < 6; ++i) {
-            const int qx = cx + (pv ? kFirstV[i][0] : kFirstH[i][0]);
-            const int qy = cy + (pv ? kFirstV[i][1] : kFirstH[i][1]);
-            if (visit(b, bm, wmin, wmax, nsp, qx, qy, &v, lane) && v < bsad) { bsad = v; bxp = qx; byp = qy; }
+        {
+            int qx[6], qy[6];
+            uint32_t v[6];
+#pragma unroll
+            for (int i = 0; i < 6; ++i) {
+                qx[i] = cx + (pv ? kFirstV[i][0] : kFirstH[i][0]);
+                qy[i] = cy + (pv ? kFirstV[i][1] : kFirstH[i][1]);
+            }
+            const unsigned f = visit_many<6>(b, bm, wmin, wmax, nsp, qx, qy, v, lane);
+#pragma unroll
+            for (int i = 0; i < 6; ++i)
+                if (((f >> i) & 1u) && v[i] < bsad) { bsad = v[i]; bxp = qx[i]; byp = qy[i]; }
         }
         if (bxp != cx || byp != cy) {
             int pat = (byp == cy) ? 0 : 1;  // switching strategy one
             cx = bxp; cy = byp;
             for (int guard = 0; guard < 4 * side_max * side_max; ++guard) {
-                for (int i = 0; i < 4; ++i) {
-                    const int qx = cx + kDd[pat][i][0], qy = cy + kDd[pat][i][1];
-                    if (visit(b, bm, wmin, wmax, nsp, qx, qy, &v, lane) && v < bsad) { bsad = v; bxp = qx; byp = qy; }
-                }
+                int qx[4], qy[4];
+                uint32_t v[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) { qx[i] = cx + kDd[pat][i][0]; qy[i] = cy + kDd[pat][i][1]; }
+                const unsigned f = visit_many<4>(b, bm, wmin, wmax, nsp, qx, qy, v, lane);
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    if (((f >> i) & 1u) && v[i] < bsad) { bsad = v[i]; bxp = qx[i]; byp = qy[i]; }
                 if (bxp == cx && byp == cy) break;
                 if (abs(bxp - cx) + abs(byp - cy) == 1) pat ^= 1;  // switching strategy two
                 cx = bxp; cy = byp;
             }
-            for (int i = 0; i < 2; ++i) {
-                const int qx = cx + kMid[pat][i][0], qy = cy + kMid[pat][i][1];
-                if (visit(b, bm, wmin, wmax, nsp, qx, qy, &v, lane) && v < bsad) { bsad = v; bxp = qx; byp = qy; }
-            }
+            int qx[2], qy[2];
+            uint32_t v[2];
+#pragma unroll
+            for (int i = 0; i < 2; ++i) { qx[i] = cx + kMid[pat][i][0]; qy[i] = cy + kMid[pat][i][1]; }
+            const unsigned f = visit_many<2>(b, bm, wmin, wmax, nsp, qx, qy, v, lane);
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+                if (((f >> i) & 1u) && v[i] < bsad) { bsad = v[i]; bxp = qx[i]; byp = qy[i]; }
         }
         if (lane == 0) {
             reinterpret_cast<uint32_t*>(F.mv)[k] = (uint32_t)(uint16_t)bxp | ((uint32_t)(uint16_t)byp << 16);
@@ -355,13 +431,10 @@ size_t ws_layout(uint8_t* base, int n, bool train, Ws* w)
     w->mvf = (float*)take(N * 6 * 4);
     w->labels = (int*)take(N * 3 * 4);
     for (int l = 0; l < LAYERS; ++l) {
+        // inference runs the fused trunk: no im2col buffers, only the conv-4 activations
         const size_t ho = HIN[l] / 2;
-        w->cols[l] = (__nv_bfloat16*)take((train || l == 0 ? N * ho * ho * KP[l] : (l == 1 ? N * 64 * 288 : 0)) * 2);
-        w->a[l] = (__nv_bfloat16*)take(N * ho * ho * CH * 2);
-    }
-    if (!train) {  // one shared im2col buffer at inference
-        for (int l = 1; l < LAYERS; ++l) w->cols[l] = w->cols[1];
-        w->cols[0] = w->cols[0];
+        w->cols[l] = train ? (__nv_bfloat16*)take(N * ho * ho * KP[l] * 2) : nullptr;
+        w->a[l] = (train || l == LAYERS - 1) ? (__nv_bfloat16*)take(N * ho * ho * CH * 2) : nullptr;
     }
     w->logits = (float*)take(N * NLOGIT * 4);
     w->dlogits = (float*)take(N * NLOGIT * 4);
@@ -451,6 +524,14 @@ cudaError_t forward(me_proposal* P, const Ws& w, int n, bool head, cudaStream_t 
                      P->p + PB[l], w.a[l], st);
     }
     if (e == cudaSuccess && head) e = head_fwd(w.a[3], w.mvf, n, P->p + P_FW, P->p + P_FB, w.logits, st);
+    return e;
+}
+
+// inference: the fused trunk writes the conv-4 activations to a4 (then the head)
+cudaError_t forward_infer(me_proposal* P, const Ws& w, int n, __nv_bfloat16* a4, bool head, cudaStream_t st)
+{
+    cudaError_t e = trunk(w.x, n, P->w, P->p, a4, P->ctx->num_sms, st);
+    if (e == cudaSuccess && head) e = head_fwd(a4, w.mvf, n, P->p + P_FW, P->p + P_FB, w.logits, st);
     return e;
 }
 
@@ -584,7 +665,7 @@ int me_proposal_logits(me_ctx* c, me_proposal* P, const me_frame_desc* d, float*
         if (rc != ME_OK) return rc;
         feat_kernel<<<nblk((long)ns * 1024), 256, 0, st>>>(P->frames, 1, s0, ns, w.x, w.mvf, nullptr);
         cudaError_t e = cudaGetLastError();
-        if (e == cudaSuccess) e = forward(P, w, ns, true, st);
+        if (e == cudaSuccess) e = forward_infer(P, w, ns, w.a[3], true, st);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(logits + s0 * NLOGIT, w.logits, sizeof(float) * ns * NLOGIT, cudaMemcpyDeviceToDevice, st);
         if (e != cudaSuccess) return cuda_fail(c, e, "me_proposal_logits");
@@ -605,7 +686,8 @@ int me_estimate_learned_batch(me_ctx* c, me_proposal* P, const me_frame_desc* d,
     // buffers after the trunk workspace: conv-4 features, done flags, counter
     Ws w;
     const size_t trunk = ws_layout(nullptr, kChunk, false, &w);
-    const size_t need = al(trunk) + al((size_t)total * 128 * 2) + al((size_t)total * 4) + 256;
+    const size_t need = al(trunk) + al((size_t)total * 128 * 2) + al((size_t)total * 4) + 256 +
+                        al((size_t)total * NLOGIT * 4);
     if (P->ws_cap < need) {
         cudaFree(P->ws);
         P->ws = nullptr;
@@ -617,6 +699,7 @@ int me_estimate_learned_batch(me_ctx* c, me_proposal* P, const me_frame_desc* d,
     __nv_bfloat16* a4all = reinterpret_cast<__nv_bfloat16*>(P->ws + al(trunk));
     int* done = reinterpret_cast<int*>(P->ws + al(trunk) + al((size_t)total * 128 * 2));
     int* counter = done + ((al((size_t)total * 4)) / 4);
+    float* zpart = reinterpret_cast<float*>(P->ws + al(trunk) + al((size_t)total * 128 * 2) + al((size_t)total * 4) + 256);
     // wavefront order: t = bx + 2 by ascending, frames interleaved
     std::vector<int> ord;
     ord.reserve(total);
@@ -644,11 +727,12 @@ int me_estimate_learned_batch(me_ctx* c, me_proposal* P, const me_frame_desc* d,
         const int ns = (int)std::min<long>(kChunk, total - s0);
         feat_kernel<<<nblk((long)ns * 1024), 256, 0, st>>>(P->frames, n, s0, ns, w.x, w.mvf, nullptr);
         e = cudaGetLastError();
-        if (e == cudaSuccess) e = forward(P, w, ns, false, st);
-        if (e == cudaSuccess) {
-            copy_rows_kernel<<<nblk((long)ns * 128), 256, 0, st>>>(w.a[3], (long)ns * 128, a4all + s0 * 128);
-            e = cudaGetLastError();
-        }
+        if (e == cudaSuccess) e = forward_infer(P, w, ns, a4all + s0 * 128, false, st);
+    }
+    if (e == cudaSuccess) {
+        const int zb = (int)std::max(1l, std::min((total + kZS - 1) / kZS, (long)c->num_sms * 4));
+        zpart_kernel<<<zb, 4 * NLOGIT, 0, st>>>(a4all, total, P->p + P_FW, P->p + P_FB, zpart);
+        e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(done, 0, al((size_t)total * 4) + 256, st);
     int max_range = 1;
@@ -656,8 +740,8 @@ int me_estimate_learned_batch(me_ctx* c, me_proposal* P, const me_frame_desc* d,
     const int side = 2 * max_range + 1;
     const size_t smem = (size_t)8 * ((side * side + 31) / 32) * 4;
     if (e == cudaSuccess) {
-        learned_dcds_kernel<<<c->num_sms * 4, 256, smem, st>>>(P->frames, n, P->order, (int)total, a4all, P->p + P_FW,
-                                                              P->p + P_FB, done, counter, starts, c->status, max_range);
+        learned_dcds_kernel<<<c->num_sms * 4, 256, smem, st>>>(P->frames, n, P->order, (int)total, zpart,
+                                                              P->p + P_FW, done, counter, starts, c->status, max_range);
         e = cudaGetLastError();
     }
     // the host-side tables are reused by the next call: wait for this one
