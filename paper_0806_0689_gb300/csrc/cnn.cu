@@ -115,17 +115,18 @@ __global__ void __launch_bounds__(128) gemm_kernel(const __nv_bfloat16* __restri
 }
 
 // ------------------------------------------------------------------ fused trunk (inference)
-// All four convolutions for TS samples at a time, without im2col: each layer
-// is an implicit GEMM whose A fragments are gathered straight from the
-// previous layer's activations in shared memory (NHWC, a pixel padded to
-// PXW words so that the 8 output pixels of a fragment, two input pixels
-// apart, fall on 8 different bank groups), B fragments come from the
-// weights staged once per CTA, and bias + ReLU + bf16 rounding happen in the
-// epilogue.  The arithmetic per output is the im2col path's: bf16 operands,
-// fp32 accumulation, one bf16 rounding of each activation.
+// Features and all four convolutions for TS samples at a time, without
+// im2col: the two input planes are built from the frames straight into shared
+// memory (the features of feat_kernel), each layer is an implicit GEMM whose
+// A fragments are gathered from the previous layer's activations in shared
+// memory (NHWC, a pixel padded to PXW words so that the 8 output pixels of a
+// fragment, two input pixels apart, fall on 8 different bank groups), B
+// fragments are read from the GEMM-layout weights (L1-resident), and bias +
+// ReLU + bf16 rounding happen in the epilogue.  The arithmetic per output is
+// the im2col path's: bf16 operands, fp32 accumulation, one bf16 rounding of
+// each activation.  Two CTAs of 8 warps share an SM.
 constexpr int TS = 4;     // samples per trunk iteration
 constexpr int PXW = 18;   // smem words per pixel of a 32-channel activation (16 + 2 padding)
-constexpr int WRW = 148;  // smem words per weight row of layers 2-4 (144 + 4 padding)
 
 struct TrunkW {
     const __nv_bfloat16* w[LAYERS];
@@ -173,9 +174,9 @@ __device__ __forceinline__ void conv32(const uint32_t* __restrict__ in, const ui
             uint32_t bf[NN][2];
 #pragma unroll
             for (int j = 0; j < NN; ++j) {
-                const uint32_t* wr = Wl + (size_t)((n0 + j) * 8 + g) * WRW + tap * 16 + half * 8 + t;
-                bf[j][0] = wr[0];
-                bf[j][1] = wr[4];
+                const uint32_t* wr = Wl + (size_t)((n0 + j) * 8 + g) * 144 + tap * 16 + half * 8 + t;
+                bf[j][0] = __ldg(wr);
+                bf[j][1] = __ldg(wr + 4);
             }
 #pragma unroll
             for (int i = 0; i < NM; ++i) {
@@ -191,27 +192,31 @@ __device__ __forceinline__ void conv32(const uint32_t* __restrict__ in, const ui
     }
 }
 
-__global__ void __launch_bounds__(256, 1) trunk_kernel(const __nv_bfloat16* __restrict__ x, int n, TrunkW tw,
-                                                       __nv_bfloat16* __restrict__ a4)
+__device__ __forceinline__ int trunk_frame(const PropFrame* fr, int nframes, long gid)
+{
+    int lo = 0, hi = nframes - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (fr[mid].base <= gid) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(256, 2) trunk_kernel(const PropFrame* __restrict__ fr, int nframes, long sbase,
+                                                       int n, TrunkW tw, __nv_bfloat16* __restrict__ a4)
 {
     extern __shared__ __align__(16) uint32_t tsm[];
-    uint32_t* Ws = tsm;                         // layers 2-4: [3][32][WRW]
-    uint32_t* X = Ws + 3 * 32 * WRW;            // [TS][32][32] pixels of 2 channels (one word)
-    uint32_t* A1 = X + TS * 1024;               // [TS][16][16][PXW]
+    uint32_t* A1 = tsm;                         // [TS][16][16][PXW]
     uint32_t* A2 = A1 + TS * 256 * PXW;         // [TS][8][8][PXW]
     uint32_t* A3 = A2 + TS * 64 * PXW;          // [TS][4][4][PXW]
+    uint32_t* X = A2;                           // [TS][32][32] pixels of 2 channels; dead once layer 1 is done
     __shared__ float sb[LAYERS][CH];
+    __shared__ int s_fr[TS], s_px[TS], s_py[TS];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int g = lane >> 2, t = lane & 3;
-
-#pragma unroll
-    for (int l = 0; l < 3; ++l) {
-        const uint32_t* wl = reinterpret_cast<const uint32_t*>(tw.w[l + 1]);
-        for (int i = tid; i < 32 * 144; i += blockDim.x) {
-            const int r = i / 144, k = i - r * 144;
-            Ws[(l * 32 + r) * WRW + k] = wl[i];
-        }
-    }
+    const uint32_t* W2 = reinterpret_cast<const uint32_t*>(tw.w[1]);  // [32][144] words each
+    const uint32_t* W3 = reinterpret_cast<const uint32_t*>(tw.w[2]);
+    const uint32_t* W4 = reinterpret_cast<const uint32_t*>(tw.w[3]);
 #pragma unroll
     for (int l = 0; l < LAYERS; ++l)
         if (tid < CH) sb[l][tid] = tw.b[l][tid];
@@ -231,8 +236,33 @@ __global__ void __launch_bounds__(256, 1) trunk_kernel(const __nv_bfloat16* __re
 
     for (int s0 = blockIdx.x * TS; s0 < n; s0 += gridDim.x * TS) {
         const int ns = min(TS, n - s0);
-        const uint32_t* xs = reinterpret_cast<const uint32_t*>(x) + (size_t)s0 * 1024;
-        for (int i = tid; i < TS * 1024; i += blockDim.x) X[i] = (i >> 10) < ns ? xs[i] : 0u;
+        if (tid < TS && tid < ns) {
+            const long gid = sbase + s0 + tid;
+            const int f = trunk_frame(fr, nframes, gid);
+            const int k = (int)(gid - fr[f].base);
+            s_fr[tid] = f;
+            s_px[tid] = (k % fr[f].nbx) * 16;
+            s_py[tid] = (k / fr[f].nbx) * 16;
+        }
+        __syncthreads();  // also: the previous iteration's reads of A2 / A3 are done
+        // features (as feat_kernel): channel 0 = the current block centred in a zero 32x32 canvas,
+        // channel 1 = the co-located reference patch, coordinates clamped; both (p - 128) / 128
+        for (int i = tid; i < TS * 1024; i += blockDim.x) {
+            const int s = i >> 10, pix = i & 1023, yy = pix >> 5, xx = pix & 31;
+            uint32_t v = 0u;
+            if (s < ns) {
+                const PropFrame& F = fr[s_fr[s]];
+                const int px = s_px[s], py = s_py[s];
+                float v0 = 0.f;
+                if (yy >= 8 && yy < 24 && xx >= 8 && xx < 24)
+                    v0 = ((float)F.cur[(size_t)(py + yy - 8) * F.pitch + (px + xx - 8)] - 128.f) * (1.f / 128.f);
+                const int ry = min(max(py + yy - 8, 0), F.h - 1), rxx = min(max(px + xx - 8, 0), F.w - 1);
+                const float v1 = ((float)F.ref[(size_t)ry * F.pitch + rxx] - 128.f) * (1.f / 128.f);
+                const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+                v = *reinterpret_cast<const uint32_t*>(&h);
+            }
+            X[i] = v;
+        }
         __syncthreads();
 
         // ---- layer 1: 32x32x2 -> 16x16x32; an m-tile is one output row of 16 pixels ----
@@ -285,7 +315,7 @@ __global__ void __launch_bounds__(256, 1) trunk_kernel(const __nv_bfloat16* __re
                 }
             }
             float acc[2][4][4];
-            conv32<16, 2, 4>(A1, Ws, rw, 0, acc, g, t);
+            conv32<16, 2, 4>(A1, W2, rw, 0, acc, g, t);
 #pragma unroll
             for (int i = 0; i < 2; ++i)
 #pragma unroll
@@ -310,7 +340,7 @@ __global__ void __launch_bounds__(256, 1) trunk_kernel(const __nv_bfloat16* __re
                 rw.ox[0][h] = g & 3;
             }
             float acc[1][2][4];
-            conv32<8, 1, 2>(A2, Ws + 32 * WRW, rw, 2 * nh, acc, g, t);
+            conv32<8, 1, 2>(A2, W3, rw, 2 * nh, acc, g, t);
 #pragma unroll
             for (int j = 0; j < 2; ++j)
 #pragma unroll
@@ -332,7 +362,7 @@ __global__ void __launch_bounds__(256, 1) trunk_kernel(const __nv_bfloat16* __re
                 rw.ox[0][h] = g & 1;
             }
             float acc[1][1][4];
-            conv32<4, 1, 1>(A3, Ws + 2 * 32 * WRW, rw, warp, acc, g, t);
+            conv32<4, 1, 1>(A3, W4, rw, warp, acc, g, t);
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int s = rw.s[0][h], pix = (g & 3), c = warp * 8 + 2 * t;
@@ -342,7 +372,6 @@ __global__ void __launch_bounds__(256, 1) trunk_kernel(const __nv_bfloat16* __re
                 }
             }
         }
-        __syncthreads();
     }
 }
 
@@ -607,11 +636,12 @@ cudaError_t relu_back(const float* da, const __nv_bfloat16* a, long rows, __nv_b
 
 size_t trunk_smem_bytes()
 {
-    return sizeof(uint32_t) * ((size_t)3 * 32 * WRW + (size_t)TS * 1024 + (size_t)TS * (256 + 64 + 16) * PXW);
+    static_assert(TS * 1024 <= TS * (64 + 16) * PXW, "the feature planes fit in the layer-2/3 buffers");
+    return sizeof(uint32_t) * ((size_t)TS * (256 + 64 + 16) * PXW);
 }
 
-cudaError_t trunk(const __nv_bfloat16* x, int n, const __nv_bfloat16* const* w, const float* params,
-                  __nv_bfloat16* a4, int num_sms, cudaStream_t st)
+cudaError_t trunk(const PropFrame* frames, int nframes, long sbase, int n, const __nv_bfloat16* const* w,
+                  const float* params, __nv_bfloat16* a4, int num_sms, cudaStream_t st)
 {
     TrunkW tw;
     for (int l = 0; l < LAYERS; ++l) {
@@ -622,7 +652,7 @@ cudaError_t trunk(const __nv_bfloat16* x, int n, const __nv_bfloat16* const* w, 
     cudaError_t e = cudaFuncSetAttribute(trunk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int groups = (n + TS - 1) / TS;
-    trunk_kernel<<<std::max(1, std::min(groups, num_sms)), 256, smem, st>>>(x, n, tw, a4);
+    trunk_kernel<<<std::max(1, std::min(groups, 2 * num_sms)), 256, smem, st>>>(frames, nframes, sbase, n, tw, a4);
     return cudaGetLastError();
 }
 

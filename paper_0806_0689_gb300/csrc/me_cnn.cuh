@@ -31,12 +31,6 @@ enum { GEMM_STORE = 0, GEMM_ATOMIC = 1, GEMM_BIAS_RELU = 2 };
 
 cudaError_t gemm(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, float* C, int ldc, int M,
                  int N, int K, int splits, int mode, const float* bias, __nv_bfloat16* out_bf16, cudaStream_t st);
-// Inference trunk: features x (NHWC [n][32][32][2] bf16) -> conv-4 activations
-// a4 ([n][2][2][32] bf16), all four layers in one launch (no im2col).
-// w: the four GEMM-layout weights [32][KP[l]]; params: canonical parameters
-// (biases at PB[l]).
-cudaError_t trunk(const __nv_bfloat16* x, int n, const __nv_bfloat16* const* w, const float* params,
-                  __nv_bfloat16* a4, int num_sms, cudaStream_t st);
 cudaError_t im2col(const __nv_bfloat16* in, int n, int hin, int cin, int kp, __nv_bfloat16* cols, cudaStream_t st);
 cudaError_t col2im(const float* dcols, int n, int hin, int cin, int kp, float* din, cudaStream_t st);
 cudaError_t transpose(const __nv_bfloat16* in, int rows, int ncols, int ld_in, __nv_bfloat16* out, int rows_pad,
@@ -64,6 +58,14 @@ struct PropFrame {
     int32_t w, h, pitch, range, nbx, nby, base;  // base: index of the frame's first block
     int32_t pad_;
 };
+
+// Inference trunk for the n blocks sbase .. sbase + n - 1 of the frame table
+// (blocks numbered through the frames' bases): features from the frames, then
+// the four layers, writing conv-4 activations a4 ([n][2][2][32] bf16) in one
+// launch (no im2col).  w: the four GEMM-layout weights [32][KP[l]]; params:
+// canonical parameters (biases at PB[l]).
+cudaError_t trunk(const PropFrame* frames, int nframes, long sbase, int n, const __nv_bfloat16* const* w,
+                  const float* params, __nv_bfloat16* a4, int num_sms, cudaStream_t st);
 
 }  // namespace cnn
 }  // namespace me

@@ -527,10 +527,12 @@ cudaError_t forward(me_proposal* P, const Ws& w, int n, bool head, cudaStream_t 
     return e;
 }
 
-// inference: the fused trunk writes the conv-4 activations to a4 (then the head)
-cudaError_t forward_infer(me_proposal* P, const Ws& w, int n, __nv_bfloat16* a4, bool head, cudaStream_t st)
+// inference: the fused trunk writes the conv-4 activations of blocks
+// [s0, s0 + n) to a4 (then the head, whose neighbour scalars are in w.mvf)
+cudaError_t forward_infer(me_proposal* P, int nframes, long s0, const Ws& w, int n, __nv_bfloat16* a4, bool head,
+                          cudaStream_t st)
 {
-    cudaError_t e = trunk(w.x, n, P->w, P->p, a4, P->ctx->num_sms, st);
+    cudaError_t e = trunk(P->frames, nframes, s0, n, P->w, P->p, a4, P->ctx->num_sms, st);
     if (e == cudaSuccess && head) e = head_fwd(a4, w.mvf, n, P->p + P_FW, P->p + P_FB, w.logits, st);
     return e;
 }
@@ -665,7 +667,7 @@ int me_proposal_logits(me_ctx* c, me_proposal* P, const me_frame_desc* d, float*
         if (rc != ME_OK) return rc;
         feat_kernel<<<nblk((long)ns * 1024), 256, 0, st>>>(P->frames, 1, s0, ns, w.x, w.mvf, nullptr);
         cudaError_t e = cudaGetLastError();
-        if (e == cudaSuccess) e = forward_infer(P, w, ns, w.a[3], true, st);
+        if (e == cudaSuccess) e = forward_infer(P, 1, s0, w, ns, w.a[3], true, st);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(logits + s0 * NLOGIT, w.logits, sizeof(float) * ns * NLOGIT, cudaMemcpyDeviceToDevice, st);
         if (e != cudaSuccess) return cuda_fail(c, e, "me_proposal_logits");
@@ -723,12 +725,8 @@ int me_estimate_learned_batch(me_ctx* c, me_proposal* P, const me_frame_desc* d,
         P->order_cap = total;
     }
     cudaError_t e = cudaMemcpyAsync(P->order, ord.data(), sizeof(int) * total, cudaMemcpyHostToDevice, st);
-    for (long s0 = 0; s0 < total && e == cudaSuccess; s0 += kChunk) {
-        const int ns = (int)std::min<long>(kChunk, total - s0);
-        feat_kernel<<<nblk((long)ns * 1024), 256, 0, st>>>(P->frames, n, s0, ns, w.x, w.mvf, nullptr);
-        e = cudaGetLastError();
-        if (e == cudaSuccess) e = forward_infer(P, w, ns, a4all + s0 * 128, false, st);
-    }
+    // the trunk builds the features itself: one launch over every block of the batch
+    if (e == cudaSuccess) e = forward_infer(P, n, 0, w, (int)total, a4all, false, st);
     if (e == cudaSuccess) {
         const int zb = (int)std::max(1l, std::min((total + kZS - 1) / kZS, (long)c->num_sms * 4));
         zpart_kernel<<<zb, 4 * NLOGIT, 0, st>>>(a4all, total, P->p + P_FW, P->p + P_FB, zpart);
