@@ -210,13 +210,33 @@ def learned_leg(ctx, me, torch, dev, curs, refs, mv_plain, mv_fs, st_plain, nb, 
     ctx.me_proposal_free(prop)
     mean = lambda rows, k: float(np.mean([r[k] for r in rows]))
     ms = float(np.median(ts))
+    # the non-learned control: the same wavefront search from the neighbours' median
+    ctx.me_estimate_median_batch(d_l)
+    tm = []
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ctx.me_estimate_median_batch(d_l)
+        e1.record()
+        torch.cuda.synchronize()
+        tm.append(e0.elapsed_time(e1))
+    sums_m = torch.zeros_like(sums)
+    ctx.me_eval_batch(e_l, B_, sums_m)
+    torch.cuda.synchronize()
+    st_m = [ctx.me_stats_from_sums(r) for r in sums_m.cpu().numpy().view(np.uint64)]
+    ms_m = float(np.median(tm))
+    median = {"macroblocks_per_s": npairs * nb / (ms_m * 1e-3), "ms_per_batch": ms_m,
+              "nsp_per_mb": mean(st_m, "nsp"), "psnr_db": mean(st_m, "psnr"),
+              "psnr_minus_plain_db": mean(st_m, "psnr") - mean(st_plain, "psnr"),
+              "probability_fs": mean(st_m, "probability")}
     return {"macroblocks_per_s": npairs * nb / (ms * 1e-3), "ms_per_batch": ms,
             "nsp_per_mb": mean(st, "nsp"), "psnr_db": mean(st, "psnr"),
             "plain_nsp_per_mb": mean(st_plain, "nsp"), "plain_psnr_db": mean(st_plain, "psnr"),
             "psnr_minus_plain_db": mean(st, "psnr") - mean(st_plain, "psnr"),
             "distance_to_fs": mean(st, "distance"), "probability_fs": mean(st, "probability"),
             "training": {"pairs": len(items), "steps": steps, "final_loss": float(np.mean(losses[-50:])),
-                         "seconds": t_train, "labels": "full-search fields from this library (CIF, seeds >= 100000)"}}
+                         "seconds": t_train, "labels": "full-search fields from this library (CIF, seeds >= 100000)"},
+            "median_start_control": median}
 
 
 # ---------------------------------------------------------------- reference arm

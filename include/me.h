@@ -232,6 +232,18 @@ int me_proposal_logits(me_ctx* ctx, me_proposal* p, const me_frame_desc* desc, f
 int me_estimate_learned_batch(me_ctx* ctx, me_proposal* p, const me_frame_desc* descs, int n,
                               int16_t* starts, void* stream);
 
+/* me_estimate_median_batch: the non-learned control for the learned start
+ * (not in the paper).  The same wavefront search as me_estimate_learned_batch
+ * (16x16 blocks, left, top and top-right blocks final first), with the start
+ * at the component-wise median of those three neighbours' final MVs (an
+ * absent neighbour counts as (0,0)), clamped to the window and the frame,
+ * and a vertical prior (the VCSP first) when the median's |dy| > |dx|.  The
+ * origin and the start are evaluated, the better one (the origin on a tie)
+ * centres the first pattern, then DCDS steps 2-4.  Arguments, outputs and
+ * errors as for me_estimate_learned_batch; no proposal is needed.  The call
+ * returns after the search (it waits on `stream`). */
+int me_estimate_median_batch(me_ctx* ctx, const me_frame_desc* descs, int n, int16_t* starts, void* stream);
+
 /* ---------------------------------------------------------------------- */
 /* Evaluation: the six measures of Sec. IV (MAD, MSE, NSP, PSNR, distance  */
 /* to the FS motion vector, probability of finding it).                    */

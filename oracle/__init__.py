@@ -279,6 +279,52 @@ def cnn_start(logits, px, py, w, h, rng, block=16):
     return sx, sy, int(logits[67] > logits[66])
 
 
+def median_start(mv, k, nbx, px, py, w, h, rng, block=16):
+    """Start of the non-learned control: the component-wise median of the
+    left, top and top-right final MVs (absent neighbours count as (0,0)),
+    clamped to the window and the frame; vertical prior when |dy| > |dx|."""
+    bx, by = k % nbx, k // nbx
+    cand = []
+    for ax, ay in ((bx - 1, by), (bx, by - 1), (bx + 1, by - 1)):
+        if 0 <= ax < nbx and ay >= 0:
+            cand.append((int(mv[ay * nbx + ax][0]), int(mv[ay * nbx + ax][1])))
+        else:
+            cand.append((0, 0))
+    sx = sorted(c[0] for c in cand)[1]
+    sy = sorted(c[1] for c in cand)[1]
+    pv = int(abs(sy) > abs(sx))
+    sx = max(max(-rng, -px), min(min(rng, w - block - px), sx))
+    sy = max(max(-rng, -py), min(min(rng, h - block - py), sy))
+    return sx, sy, pv
+
+
+def median_dcds(cur, ref, rng):
+    """DCDS from the neighbour-median start (16x16 blocks, raster order, so the
+    left, top and top-right neighbours are final first).  Returns
+    (mv, sad, nsp, starts)."""
+    cur, ref = _frames(cur, ref)
+    h, w = cur.shape
+    nbx, nby = w // 16, h // 16
+    nb = nbx * nby
+    mv = np.zeros((nb, 2), np.int16)
+    sd = np.zeros(nb, np.uint32)
+    ns = np.zeros(nb, np.uint16)
+    starts = np.zeros((nb, 3), np.int16)
+    out = (ctypes.c_int64 * 4)()
+    L = _load()
+    for k in range(nb):
+        px, py = (k % nbx) * 16, (k // nbx) * 16
+        starts[k] = median_start(mv, k, nbx, px, py, w, h, rng)
+        rc = L.oracle_dcds_block_from(_ptr(cur), _ptr(ref), w, h, w, 16, rng, px, py, int(starts[k][0]),
+                                      int(starts[k][1]), int(starts[k][2]), ctypes.cast(out, ctypes.c_void_p))
+        if rc:
+            raise MemoryError("oracle_dcds_block_from failed")
+        mv[k] = (out[0], out[1])
+        sd[k] = out[2]
+        ns[k] = out[3]
+    return mv, sd, ns, starts
+
+
 def learned_dcds(cur, ref, rng, params):
     """Learned-start DCDS of a frame, 16x16 blocks, blocks in raster order (the
     left, top and top-right neighbours are final before a block starts).

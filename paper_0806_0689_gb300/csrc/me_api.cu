@@ -373,6 +373,7 @@ void me_free(me_ctx* c)
         if (s.queue) cudaFree(s.queue);
     }
     if (c->status) cudaFree(c->status);
+    if (c->median_ws) me_proposal_free(c->median_ws);
     delete c;
 }
 

@@ -36,6 +36,7 @@ struct me_ctx {
     int next_slot = 0;
     unsigned* status = nullptr;  // device word written by kernels
     unsigned* sink = nullptr;    // microbenchmark sink
+    struct me_proposal* median_ws = nullptr;  // wavefront buffers of the neighbour-median start (lazy)
 };
 
 struct me_graph {

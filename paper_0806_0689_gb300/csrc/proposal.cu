@@ -12,7 +12,10 @@
 // |mvx| >= |mvy|, else 1.  The neighbour scalars use the same field.
 //
 // Learned-start search: blocks are processed in wavefront order (t = bx + 2 by)
-// so that the left, top and top-right blocks are final first.  Per block, one
+// so that the left, top and top-right blocks are final first.  The same kernel
+// runs the non-learned control: the start is the component-wise median of the
+// three neighbours' MVs (an absent neighbour counts as (0,0)) and the prior is
+// vertical when its |dy| > |dx|.  Per block, one
 // warp waits for those three (acquire loads, bounded), runs the head on the
 // precomputed conv-4 features and the neighbours' MVs, picks the start (argmax
 // of the dx and dy heads, ties to the class nearest the centre) and the prior
@@ -117,6 +120,8 @@ __global__ void feat_kernel(const PropFrame* __restrict__ fr, int nframes, long 
 }
 
 // ------------------------------------------------------------------ learned-start search
+__device__ __forceinline__ int med3(int a, int b, int c) { return max(min(a, b), min(max(a, b), c)); }
+
 __device__ __forceinline__ int ld_acquire(const int* p)
 {
     int v;
@@ -286,6 +291,7 @@ __global__ void __launch_bounds__(256) learned_dcds_kernel(const PropFrame* __re
         // ---- wait until the causal neighbours are final ----
         const int nbdx[3] = {-1, 0, 1}, nbdy[3] = {0, -1, -1};
         float mvx = 0.f, mvy = 0.f;
+        int nmx = 0, nmy = 0;  // the neighbour's MV (median start)
         bool late = false;
         if (lane < 3) {
             const int ax = bx + nbdx[lane], ay = by + nbdy[lane];
@@ -298,8 +304,10 @@ __global__ void __launch_bounds__(256) learned_dcds_kernel(const PropFrame* __re
                 }
                 if (!late) {
                     const uint32_t m = __ldcg(reinterpret_cast<const uint32_t*>(F.mv) + nk);
-                    mvx = (float)(int16_t)(m & 0xffffu) * (1.f / 16.f);
-                    mvy = (float)(int16_t)(m >> 16) * (1.f / 16.f);
+                    nmx = (int)(int16_t)(m & 0xffffu);
+                    nmy = (int)(int16_t)(m >> 16);
+                    mvx = (float)nmx * (1.f / 16.f);
+                    mvy = (float)nmy * (1.f / 16.f);
                 }
             }
         }
@@ -310,6 +318,8 @@ __global__ void __launch_bounds__(256) learned_dcds_kernel(const PropFrame* __re
             mvf[2 * q] = __shfl_sync(0xffffffffu, mvx, q);
             mvf[2 * q + 1] = __shfl_sync(0xffffffffu, mvy, q);
         }
+        int sx = 0, sy = 0, pv = 0;
+        if (zpart) {
         // ---- head: the conv-feature part of the logits was computed for every block
         //      beforehand (zpart = bias + conv terms, in the head's order); add the
         //      neighbours' terms ----
@@ -322,7 +332,6 @@ __global__ void __launch_bounds__(256) learned_dcds_kernel(const PropFrame* __re
             s_logit[warp][o] = acc;
         }
         __syncwarp();
-        int sx = 0, sy = 0, pv = 0;
         {
             // argmax with ties to the class nearest the centre: 0, -1, +1, -2, +2, ...
             const float* z = s_logit[warp];
@@ -334,10 +343,22 @@ __global__ void __launch_bounds__(256) learned_dcds_kernel(const PropFrame* __re
                 if (z[49 + a] > bvy) { bvy = z[49 + a]; sy = a; }
             }
             pv = z[67] > z[66] ? 1 : 0;
-            sx = min(max(sx, b.dxlo), b.dxhi);
-            sy = min(max(sy, b.dylo), b.dyhi);
         }
         __syncwarp();  // s_logit is reused by the next block of this warp
+        } else {
+            // neighbour-median start (absent neighbours count as (0,0))
+            int ax[3], ay[3];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                ax[q] = __shfl_sync(0xffffffffu, nmx, q);
+                ay[q] = __shfl_sync(0xffffffffu, nmy, q);
+            }
+            sx = med3(ax[0], ax[1], ax[2]);
+            sy = med3(ay[0], ay[1], ay[2]);
+            pv = abs(sy) > abs(sx) ? 1 : 0;
+        }
+        sx = min(max(sx, b.dxlo), b.dxhi);
+        sy = min(max(sy, b.dylo), b.dyhi);
         // ---- search ----
         int cx = 0, cy = 0;
         {
@@ -675,8 +696,15 @@ int me_proposal_logits(me_ctx* c, me_proposal* P, const me_frame_desc* d, float*
     return ME_OK;
 }
 
-int me_estimate_learned_batch(me_ctx* c, me_proposal* P, const me_frame_desc* d, int n, int16_t* starts,
-                              void* stream)
+}  // extern "C"
+
+namespace {
+
+// The wavefront search over a batch: with a proposal (median = false) the
+// CNN proposes the starts; with median = true the neighbour-median does and
+// P only lends its buffers.
+int wavefront_batch(me_ctx* c, me_proposal* P, const me_frame_desc* d, int n, int16_t* starts, bool median,
+                    void* stream)
 {
     if (!c || !P || !d || n <= 0) return ME_ERR_ARG;
     for (int i = 0; i < n; ++i)
@@ -726,8 +754,8 @@ int me_estimate_learned_batch(me_ctx* c, me_proposal* P, const me_frame_desc* d,
     }
     cudaError_t e = cudaMemcpyAsync(P->order, ord.data(), sizeof(int) * total, cudaMemcpyHostToDevice, st);
     // the trunk builds the features itself: one launch over every block of the batch
-    if (e == cudaSuccess) e = forward_infer(P, n, 0, w, (int)total, a4all, false, st);
-    if (e == cudaSuccess) {
+    if (!median && e == cudaSuccess) e = forward_infer(P, n, 0, w, (int)total, a4all, false, st);
+    if (!median && e == cudaSuccess) {
         const int zb = (int)std::max(1l, std::min((total + kZS - 1) / kZS, (long)c->num_sms * 4));
         zpart_kernel<<<zb, 4 * NLOGIT, 0, st>>>(a4all, total, P->p + P_FW, P->p + P_FB, zpart);
         e = cudaGetLastError();
@@ -738,13 +766,35 @@ int me_estimate_learned_batch(me_ctx* c, me_proposal* P, const me_frame_desc* d,
     const int side = 2 * max_range + 1;
     const size_t smem = (size_t)8 * ((side * side + 31) / 32) * 4;
     if (e == cudaSuccess) {
-        learned_dcds_kernel<<<c->num_sms * 4, 256, smem, st>>>(P->frames, n, P->order, (int)total, zpart,
-                                                              P->p + P_FW, done, counter, starts, c->status, max_range);
+        learned_dcds_kernel<<<c->num_sms * 4, 256, smem, st>>>(P->frames, n, P->order, (int)total,
+                                                              median ? nullptr : zpart, P->p + P_FW, done, counter,
+                                                              starts, c->status, max_range);
         e = cudaGetLastError();
     }
     // the host-side tables are reused by the next call: wait for this one
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     return e == cudaSuccess ? ME_OK : cuda_fail(c, e, "me_estimate_learned_batch");
+}
+
+}  // namespace
+
+extern "C" {
+
+int me_estimate_learned_batch(me_ctx* c, me_proposal* P, const me_frame_desc* d, int n, int16_t* starts,
+                              void* stream)
+{
+    if (!c || !P) return ME_ERR_ARG;
+    return wavefront_batch(c, P, d, n, starts, false, stream);
+}
+
+int me_estimate_median_batch(me_ctx* c, const me_frame_desc* d, int n, int16_t* starts, void* stream)
+{
+    if (!c) return ME_ERR_ARG;
+    if (!c->median_ws) {
+        int rc = me_proposal_create(c, &c->median_ws);
+        if (rc != ME_OK) return rc;
+    }
+    return wavefront_batch(c, c->median_ws, d, n, starts, true, stream);
 }
 
 }  // extern "C"

@@ -182,6 +182,36 @@ def test_zero_network_is_plain_dcds(ctx):
         ctx.me_proposal_free(prop)
 
 
+def test_median_start_matches_oracle(ctx):
+    """The non-learned control: DCDS from the neighbour-median start, bit-exact
+    with the oracle (MVs, SADs, search-point counts and the starts), on frames
+    with large motion and on a 1080p pair."""
+    pairs = []
+    for name, seed in (("cif", 41), ("qcif", 42), ("720p", 43)):
+        s = synth.workload_sequence(name, 2, seed=seed, scale=(6.0, 3.0), max_motion=16)
+        pairs.append((s[1], s[0]))
+    keep, items = [], []
+    for cur, ref in pairs:
+        c, r, mv, sad, nsp = _pair(ctx, cur, ref, 16, algo=None)
+        keep.append((mv, sad, nsp))
+        items.append((c, r, 16, mv, sad, nsp))
+    total = sum(k[0].shape[0] for k in keep)
+    starts = torch.zeros((total, 3), dtype=torch.int16, device="cuda")
+    ctx.me_estimate_median_batch(me.Context.frame_descs(items), starts)
+    torch.cuda.synchronize()
+    ctx.me_check_status()
+    st = starts.cpu().numpy()
+    base = 0
+    for (cur, ref), (mv, sad, nsp) in zip(pairs, keep):
+        nb = mv.shape[0]
+        m2, s2, n2, st2 = oracle.median_dcds(cur, ref, 16)
+        assert np.array_equal(mv.cpu().numpy(), m2)
+        assert np.array_equal(sad.cpu().numpy().view(np.uint32), s2)
+        assert np.array_equal(nsp.cpu().numpy().view(np.uint16), n2)
+        assert np.array_equal(st[base:base + nb], st2)
+        base += nb
+
+
 def test_training_gain(ctx):
     """Trained on full-search fields of synthetic CIF video with large motion,
     the proposal lowers the search points per block against plain DCDS at a

@@ -136,3 +136,45 @@ def test_gradient_finite_differences():
         pm[i] -= h
         fd = (oracle.cnn_loss_grad(pp, x, mvf, lab)[0] - oracle.cnn_loss_grad(pm, x, mvf, lab)[0]) / (2 * h)
         assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(fd)), (i, fd, g[i])
+
+
+# ---------------------------------------------------------------- neighbour-median start (control)
+
+def test_median_start_closed_forms():
+    nbx = 5
+    mv = np.zeros((15, 2), np.int16)
+    # block 0: no neighbours -> the origin, horizontal prior
+    assert oracle.median_start(mv, 0, nbx, 0, 0, 80, 48, 7) == (0, 0, 0)
+    # block 6 (bx 1, by 1): left 5, top 1, top-right 2
+    mv[5] = (3, 1)
+    mv[1] = (5, -2)
+    mv[2] = (4, 0)
+    assert oracle.median_start(mv, 6, nbx, 16, 16, 80, 48, 7) == (4, 0, 0)
+    # vertical prior when |dy| > |dx|
+    mv[5], mv[1], mv[2] = (1, 3), (0, 5), (-1, 4)
+    assert oracle.median_start(mv, 6, nbx, 16, 16, 80, 48, 7) == (0, 4, 1)
+    # clamped by the window and the frame (block at px = 16: dx >= -16)
+    mv[5], mv[1], mv[2] = (-20, 0), (-20, 0), (-20, 0)
+    assert oracle.median_start(mv, 6, nbx, 16, 16, 80, 48, 32) == (-16, 0, 0)
+    assert oracle.median_start(mv, 6, nbx, 16, 16, 80, 48, 7)[0] == -7
+
+
+def test_median_dcds_on_a_global_shift():
+    """White noise shifted by (2, 0), an HCSP point: every block of the first
+    row finds it with plain DCDS (its median start is the origin); from the
+    second row on the median of the neighbours is the true MV, so an interior
+    block evaluates the origin, the start and the 5 HCSP points around the
+    start that are new ((0,0) is one of the six), 7 in all, and keeps the start."""
+    rng = np.random.default_rng(3)
+    cur, ref = synth.shifted_pair(rng, 96, 128, 2, 0)
+    mv, sad, nsp, starts = oracle.median_dcds(cur, ref, 7)
+    nbx, nby = 8, 6
+    m0, s0, n0 = oracle.dcds(cur, ref, 16, 7)
+    for bx in range(nbx - 1):
+        assert tuple(starts[bx]) == (0, 0, 0)
+        assert tuple(mv[bx]) == tuple(m0[bx]) == (2, 0) and nsp[bx] == n0[bx]
+    for by in range(1, nby - 1):
+        for bx in range(1, nbx - 1):
+            k = by * nbx + bx
+            assert tuple(starts[k]) == (2, 0, 0)
+            assert tuple(mv[k]) == (2, 0) and sad[k] == 0 and nsp[k] == 7
