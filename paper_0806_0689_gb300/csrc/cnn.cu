@@ -115,17 +115,14 @@ __global__ void __launch_bounds__(128) gemm_kernel(const __nv_bfloat16* __restri
 }
 
 // ------------------------------------------------------------------ fused trunk (inference)
-// Features and all four convolutions for TS samples at a time, without
-// im2col: the two input planes are built from the frames straight into shared
-// memory (the features of feat_kernel), each layer is an implicit GEMM whose
-// A fragments are gathered from the previous layer's activations in shared
-// memory (NHWC, a pixel padded to PXW words so that the 8 output pixels of a
-// fragment, two input pixels apart, fall on 8 different bank groups), B
-// fragments are read from the GEMM-layout weights (L1-resident), and bias +
-// ReLU + bf16 rounding happen in the epilogue.  The arithmetic per output is
-// the im2col path's: bf16 operands, fp32 accumulation, one bf16 rounding of
-// each activation.  Two CTAs of 8 warps share an SM.
-constexpr int TS = 4;     // samples per trunk iteration
+// Features and all four convolutions without im2col.  Helpers shared by the
+// layers that run on mma.sync: implicit-GEMM A fragments are gathered from
+// the previous layer's activations in shared memory (NHWC, a pixel padded to
+// PXW words so that the 8 output pixels of a fragment, two input pixels
+// apart, fall on 8 different bank groups), B fragments are read from the
+// GEMM-layout weights (L1-resident), bias + ReLU + bf16 rounding happen in
+// the epilogue.  The arithmetic per output is the im2col path's: bf16
+// operands, fp32 accumulation, one bf16 rounding of each activation.
 constexpr int PXW = 18;   // smem words per pixel of a 32-channel activation (16 + 2 padding)
 
 struct TrunkW {
@@ -202,28 +199,82 @@ __device__ __forceinline__ int trunk_frame(const PropFrame* fr, int nframes, lon
     return lo;
 }
 
-__global__ void __launch_bounds__(256, 2) trunk_kernel(const PropFrame* __restrict__ fr, int nframes, long sbase,
-                                                       int n, TrunkW tw, __nv_bfloat16* __restrict__ a4)
+// ------------------------------------------------------------------ trunk with tcgen05 (inference)
+// Two samples per iteration: their two feature planes are built from the
+// frames straight into shared memory (the features of feat_kernel), then the
+// four layers run back to back.  Layer 2 (64 % of the trunk's multiply-adds)
+// runs on the 5th-generation tensor cores: one thread issues
+// tcgen05.mma (M = 128 rows = 2 samples x 8 x 8 outputs, N = 32, K = 16 per
+// instruction, bf16 x bf16 -> fp32 in TMEM) for the 9 taps x 2 channel
+// halves, completion arrives on an mbarrier, and every warp reads its TMEM
+// lane quarter back with tcgen05.ld for bias + ReLU.  The A operand needs no
+// gather: layer 1 writes its output in a parity-split layout -- for each
+// group of 8 channels and each (row parity, column parity) a plane of
+// 9 x 9 pixels of 16 bytes, row 0 / column 0 of the odd planes being the
+// zero padding at -1, the two samples' lines interleaved -- in which the
+// pixels one tap reads for 8 consecutive outputs of one output row are 8
+// consecutive 16-byte rows, i.e. one 8x16-byte core matrix of the canonical
+// K-major layout without swizzle.  Shared-memory matrix descriptors then
+// address every tap directly: the next 8 channels are one channel-group plane
+// further (leading byte offset), the next output row of the tile one
+// interleaved line further (stride byte offset).  Layers 1, 3 and 4 stay on
+// mma.sync (K = 18 for layer 1, and too few rows per sample for M = 128 in
+// layers 3-4).
+constexpr int TC_S = 2;                          // samples per iteration (one M = 128 tile in layer 2)
+constexpr int TC_LINE = 9 * 16;                  // bytes per interleaved plane line (9 pixels)
+constexpr int TC_PLANE = 9 * TC_S * TC_LINE;     // 9 rows x 2 samples
+constexpr int TC_CG = 4 * TC_PLANE;              // the 4 parity planes of one channel group
+constexpr int TC_A1 = 4 * TC_CG;                 // 4 channel groups
+constexpr int TC_W2 = 9 * 2048;                  // layer-2 weights in core layout
+constexpr uint32_t TC_WAIT = 1u << 22;
+
+__device__ __forceinline__ uint32_t tc_smem(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor, K-major, no swizzle (sm_100 family format).
+__device__ __forceinline__ uint64_t tc_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
 {
-    extern __shared__ __align__(16) uint32_t tsm[];
-    uint32_t* A1 = tsm;                         // [TS][16][16][PXW]
-    uint32_t* A2 = A1 + TS * 256 * PXW;         // [TS][8][8][PXW]
-    uint32_t* A3 = A2 + TS * 64 * PXW;          // [TS][4][4][PXW]
-    uint32_t* X = A2;                           // [TS][32][32] pixels of 2 channels; dead once layer 1 is done
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+__global__ void __launch_bounds__(256, 3) trunk_tc_kernel(const PropFrame* __restrict__ fr, int nframes, long sbase,
+                                                          int n, TrunkW tw, __nv_bfloat16* __restrict__ a4,
+                                                          unsigned* __restrict__ status)
+{
+    extern __shared__ __align__(1024) uint8_t tcs[];
+    uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(tcs) + 1023) & ~uintptr_t(1023));
+    uint8_t* A1 = base;                                                 // parity-split layer-1 output
+    uint8_t* W2c = A1 + TC_A1;                                          // layer-2 weights, core layout
+    uint32_t* A2 = reinterpret_cast<uint32_t*>(W2c + TC_W2);            // [TC_S][8][8][PXW]
+    uint32_t* A3 = A2 + TC_S * 64 * PXW;                                // [TC_S][4][4][PXW]
+    uint32_t* X = A2;                                                   // [TC_S][32][32] words; dead after layer 1
     __shared__ float sb[LAYERS][CH];
-    __shared__ int s_fr[TS], s_px[TS], s_py[TS];
+    __shared__ int s_fr[TC_S], s_px[TC_S], s_py[TC_S];
+    __shared__ __align__(8) uint64_t s_bar;
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_fail;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int g = lane >> 2, t = lane & 3;
-    const uint32_t* W2 = reinterpret_cast<const uint32_t*>(tw.w[1]);  // [32][144] words each
     const uint32_t* W3 = reinterpret_cast<const uint32_t*>(tw.w[2]);
     const uint32_t* W4 = reinterpret_cast<const uint32_t*>(tw.w[3]);
+
 #pragma unroll
     for (int l = 0; l < LAYERS; ++l)
         if (tid < CH) sb[l][tid] = tw.b[l][tid];
-    // layer 1 (K = 18 padded to 32): the B fragments live in registers
+    // zero the layer-1 planes once: the padding (row / column 0 of odd planes) is never written
+    for (int i = tid; i < TC_A1 / 16; i += blockDim.x) reinterpret_cast<uint4*>(A1)[i] = make_uint4(0u, 0u, 0u, 0u);
+    // layer-2 weights [32][288] (k = tap * 32 + c) -> core matrices (n-group, k-group) of each tap
+    {
+        const __nv_bfloat16* w2 = tw.w[1];
+        for (int i = tid; i < 32 * 288; i += blockDim.x) {
+            const int nn = i / 288, k = i - nn * 288, tap = k >> 5, c = k & 31;
+            *reinterpret_cast<__nv_bfloat16*>(W2c + tap * 2048 + ((c >> 3) * 4 + (nn >> 3)) * 128 + (nn & 7) * 16 +
+                                              (c & 7) * 2) = w2[i];
+        }
+    }
     uint32_t b1[4][2][2];
     {
-        const uint32_t* w1 = reinterpret_cast<const uint32_t*>(tw.w[0]);  // [32][16] words
+        const uint32_t* w1 = reinterpret_cast<const uint32_t*>(tw.w[0]);
 #pragma unroll
         for (int j = 0; j < 4; ++j)
 #pragma unroll
@@ -232,11 +283,27 @@ __global__ void __launch_bounds__(256, 2) trunk_kernel(const PropFrame* __restri
                 b1[j][kt][1] = w1[(j * 8 + g) * 16 + kt * 8 + t + 4];
             }
     }
+    if (tid == 0) {
+        s_fail = 0;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem(&s_bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(tc_smem(&s_tmem))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = s_tmem;
+    // D f32, A bf16, B bf16, both K-major, N = 32, M = 128
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
 
-    for (int s0 = blockIdx.x * TS; s0 < n; s0 += gridDim.x * TS) {
-        const int ns = min(TS, n - s0);
-        if (tid < TS && tid < ns) {
+    uint32_t phase = 0;
+    for (int s0 = blockIdx.x * TC_S; s0 < n; s0 += gridDim.x * TC_S) {
+        const int ns = min(TC_S, n - s0);
+        if (tid < TC_S && tid < ns) {
             const long gid = sbase + s0 + tid;
             const int f = trunk_frame(fr, nframes, gid);
             const int k = (int)(gid - fr[f].base);
@@ -244,10 +311,8 @@ __global__ void __launch_bounds__(256, 2) trunk_kernel(const PropFrame* __restri
             s_px[tid] = (k % fr[f].nbx) * 16;
             s_py[tid] = (k / fr[f].nbx) * 16;
         }
-        __syncthreads();  // also: the previous iteration's reads of A2 / A3 are done
-        // features (as feat_kernel): channel 0 = the current block centred in a zero 32x32 canvas,
-        // channel 1 = the co-located reference patch, coordinates clamped; both (p - 128) / 128
-        for (int i = tid; i < TS * 1024; i += blockDim.x) {
+        __syncthreads();
+        for (int i = tid; i < TC_S * 1024; i += blockDim.x) {
             const int s = i >> 10, pix = i & 1023, yy = pix >> 5, xx = pix & 31;
             uint32_t v = 0u;
             if (s < ns) {
@@ -265,8 +330,8 @@ __global__ void __launch_bounds__(256, 2) trunk_kernel(const PropFrame* __restri
         }
         __syncthreads();
 
-        // ---- layer 1: 32x32x2 -> 16x16x32; an m-tile is one output row of 16 pixels ----
-        for (int mt = warp; mt < TS * 16; mt += 8) {
+        // ---- layer 1 (mma.sync): output rows of 16 pixels, written to the parity-split planes ----
+        for (int mt = warp; mt < TC_S * 16; mt += 8) {
             const int s = mt >> 4, oy = mt & 15;
             float acc[4][4];
 #pragma unroll
@@ -278,7 +343,7 @@ __global__ void __launch_bounds__(256, 2) trunk_kernel(const PropFrame* __restri
                 uint32_t a[4];
 #pragma unroll
                 for (int qq = 0; qq < 4; ++qq) {
-                    const int tap = kt * 8 + t + ((qq & 2) ? 4 : 0);  // k = 2*tap + c, c = 0, 1 in one word
+                    const int tap = kt * 8 + t + ((qq & 2) ? 4 : 0);
                     const int ox = g + ((qq & 1) ? 8 : 0);
                     uint32_t v = 0u;
                     if (tap < 9) {
@@ -290,89 +355,125 @@ __global__ void __launch_bounds__(256, 2) trunk_kernel(const PropFrame* __restri
 #pragma unroll
                 for (int j = 0; j < 4; ++j) mma_bf16(acc[j], a, b1[j][kt]);
             }
+            const int py = oy & 1, yl = (oy + py) >> 1;
 #pragma unroll
             for (int j = 0; j < 4; ++j)
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const int ox = g + 8 * h, c = j * 8 + 2 * t;
-                    A1[((s * 16 + oy) * 16 + ox) * PXW + j * 4 + t] =
+                    const int px = ox & 1, xl = (ox + px) >> 1;
+                    *reinterpret_cast<uint32_t*>(A1 + j * TC_CG + (py * 2 + px) * TC_PLANE + (yl * TC_S + s) * TC_LINE +
+                                                 xl * 16 + (c & 7) * 2) =
                         pack_relu(acc[j][2 * h] + sb[0][c], acc[j][2 * h + 1] + sb[0][c + 1]);
                 }
         }
+        // ---- layer 2 (tcgen05): 18 MMAs from the planes, accumulate in TMEM ----
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor-core reads
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
-
-        // ---- layer 2: 16x16x32 -> 8x8x32; m-tile = two output rows; two m-tiles per warp ----
-        {
-            Rows<2> rw;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (tid == 0) {
+            const uint32_t a_base = tc_smem(A1), b_base = tc_smem(W2c);
+#pragma unroll 1
+            for (int tap = 0; tap < 9; ++tap) {
+                const int ky = tap / 3, kx = tap - 3 * ky;
+                const int py = ky == 1 ? 0 : 1, yoff = ky == 2 ? 1 : 0;
+                const int px = kx == 1 ? 0 : 1, xoff = kx == 2 ? 1 : 0;
 #pragma unroll
-            for (int i = 0; i < 2; ++i) {
-                const int mt = warp + 8 * i;  // 16 m-tiles: sample mt / 4, rows 2*(mt % 4) and +1
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    rw.s[i][h] = mt >> 2;
-                    rw.oy[i][h] = 2 * (mt & 3) + h;
-                    rw.ox[i][h] = g;
+                for (int ks = 0; ks < 2; ++ks) {
+                    const uint32_t aa = a_base + (2 * ks) * TC_CG + (py * 2 + px) * TC_PLANE + yoff * TC_S * TC_LINE +
+                                        xoff * 16;
+                    const uint32_t bb = b_base + tap * 2048 + ks * 1024;
+                    const uint64_t ad = tc_desc(aa, TC_CG, TC_LINE), bd = tc_desc(bb, 512, 128);
+                    const uint32_t accum = (tap | ks) ? 1u : 0u;
+                    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
+                                 ::"r"(tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(accum) : "memory");
                 }
             }
-            float acc[2][4][4];
-            conv32<16, 2, 4>(A1, W2, rw, 0, acc, g, t);
-#pragma unroll
-            for (int i = 0; i < 2; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j)
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int c = j * 8 + 2 * t;
-                        A2[((rw.s[i][h] * 8 + rw.oy[i][h]) * 8 + rw.ox[i][h]) * PXW + j * 4 + t] =
-                            pack_relu(acc[i][j][2 * h] + sb[1][c], acc[i][j][2 * h + 1] + sb[1][c + 1]);
-                    }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         ::"r"(tc_smem(&s_bar)) : "memory");
         }
+        {
+            uint32_t ok = 0;
+            for (uint32_t it = 0; it < TC_WAIT && !ok; ++it) {
+                asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                             "selp.u32 %0, 1, 0, p;\n}"
+                             : "=r"(ok) : "r"(tc_smem(&s_bar)), "r"(phase) : "memory");
+            }
+            phase ^= 1u;
+            if (!__all_sync(0xffffffffu, ok)) {
+                if (lane == 0) atomicOr(&s_fail, 1);
+            } else if (warp < 4) {
+                // warp w reads TMEM lanes 32w .. 32w + 31: row i = (2 * oy + s) * 8 + ox
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                uint32_t v[32];
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                             "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                             "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                             : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                               "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+                               "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),
+                               "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+                               "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),
+                               "=r"(v[31])
+                             : "r"(tmem + ((uint32_t)(32 * warp) << 16)) : "memory");
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                const int i = 32 * warp + lane;
+                const int oy = i >> 4, s = (i >> 3) & 1, ox = i & 7;
+                uint32_t* dst = A2 + ((s * 8 + oy) * 8 + ox) * PXW;
+#pragma unroll
+                for (int c = 0; c < 32; c += 2)
+                    dst[c >> 1] = pack_relu(__uint_as_float(v[c]) + sb[1][c], __uint_as_float(v[c + 1]) + sb[1][c + 1]);
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
+        if (s_fail) break;
 
-        // ---- layer 3: 8x8x32 -> 4x4x32; m-tile = one sample (16 pixels); warp = (sample, half of N) ----
+        // ---- layer 3 (mma.sync): m-tile = one sample; warp = (sample, n-tile) ----
         {
             Rows<1> rw;
-            const int s = warp & 3, nh = warp >> 2;
+            const int s = warp & 1, nt = warp >> 1;
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 rw.s[0][h] = s;
-                rw.oy[0][h] = (g >> 2) + 2 * h;  // rows g and g + 8 of the tile: pixel index r = 4 * oy + ox
+                rw.oy[0][h] = (g >> 2) + 2 * h;
                 rw.ox[0][h] = g & 3;
             }
-            float acc[1][2][4];
-            conv32<8, 1, 2>(A2, W3, rw, 2 * nh, acc, g, t);
+            float acc[1][1][4];
+            conv32<8, 1, 1>(A2, W3, rw, nt, acc, g, t);
 #pragma unroll
-            for (int j = 0; j < 2; ++j)
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int c = (2 * nh + j) * 8 + 2 * t;
-                    A3[((s * 4 + rw.oy[0][h]) * 4 + rw.ox[0][h]) * PXW + (2 * nh + j) * 4 + t] =
-                        pack_relu(acc[0][j][2 * h] + sb[2][c], acc[0][j][2 * h + 1] + sb[2][c + 1]);
-                }
+            for (int h = 0; h < 2; ++h) {
+                const int c = nt * 8 + 2 * t;
+                A3[((s * 4 + rw.oy[0][h]) * 4 + rw.ox[0][h]) * PXW + nt * 4 + t] =
+                    pack_relu(acc[0][0][2 * h] + sb[2][c], acc[0][0][2 * h + 1] + sb[2][c + 1]);
+            }
         }
         __syncthreads();
 
-        // ---- layer 4: 4x4x32 -> 2x2x32; one m-tile = 4 samples x 4 pixels; warp = n-tile ----
+        // ---- layer 4 (mma.sync): rows 4 * sample + pixel (rows 8-15 are padding) ----
         if (warp < 4) {
             Rows<1> rw;
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                rw.s[0][h] = (g >> 2) + 2 * h;  // row r = 4 * sample + pixel
+                rw.s[0][h] = h ? 0 : (g >> 2);
                 rw.oy[0][h] = (g & 3) >> 1;
                 rw.ox[0][h] = g & 1;
             }
             float acc[1][1][4];
             conv32<4, 1, 1>(A3, W4, rw, warp, acc, g, t);
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int s = rw.s[0][h], pix = (g & 3), c = warp * 8 + 2 * t;
-                if (s < ns) {
-                    const uint32_t v = pack_relu(acc[0][0][2 * h] + sb[3][c], acc[0][0][2 * h + 1] + sb[3][c + 1]);
-                    *reinterpret_cast<uint32_t*>(a4 + ((size_t)(s0 + s) * 4 + pix) * CH + c) = v;
-                }
+            const int s = g >> 2, pix = g & 3, c = warp * 8 + 2 * t;
+            if (s < ns) {
+                const uint32_t v = pack_relu(acc[0][0][0] + sb[3][c], acc[0][0][1] + sb[3][c + 1]);
+                *reinterpret_cast<uint32_t*>(a4 + ((size_t)(s0 + s) * 4 + pix) * CH + c) = v;
             }
         }
     }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (s_fail && tid == 0 && status) atomicOr(status, 1u);
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem) : "memory");
 }
 
 // ------------------------------------------------------------------ im2col / col2im
@@ -634,25 +735,26 @@ cudaError_t relu_back(const float* da, const __nv_bfloat16* a, long rows, __nv_b
     return cudaGetLastError();
 }
 
-size_t trunk_smem_bytes()
+size_t trunk_tc_smem_bytes()
 {
-    static_assert(TS * 1024 <= TS * (64 + 16) * PXW, "the feature planes fit in the layer-2/3 buffers");
-    return sizeof(uint32_t) * ((size_t)TS * (256 + 64 + 16) * PXW);
+    return 1024 + (size_t)TC_A1 + TC_W2 + sizeof(uint32_t) * (size_t)TC_S * (64 + 16) * PXW;
 }
 
-cudaError_t trunk(const PropFrame* frames, int nframes, long sbase, int n, const __nv_bfloat16* const* w,
-                  const float* params, __nv_bfloat16* a4, int num_sms, cudaStream_t st)
+cudaError_t trunk_tc(const PropFrame* frames, int nframes, long sbase, int n, const __nv_bfloat16* const* w,
+                     const float* params, __nv_bfloat16* a4, unsigned* status, int num_sms, cudaStream_t st)
 {
+    static_assert(TC_S * 1024 <= TC_S * (64 + 16) * PXW, "the feature planes fit in the layer-2/3 buffers");
     TrunkW tw;
     for (int l = 0; l < LAYERS; ++l) {
         tw.w[l] = w[l];
         tw.b[l] = params + PB[l];
     }
-    const size_t smem = trunk_smem_bytes();
-    cudaError_t e = cudaFuncSetAttribute(trunk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = trunk_tc_smem_bytes();
+    cudaError_t e = cudaFuncSetAttribute(trunk_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const int groups = (n + TS - 1) / TS;
-    trunk_kernel<<<std::max(1, std::min(groups, 2 * num_sms)), 256, smem, st>>>(frames, nframes, sbase, n, tw, a4);
+    const int groups = (n + TC_S - 1) / TC_S;
+    trunk_tc_kernel<<<std::max(1, std::min(groups, 3 * num_sms)), 256, smem, st>>>(frames, nframes, sbase, n, tw, a4,
+                                                                                 status);
     return cudaGetLastError();
 }
 

@@ -61,11 +61,13 @@ struct PropFrame {
 
 // Inference trunk for the n blocks sbase .. sbase + n - 1 of the frame table
 // (blocks numbered through the frames' bases): features from the frames, then
-// the four layers, writing conv-4 activations a4 ([n][2][2][32] bf16) in one
+// the four layers (layer 2 on tcgen05 with TMEM accumulators, layers 1, 3 and
+// 4 on mma.sync), writing conv-4 activations a4 ([n][2][2][32] bf16) in one
 // launch (no im2col).  w: the four GEMM-layout weights [32][KP[l]]; params:
-// canonical parameters (biases at PB[l]).
-cudaError_t trunk(const PropFrame* frames, int nframes, long sbase, int n, const __nv_bfloat16* const* w,
-                  const float* params, __nv_bfloat16* a4, int num_sms, cudaStream_t st);
+// canonical parameters (biases at PB[l]); status (nullable) receives bit 1 if
+// the bounded wait for the tensor cores gave up.
+cudaError_t trunk_tc(const PropFrame* frames, int nframes, long sbase, int n, const __nv_bfloat16* const* w,
+                     const float* params, __nv_bfloat16* a4, unsigned* status, int num_sms, cudaStream_t st);
 
 }  // namespace cnn
 }  // namespace me

@@ -553,7 +553,7 @@ cudaError_t forward(me_proposal* P, const Ws& w, int n, bool head, cudaStream_t 
 cudaError_t forward_infer(me_proposal* P, int nframes, long s0, const Ws& w, int n, __nv_bfloat16* a4, bool head,
                           cudaStream_t st)
 {
-    cudaError_t e = trunk(P->frames, nframes, s0, n, P->w, P->p, a4, P->ctx->num_sms, st);
+    cudaError_t e = trunk_tc(P->frames, nframes, s0, n, P->w, P->p, a4, P->ctx->status, P->ctx->num_sms, st);
     if (e == cudaSuccess && head) e = head_fwd(a4, w.mvf, n, P->p + P_FW, P->p + P_FB, w.logits, st);
     return e;
 }
