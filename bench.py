@@ -379,6 +379,21 @@ def main():
     st_f = [ctx.me_stats_from_sums(s_f[i]) for i in range(npairs)]
     mean = lambda rows, k: float(np.mean([r[k] for r in rows]))
 
+    # ---- Sec. II-C statistics of the FS field (the directional model's inputs) ----
+    from paper_0806_0689_gb300 import mvp
+    mvp_counts = torch.zeros(35 * (2 * R_ + 1) ** 2, dtype=torch.int64, device=dev)
+    ctx.me_mvp_stats(d_fs, R_, mvp_counts)
+    torch.cuda.synchronize()
+    hist, _, _ = mvp.unpack(mvp_counts.cpu().numpy(), R_)
+    P = mvp.probabilities(hist)
+    ax = mvp.axes_1d(P)
+    mvp_line = {"regions": mvp.regions(P),
+                "horizontal_axis_share": float(ax["Bx"].sum() - P[R_, R_]),
+                "vertical_axis_share": float(ax["By"].sum() - P[R_, R_]),
+                "var_x": mvp.moments(ax["Ax"])[1], "var_y": mvp.moments(ax["Ay"])[1],
+                "paper_regions": {"square5": 0.8745, "diamond5": 0.8557, "cross5": 0.8315, "square3": 0.7899,
+                                  "hcsp": 0.8248}}
+
     # ---- FS timed on its own (same batch) ----
     fs_ms = []
     for _ in range(3):
@@ -472,6 +487,7 @@ def main():
                             "frac": fs_absdiff / (fs_launch_ms * 1e-3) / sad_peak,
                             "peak_source": "measured byte-absdiff microbenchmark (me_absdiff_peak)"}},
         "absdiff_peak_per_s": {"variants": rates, "used": used},
+        "mvp_statistics_fs_field": mvp_line,
         "tuned_shape_index": tuned,
         "step_kernels": "dcds_kernel with the Sec. IV sums fused (one launch per step)",
         "search_only_ms": search_only_ms, "unfused_eval_ms": unfused_eval_ms,

@@ -282,6 +282,28 @@ int me_eval(me_ctx* ctx, const uint8_t* cur, const uint8_t* ref, int w, int h, i
 int me_eval_batch(me_ctx* ctx, const me_eval_desc* descs, int n, int block,
                   uint64_t* sums, void* stream);
 
+/* me_mvp_stats: the motion-vector probability statistics of Sec. II-C
+ * (Tables II-V) over full-search fields, for 16x16 blocks.  descs[i].mv is
+ * frame i's FS field (input, [nb][2] int16), descs[i].range its search range
+ * (at most `range`); sad and nsp are not used.  out (DEVICE uint64,
+ * 8-byte aligned, overwritten) receives, with Q = (2*range + 1)^2 and
+ * q(dx, dy) = (dy + range) * (2*range + 1) + (dx + range):
+ *   out[q]                 blocks whose FS MV (the global best-matched point,
+ *                          eq. (5)) is (dx, dy)              -- Tables II, III
+ *   out[Q + p*Q + q]       blocks whose current best-matched point (eq. (3))
+ *                          in S1 is point p and whose FS MV is q: the prior
+ *                          distribution D1 of eq. (4)        -- Table IV
+ *   out[10*Q + q*25 + i]   blocks whose FS MV is q and whose current
+ *                          best-matched point in S2 is point i: the
+ *                          posterior distribution D2 of eq. (6) -- Table V
+ * S1 = the first step of CDS as in the paper's example, in the order
+ * (0,0), (-2,0), (-1,0), (1,0), (2,0), (0,2), (0,1), (0,-1), (0,-2);
+ * S2 = the 5x5 square, point i = (i % 5 - 2, i / 5 - 2).  A set's current
+ * best-matched point is the strict SAD minimum over its points inside the
+ * window and the frame, compared with the centre first, then in the set's
+ * order.  35 * Q values in all. */
+int me_mvp_stats(me_ctx* ctx, const me_frame_desc* descs, int n, int range, uint64_t* out, void* stream);
+
 typedef struct me_stats {
     double mad, mse, nsp, psnr, distance, probability;
 } me_stats;

@@ -325,6 +325,50 @@ def median_dcds(cur, ref, rng):
     return mv, sd, ns, starts
 
 
+def mvp_counts(frames, R):
+    """Counts of the Sec. II-C statistics (the layout of me_mvp_stats) for 16x16
+    blocks.  frames: list of (cur, ref, mv_fs, range).  Each block's current
+    best-matched point in a set is the strict SAD minimum over the set's points
+    inside the window and the frame, the centre compared first."""
+    side = 2 * R + 1
+    q = side * side
+    out = np.zeros(35 * q, np.int64)
+    s1 = [(0, 0), (-2, 0), (-1, 0), (1, 0), (2, 0), (0, 2), (0, 1), (0, -1), (0, -2)]
+    s2 = [(0, 0)] + [(i % 5 - 2, i // 5 - 2) for i in range(25) if i != 12]
+    for cur, ref, mv_fs, rf in frames:
+        cur_c, ref_c = _frames(cur, ref)
+        h, w = cur_c.shape
+        nbx = w // 16
+        for k in range(nbx * (h // 16)):
+            bx, by = k % nbx, k // nbx
+            px, py = bx * 16, by * 16
+
+            def ok(dx, dy):
+                return -rf <= dx <= rf and -rf <= dy <= rf and 0 <= px + dx <= w - 16 and 0 <= py + dy <= h - 16
+
+            def best(points):
+                bi, bs = None, None
+                for i, (dx, dy) in enumerate(points):
+                    if not ok(dx, dy):
+                        continue
+                    s = sad(cur_c, ref_c, px, py, 16, dx, dy)
+                    if bs is None or s < bs:
+                        bi, bs = i, s
+                return bi
+
+            p1 = best(s1)
+            p2s = s2[best(s2)]
+            p2 = (p2s[1] + 2) * 5 + (p2s[0] + 2)
+            qx, qy = int(mv_fs[k][0]), int(mv_fs[k][1])
+            if abs(qx) > R or abs(qy) > R:
+                continue
+            qi = (qy + R) * side + (qx + R)
+            out[qi] += 1
+            out[q + p1 * q + qi] += 1
+            out[10 * q + qi * 25 + p2] += 1
+    return out
+
+
 def learned_dcds(cur, ref, rng, params):
     """Learned-start DCDS of a frame, 16x16 blocks, blocks in raster order (the
     left, top and top-right neighbours are final before a block starts).

@@ -552,6 +552,57 @@ int me_eval_batch(me_ctx* c, const me_eval_desc* d, int n, int block, uint64_t* 
     return ME_OK;
 }
 
+int me_mvp_stats(me_ctx* c, const me_frame_desc* d, int n, int range, uint64_t* out, void* stream)
+{
+    if (!c) return ME_ERR_ARG;
+    if (!d || n <= 0 || !out) return fail(c, ME_ERR_ARG, "descs and out must not be NULL, n positive");
+    if (!aligned(out, 8)) return fail(c, ME_ERR_ARG, "out must be 8-byte aligned");
+    if (range < 1 || range > ME_MAX_RANGE) return fail(c, ME_ERR_ARG, "range must be in 1..32");
+    long total = 0;
+    for (int i = 0; i < n; ++i) {
+        if (!d[i].cur || !d[i].ref || !d[i].mv) return fail(c, ME_ERR_ARG, "cur, ref and mv must not be NULL");
+        if (!aligned(d[i].cur, 16) || !aligned(d[i].ref, 16) || !aligned(d[i].mv, 4))
+            return fail(c, ME_ERR_ARG, "cur/ref must be 16-byte aligned, mv 4-byte aligned");
+        if (d[i].w <= 0 || d[i].h <= 0 || d[i].w % 16 || d[i].h % 16 || d[i].pitch < d[i].w || d[i].pitch % 16)
+            return fail(c, ME_ERR_ARG, "16x16 blocks: w and h multiples of 16, pitch >= w and a multiple of 16");
+        if (d[i].range < 1 || d[i].range > range) return fail(c, ME_ERR_ARG, "every frame's range must be in 1..range");
+        total += (long)(d[i].w / 16) * (d[i].h / 16);
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t tbl = sizeof(EvalDev) * (size_t)n, rng = ((sizeof(int) * (size_t)n) + 7) & ~size_t(7);
+    const size_t bytes = kHeadBytes + tbl + rng + sizeof(long) * (size_t)n;
+    Slot* slot = nullptr;
+    int rc = take_slot(c, bytes, &slot);
+    if (rc != ME_OK) return rc;
+    char* h = reinterpret_cast<char*>(slot->host);
+    EvalDev* table = reinterpret_cast<EvalDev*>(h + kHeadBytes);
+    int* ranges = reinterpret_cast<int*>(h + kHeadBytes + tbl);
+    long* bases = reinterpret_cast<long*>(h + kHeadBytes + tbl + rng);
+    long base = 0;
+    for (int i = 0; i < n; ++i) {
+        EvalDev f{};
+        f.cur = d[i].cur; f.ref = d[i].ref; f.mv = d[i].mv;
+        f.w = d[i].w; f.h = d[i].h; f.pitch = d[i].pitch; f.nbx = d[i].w / 16; f.nby = d[i].h / 16;
+        table[i] = f;
+        ranges[i] = d[i].range;
+        bases[i] = base;
+        base += (long)f.nbx * f.nby;
+    }
+    const size_t nq = (size_t)(2 * range + 1) * (2 * range + 1);
+    char* dv = reinterpret_cast<char*>(slot->dev);
+    cudaError_t e = cudaMemcpyAsync(slot->dev, slot->host, bytes, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(out, 0, sizeof(uint64_t) * 35 * nq, st);
+    if (e == cudaSuccess)
+        e = me::launch_mvp(reinterpret_cast<const EvalDev*>(dv + kHeadBytes),
+                           reinterpret_cast<const int*>(dv + kHeadBytes + tbl),
+                           reinterpret_cast<const long*>(dv + kHeadBytes + tbl + rng), n, total, range, c->num_sms,
+                           reinterpret_cast<unsigned long long*>(out), st);
+    if (e == cudaSuccess) e = cudaEventRecord(slot->done, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "motion-vector statistics launch");
+    slot->used = true;
+    return ME_OK;
+}
+
 int me_eval(me_ctx* c, const uint8_t* cur, const uint8_t* ref, int w, int h, int block, const int16_t* mv,
             const int16_t* mv_fs, const uint16_t* nsp, uint64_t* sums, void* stream)
 {

@@ -165,6 +165,12 @@ bool encode_fs_maps(FrameDev& f, int nch, int rows, int cur_w, int block);
 cudaError_t launch_eval(const EvalDev* frames, int nframes, int block, int max_blocks, int num_sms,
                         unsigned long long* sums, cudaStream_t st);
 
+// Motion-vector statistics (16x16 blocks): frames[i].mv is the FS field,
+// ranges[i] its search range, bases[i] its first block; out (zeroed) receives
+// [(2R+1)^2] histogram, [9][(2R+1)^2] D1 counts, [(2R+1)^2][25] D2 counts.
+cudaError_t launch_mvp(const EvalDev* frames, const int* ranges, const long* bases, int nframes, long total, int R,
+                       int num_sms, unsigned long long* out, cudaStream_t st);
+
 cudaError_t launch_absdiff_peak(int variant, int iters, int blocks, int threads, unsigned* sink,
                                 cudaStream_t st);
 
