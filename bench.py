@@ -407,6 +407,27 @@ def main():
         torch.cuda.synchronize()
         fs_ms.append(e0.elapsed_time(e1))
 
+    # ---- both block sizes in one full-search sweep (8x8 outputs of the same batch) ----
+    nb8 = 4 * nb
+    mv8 = torch.empty((npairs, nb8, 2), dtype=torch.int16, device=dev)
+    sad8 = torch.empty((npairs, nb8), dtype=torch.int32, device=dev)
+    nsp8 = torch.empty((npairs, nb8), dtype=torch.int16, device=dev)
+    d8 = me.Context.frame_descs((curs[i], refs[i], R_, mv8[i], sad8[i], nsp8[i]) for i in range(npairs))
+
+    def _time2(fn, reps=3):
+        fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+    dual_ms = _time2(lambda: ctx.me_fs_dual_batch(d_fs, d8))
+    fs8_ms = _time2(lambda: ctx.me_estimate_batch(d8, 8, "fs"))
+    fs_dual = {"launch_ms": dual_ms, "fs16_ms": float(np.median(fs_ms)), "fs8_ms": fs8_ms,
+               "speedup_vs_two_searches": (float(np.median(fs_ms)) + fs8_ms) / dual_ms}
+
     # ---- end to end through the C-ABI with host buffers ----
     h_cur = torch.from_numpy(np.stack(seq[1:npairs + 1])).pin_memory()
     h_ref = torch.from_numpy(np.stack(seq[0:npairs])).pin_memory()
@@ -486,6 +507,7 @@ def main():
                             "peak": sad_peak / 1e12, "unit": "Tabsdiff/s",
                             "frac": fs_absdiff / (fs_launch_ms * 1e-3) / sad_peak,
                             "peak_source": "measured byte-absdiff microbenchmark (me_absdiff_peak)"}},
+        "fs_two_sizes_one_sweep": fs_dual,
         "absdiff_peak_per_s": {"variants": rates, "used": used},
         "mvp_statistics_fs_field": mvp_line,
         "tuned_shape_index": tuned,

@@ -155,6 +155,20 @@ int me_graph_create(me_ctx* ctx, const me_frame_desc* descs, int n, int block, i
 int me_graph_launch(me_ctx* ctx, me_graph* g, void* stream);
 void me_graph_free(me_graph* g);
 
+/* me_fs_dual_batch: the full search of every frame for 16x16 AND 8x8 blocks
+ * in one sweep (not in the paper; both block sizes of the CIF workload at
+ * once).  The 16x16 accumulation keeps its four 8x8 quadrants apart, so each
+ * 8x8 sub-block's SAD at every displacement of the +-range square comes out
+ * of the same pass; each field is the argmin of its own candidates (the
+ * 8x8 candidates limited by the 8x8 block's own frame borders) under the key
+ * (SAD, |dx|+|dy|, dy, dx).  Results equal me_estimate_batch(FS) with block 16
+ * on d16 and with block 8 on the 8x8 outputs.
+ *   d16: as for me_estimate_batch (block 16; w, h multiples of 16).
+ *   d8:  HOST array of n descriptors whose mv ([4 nb][2] int16), sad and nsp
+ *        (nullable) receive the 8x8 field (raster order over the frame's
+ *        2 nbx x 2 nby 8x8 blocks); its other fields are not used. */
+int me_fs_dual_batch(me_ctx* ctx, const me_frame_desc* d16, const me_frame_desc* d8, int n, void* stream);
+
 /* me_estimate_eval_batch: me_estimate_batch (DCDS or DCDS^S) with the
  * evaluation of Sec. IV fused into the search.  The search writes mv, sad
  * and nsp as me_estimate_batch does; in the same pass, from the tiles it has

@@ -31,6 +31,11 @@
 //     meet in a 64-bit shared-memory atomicMin on the packed key
 //     (SAD << 21 | (|dx|+|dy|) << 14 | (dy+32) << 7 | (dx+32)).
 //   * Every wait is bounded; a time-out sets STATUS_TIMEOUT and ends the CTA.
+//   * DUAL (16x16 blocks): the accumulators are kept per 8x8 quadrant, so the
+//     same sweep also yields the full search of the four 8x8 sub-blocks (their
+//     SADs at every displacement of the +-R square; a 16x16 SAD is the sum of
+//     its quadrants' at the same displacement), each with its own validity and
+//     key -- both block sizes of a frame for the price of the 16x16 search.
 #include "dcds_common.cuh"
 
 #include <algorithm>
@@ -88,17 +93,21 @@ __device__ __forceinline__ void fs_issue(int t, const FrameDev* frames, int nfra
     tma_load_2d(cur, &F.tm_cur, x0, y0, bar);
 }
 
-template <int B, int K>
+template <int B, int K, bool DUAL>
 __global__ void __launch_bounds__(256, 2) fs_kernel(const FrameDev* __restrict__ frames, int nframes, int ntiles,
                                                     int* __restrict__ counter, unsigned* __restrict__ status,
                                                     FsArgs a)
 {
+    static_assert(!DUAL || B == 16, "the two-size sweep runs over 16x16 blocks");
     constexpr int V = kSadVariant;
     constexpr int BW = B / 4;
+    constexpr int NQ = DUAL ? 4 : 1;  // accumulators per candidate: the 8x8 quadrants, or the block
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t s_bar[2];
     __shared__ unsigned long long s_key[kMaxTx];
+    __shared__ unsigned long long s_key8[DUAL ? 4 * kMaxTx : 1];  // DUAL: 8x8 blocks (2 rows x 2 tx)
     __shared__ uint32_t s_dkey[kDyTable];
+    __shared__ uint32_t s_dkey8[DUAL ? 2 : 1][kDyTable];          // DUAL: rows of the upper / lower 8x8
     __shared__ int s_tile[2], s_frame[2], s_fail;
 
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
@@ -111,6 +120,8 @@ __global__ void __launch_bounds__(256, 2) fs_kernel(const FrameDev* __restrict__
     const int lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
 
     for (int i = tid; i < kMaxTx; i += blockDim.x) s_key[i] = ~0ull;
+    if constexpr (DUAL)
+        for (int i = tid; i < 4 * kMaxTx; i += blockDim.x) s_key8[i] = ~0ull;
     if (tid == 0) {
         s_fail = 0;
         mbar_init(&s_bar[0], 1);
@@ -158,7 +169,15 @@ __global__ void __launch_bounds__(256, 2) fs_kernel(const FrameDev* __restrict__
         // dy part of the candidate key; bit 31 marks a row outside the frame or the range
         for (int i = tid; i < kDyTable; i += blockDim.x) {
             const int dy = i - 32;
-            s_dkey[i] = (dy >= dylo && dy <= dyhi) ? ((uint32_t)abs(dy) << 7) | (uint32_t)(dy + 32) : kDyInvalid;
+            const uint32_t v = ((uint32_t)abs(dy) << 7) | (uint32_t)(dy + 32);
+            s_dkey[i] = (dy >= dylo && dy <= dyhi) ? v : kDyInvalid;
+            if constexpr (DUAL) {
+#pragma unroll
+                for (int qy = 0; qy < 2; ++qy) {
+                    const int lo = max(-R, -(py + 8 * qy)), hi = min(R, H - 8 - (py + 8 * qy));
+                    s_dkey8[qy][i] = (dy >= lo && dy <= hi) ? v : kDyInvalid;
+                }
+            }
         }
 
         // ---- expand the raw window: E[r][c] = bytes c..c+3 of window row r ----
@@ -207,9 +226,11 @@ __global__ void __launch_bounds__(256, 2) fs_kernel(const FrameDev* __restrict__
                 for (int w = 0; w < BW; ++w) cb[r][w] = curw[r * cwpr + b * BW + w];
 
             const uint32_t* ep = E + dyg * K * P + b * B + rx + dx;
-            uint32_t acc[K];
+            uint32_t acc[K][NQ];  // DUAL: quadrant (r / 8) * 2 + (w / 2) of the 16x16 block
 #pragma unroll
-            for (int i = 0; i < K; ++i) acc[i] = 0u;
+            for (int i = 0; i < K; ++i)
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) acc[i][q] = 0u;
 #pragma unroll
             for (int j = 0; j < K + B - 1; ++j) {
                 uint32_t rw[BW];
@@ -221,7 +242,10 @@ __global__ void __launch_bounds__(256, 2) fs_kernel(const FrameDev* __restrict__
                     const int r = j - i;
                     if (r >= 0 && r < B) {
 #pragma unroll
-                        for (int w = 0; w < BW; ++w) acc[i] = sadacc<V>(rw[w], cb[r][w], acc[i]);
+                        for (int w = 0; w < BW; ++w) {
+                            const int q = DUAL ? (r >> 3) * 2 + (w >> 1) : 0;
+                            acc[i][q] = sadacc<V>(rw[w], cb[r][w], acc[i][q]);
+                        }
                     }
                 }
             }
@@ -229,10 +253,32 @@ __global__ void __launch_bounds__(256, 2) fs_kernel(const FrameDev* __restrict__
             const uint32_t* dk = s_dkey + dy0 + 32;
             uint32_t best = 0xffffffffu;
 #pragma unroll
-            for (int i = 0; i < K; ++i) best = min(best, acc[i] * 16384u + dk[i]);
+            for (int i = 0; i < K; ++i) {
+                uint32_t sum = acc[i][0];
+#pragma unroll
+                for (int q = 1; q < NQ; ++q) sum += acc[i][q];
+                best = min(best, sum * 16384u + dk[i]);
+            }
             if (best < kDyInvalid && px + dx >= 0 && px + dx <= W - B) {
                 const uint32_t key = best + ((uint32_t)abs(dx) << 7);  // (SAD, |dx|+|dy|, dy)
                 atomicMin(&s_key[b], ((unsigned long long)key << 7) | (unsigned long long)(dx + 32));
+            }
+            if constexpr (DUAL) {
+                // the four 8x8 sub-blocks at the same displacements, each with its own window / frame limits
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int qy = q >> 1, qx = q & 1;
+                    const uint32_t* dk8 = s_dkey8[qy] + dy0 + 32;
+                    uint32_t b8 = 0xffffffffu;
+#pragma unroll
+                    for (int i = 0; i < K; ++i) b8 = min(b8, acc[i][q] * 16384u + dk8[i]);
+                    const int px8 = px + 8 * qx;
+                    if (b8 < kDyInvalid && px8 + dx >= 0 && px8 + dx <= W - 8) {
+                        const uint32_t key = b8 + ((uint32_t)abs(dx) << 7);
+                        atomicMin(&s_key8[(2 * b + qx) * 2 + qy],
+                                  ((unsigned long long)key << 7) | (unsigned long long)(dx + 32));
+                    }
+                }
             }
         }
         __syncthreads();
@@ -250,6 +296,24 @@ __global__ void __launch_bounds__(256, 2) fs_kernel(const FrameDev* __restrict__
             F.sad[blk] = (uint32_t)(key >> 21);
             if (F.nsp) F.nsp[blk] = (uint16_t)(nx * ny);
         }
+        if constexpr (DUAL) {
+            // the 8x8 field: blocks (2 (bx0 + b) + qx, 2 by + qy) of a frame 2 * nbx blocks wide
+            for (int i = tid; i < 4 * nbx_t; i += blockDim.x) {
+                const int qy = i & 1, c8 = i >> 1;  // c8 = 2 b + qx
+                const unsigned long long key = s_key8[i];
+                s_key8[i] = ~0ull;
+                const int dx = (int)(key & 127ull) - 32;
+                const int dy = (int)((key >> 7) & 127ull) - 32;
+                const int px8 = bx0 * B + 8 * c8, py8 = by * B + 8 * qy;
+                const int nx = min(R, W - 8 - px8) - max(-R, -px8) + 1;
+                const int ny = min(R, H - 8 - py8) - max(-R, -py8) + 1;
+                const size_t blk8 = (size_t)(2 * by + qy) * (2 * F.nbx) + 2 * bx0 + c8;
+                *reinterpret_cast<uint32_t*>(F.mv8 + 2 * blk8) =
+                    (uint32_t)(uint16_t)dx | ((uint32_t)(uint16_t)dy << 16);
+                F.sad8[blk8] = (uint32_t)(key >> 21);
+                if (F.nsp8) F.nsp8[blk8] = (uint16_t)(nx * ny);
+            }
+        }
         // the next iteration's first barrier orders these resets before the next search
     }
 }
@@ -261,12 +325,12 @@ int inv_mod32(int k)
     return 1;
 }
 
-template <int B, int K>
+template <int B, int K, bool DUAL>
 cudaError_t launch_t(const FrameDev* frames, int nframes, int ntiles, int max_range, const Shape& s, int* counter,
                      unsigned* status, int num_sms, cudaStream_t st)
 {
     const FsGeom g = fs_geom(B, max_range, s.tx, K);
-    auto kern = fs_kernel<B, K>;
+    auto kern = fs_kernel<B, K, DUAL>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
@@ -319,11 +383,18 @@ size_t fs_smem_bytes(int block, int max_range, const Shape& s)
 }
 
 cudaError_t launch_fs(const FrameDev* frames, int nframes, int ntiles, int block, int max_range, const Shape& s,
-                      int* counter, unsigned* status, int num_sms, cudaStream_t st)
+                      int* counter, unsigned* status, int num_sms, cudaStream_t st, bool dual)
 {
     if (!fs_shape_ok(block, max_range, s)) return cudaErrorInvalidValue;
+    if (dual) {
+        if (block != 16) return cudaErrorInvalidValue;
+        // quadrant accumulators: rows of work per thread kept small (registers)
+        if (s.k == 9) return launch_t<16, 9, true>(frames, nframes, ntiles, max_range, s, counter, status, num_sms, st);
+        if (s.k == 11) return launch_t<16, 11, true>(frames, nframes, ntiles, max_range, s, counter, status, num_sms, st);
+        return cudaErrorInvalidValue;
+    }
 #define ME_FS_CASE(BB, KK) \
-    if (block == BB && s.k == KK) return launch_t<BB, KK>(frames, nframes, ntiles, max_range, s, counter, status, num_sms, st);
+    if (block == BB && s.k == KK) return launch_t<BB, KK, false>(frames, nframes, ntiles, max_range, s, counter, status, num_sms, st);
     ME_FS_CASE(16, 9) ME_FS_CASE(16, 11) ME_FS_CASE(16, 13) ME_FS_CASE(16, 15)
     ME_FS_CASE(8, 9) ME_FS_CASE(8, 11) ME_FS_CASE(8, 13) ME_FS_CASE(8, 15)
     ME_FS_CASE(16, 33) ME_FS_CASE(8, 33)

@@ -189,10 +189,12 @@ int ensure_queue(me_ctx* c, void** q, size_t* qcap, size_t entries)
 // Fill the device-side table (tiles per frame, TMA maps for DCDS) into
 // `table`; returns the number of tiles, or -1 if a tensor map is rejected.
 // Fused evaluation of a DCDS batch: mv_fs (host array of n device pointers,
-// nullable) and the device sums [n][ME_NSUMS].
+// nullable) and the device sums [n][ME_NSUMS].  d8 (FS only): the 8x8 outputs
+// of the two-size full search.
 struct EvalArgs {
     const int16_t* const* mv_fs = nullptr;
     uint64_t* sums = nullptr;
+    const me_frame_desc* d8 = nullptr;
 };
 
 int build_table(const me_frame_desc* d, int n, int block, const Shape& s, bool fs, FrameDev* table,
@@ -226,6 +228,11 @@ int build_table(const me_frame_desc* d, int n, int block, const Shape& s, bool f
         if (ev && ev->sums) {
             f.sums = reinterpret_cast<unsigned long long*>(ev->sums) + (size_t)ME_NSUMS * i;
             f.mv_fs = ev->mv_fs ? ev->mv_fs[i] : nullptr;
+        }
+        if (ev && ev->d8) {
+            f.mv8 = ev->d8[i].mv;
+            f.sad8 = ev->d8[i].sad;
+            f.nsp8 = ev->d8[i].nsp;
         }
         f.tile_base = tiles;
         tiles += f.tiles_x * f.tiles_y;
@@ -271,7 +278,9 @@ cudaError_t launch_search(me_ctx* c, void* dev, void* queue, size_t qcap, int n,
         return me::launch_dcds(table, n, ntiles, block, max_range, algo == ME_ALGO_DCDS_S, t, head, c->status,
                                c->num_sms, st, true);
     }
-    if (algo == ME_ALGO_FS) return me::launch_fs(table, n, ntiles, block, max_range, s, head, c->status, c->num_sms, st);
+    if (algo == ME_ALGO_FS)
+        return me::launch_fs(table, n, ntiles, block, max_range, s, head, c->status, c->num_sms, st,
+                             ev && ev->d8);
     if (s.kernel == 1)
         return me::launch_dcds_ws(table, n, ntiles, block, max_range, algo == ME_ALGO_DCDS_S, s, head, queue,
                                   (int)qcap, c->status, c->num_sms, st);
@@ -496,6 +505,29 @@ int me_estimate_eval_batch(me_ctx* c, const me_frame_desc* descs, const int16_t*
     ev.mv_fs = mv_fs;
     ev.sums = sums;
     return run_batch(c, descs, n, block, algo, pick_shape(c, algo, block, mr, mw, mh), (cudaStream_t)stream, &ev);
+}
+
+int me_fs_dual_batch(me_ctx* c, const me_frame_desc* d16, const me_frame_desc* d8, int n, void* stream)
+{
+    if (!c) return ME_ERR_ARG;
+    int rc = validate_batch(c, d16, n, 16, ME_ALGO_FS);
+    if (rc != ME_OK) return rc;
+    if (!d8) return fail(c, ME_ERR_ARG, "d8 must not be NULL");
+    int mr = 1, mw = 0, mh = 0;
+    for (int i = 0; i < n; ++i) {
+        if (!d8[i].mv || !d8[i].sad) return fail(c, ME_ERR_ARG, "8x8 mv and sad must not be NULL");
+        if (!aligned(d8[i].mv, 4) || !aligned(d8[i].sad, 4) || (d8[i].nsp && !aligned(d8[i].nsp, 2)))
+            return fail(c, ME_ERR_ARG, "8x8 mv/sad must be 4-byte aligned, nsp 2-byte aligned");
+        mr = std::max(mr, d16[i].range); mw = std::max(mw, d16[i].w); mh = std::max(mh, d16[i].h);
+    }
+    // the quadrant accumulators need the short task heights (9 or 11 candidate rows)
+    Shape s = pick_shape(c, ME_ALGO_FS, 16, mr, mw, mh);
+    const int n1 = 2 * mr + 1;
+    s.k = (((n1 + 8) / 9) * 12 <= ((n1 + 10) / 11) * 14) ? 9 : 11;
+    s.tx = fs_pick_tx(16, mr, s.k);
+    EvalArgs ev;
+    ev.d8 = d8;
+    return run_batch(c, d16, n, 16, ME_ALGO_FS, s, (cudaStream_t)stream, &ev);
 }
 
 int me_graph_launch(me_ctx* c, me_graph* g, void* stream)

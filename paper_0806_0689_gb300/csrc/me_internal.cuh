@@ -30,6 +30,9 @@ struct __align__(128) FrameDev {
     int32_t pad_[1];
     const int16_t* mv_fs;      // fused evaluation: the full-search field (may be null)
     unsigned long long* sums;  // fused evaluation: the frame's eight sums (null: no evaluation)
+    int16_t* mv8;              // two-size full search: the 8x8 field (null: not requested)
+    uint32_t* sad8;
+    uint16_t* nsp8;
 };
 
 // Encode the two tensor maps of `f` (its pointers, sizes and range must be
@@ -131,7 +134,7 @@ size_t dcds_stream_smem_bytes(int block, int max_range, const Shape& s);
 // Shape: threads 256, tx blocks per tile with tx*block <= 256 (tx even for
 // block 8), k in {9, 11, 13, 15} candidate rows per thread.
 cudaError_t launch_fs(const FrameDev* frames, int nframes, int ntiles, int block, int max_range, const Shape& s,
-                      int* counter, unsigned* status, int num_sms, cudaStream_t st);
+                      int* counter, unsigned* status, int num_sms, cudaStream_t st, bool dual = false);
 size_t fs_smem_bytes(int block, int max_range, const Shape& s);
 bool fs_shape_ok(int block, int max_range, const Shape& s);
 

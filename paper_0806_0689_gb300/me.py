@@ -27,7 +27,8 @@ EXPORTS = ["me_init", "me_free", "me_last_error", "me_estimate", "me_estimate_ba
            "me_absdiff_peak", "me_check_status", "me_estimate_batch_noalloc", "me_tune_batch",
            "me_proposal_create", "me_proposal_free", "me_proposal_set_params", "me_proposal_get_params",
            "me_proposal_train_step", "me_proposal_logits", "me_estimate_learned_batch",
-           "me_estimate_eval_batch", "me_graph_create_eval", "me_estimate_median_batch", "me_mvp_stats"]
+           "me_estimate_eval_batch", "me_graph_create_eval", "me_estimate_median_batch", "me_mvp_stats",
+           "me_fs_dual_batch"]
 ME_PROPOSAL_NPARAMS = 37532
 ME_PROPOSAL_NLOGITS = 68
 
@@ -277,6 +278,10 @@ class Context:
     def me_estimate_learned_batch(self, prop, descs, starts=None, stream=None):
         self._check(self.L.me_estimate_learned_batch(self.h, prop, descs, len(descs), _ptr(starts),
                                                      _stream(stream)))
+
+    def me_fs_dual_batch(self, d16, d8, stream=None):
+        """Full search for 16x16 (d16) and 8x8 (d8: outputs only) in one sweep."""
+        self._check(self.L.me_fs_dual_batch(self.h, d16, d8, len(d16), _stream(stream)))
 
     def me_mvp_stats(self, descs, rng, out, stream=None):
         """Counts of the Sec. II-C statistics; out: device int64 [35 * (2*rng+1)**2]."""

@@ -356,3 +356,24 @@ def test_dcds_shape_graph_replays(tmp_path, qcif, shape):
         c2.me_check_status()
     finally:
         c2.close()
+
+
+@pytest.mark.parametrize("R", [1, 7, 15, 32])
+def test_fs_dual_sizes_match_oracle(ctx, cif, qcif, R):
+    """One sweep gives the 16x16 and the 8x8 full searches, each bit-exact."""
+    pairs = [(cif[2], cif[1]), (qcif[4], qcif[3]), (cif[4], cif[3])]
+    items16, items8, keep = [], [], []
+    for cur, ref in pairs:
+        h, w = cur.shape
+        c, r = _dev(cur), _dev(ref)
+        o16 = _outs(h, w, 16)
+        o8 = _outs(h, w, 8)
+        keep.append((cur, ref, o16, o8))
+        items16.append((c, r, R) + o16)
+        items8.append((c, r, R) + o8)
+    ctx.me_fs_dual_batch(me.Context.frame_descs(items16), me.Context.frame_descs(items8))
+    torch.cuda.synchronize()
+    ctx.me_check_status()
+    for cur, ref, o16, o8 in keep:
+        assert_same(_host(*o16), oracle.fs(cur, ref, 16, R), f"dual 16x16 R{R}")
+        assert_same(_host(*o8), oracle.fs(cur, ref, 8, R), f"dual 8x8 R{R}")
