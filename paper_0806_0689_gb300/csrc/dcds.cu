@@ -48,6 +48,41 @@ namespace {
 using namespace dcds;
 
 // Sec. IV measures of one finished block into the thread's sums.
+// SADs of NP candidates (slots i0 .. i0 + NP - 1 of qx / qy) of a 4-lane group:
+// lane l4 holds RPL rows of one 4-byte column of the block (cb); the loads of
+// all NP points are issued together, then each sum is completed across the
+// group (every lane of the warp takes part in the shuffles).
+template <int NP, int V, int RPL>
+__device__ __forceinline__ void eval_points(const uint8_t* win, int WP, int wx0, int wy0, const int (&qx)[4],
+                                            const int (&qy)[4], const uint32_t (&cb)[RPL], uint32_t (&sad)[4], int i0)
+{
+    const uint8_t* p[NP];
+    unsigned sh[NP];
+    uint32_t a[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+        const int c = wx0 + qx[i0 + k];
+        p[k] = win + (wy0 + qy[i0 + k]) * WP + (c & ~3);
+        sh[k] = (unsigned)(c & 3) * 8u;
+        a[k] = 0u;
+    }
+#pragma unroll
+    for (int r = 0; r < RPL; ++r) {
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            const uint32_t l = *reinterpret_cast<const uint32_t*>(p[k] + r * WP);
+            const uint32_t h = *reinterpret_cast<const uint32_t*>(p[k] + r * WP + 4);
+            a[k] = sadacc<V>(__funnelshift_r(l, h, sh[k]), cb[r], a[k]);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+        a[k] += __shfl_xor_sync(0xffffffffu, a[k], 1);
+        a[k] += __shfl_xor_sync(0xffffffffu, a[k], 2);
+        sad[i0 + k] = a[k];
+    }
+}
+
 // Sec. IV sums of one finished block into the thread's tile sums e = {ABS, SQ,
 // NSP, EQUAL, PIXELS} (32 bits hold a tile's worth) and dist.  fw: the block's
 // full-search MV.
@@ -364,31 +399,15 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
                     qx[i] = cx + ox;  // unused slots read the centre: a valid address
                     qy[i] = cy + oy;
                 }
-                const bool more = __any_sync(FULL, ncand > 2);
-#pragma unroll
-                for (int half = 0; half < 2; ++half) {
-                    if (half == 1 && !more) break;
-                    const int i0 = 2 * half;
-                    const int c0 = wx0 + qx[i0], c1 = wx0 + qx[i0 + 1];
-                    const uint8_t* p0 = win + (wy0 + qy[i0]) * WP + (c0 & ~3);
-                    const uint8_t* p1 = win + (wy0 + qy[i0 + 1]) * WP + (c1 & ~3);
-                    const unsigned s0 = (unsigned)(c0 & 3) * 8u, s1 = (unsigned)(c1 & 3) * 8u;
-                    uint32_t a0 = 0u, a1 = 0u;
-#pragma unroll
-                    for (int r = 0; r < RPL; ++r) {
-                        const uint32_t l0 = *reinterpret_cast<const uint32_t*>(p0 + r * WP);
-                        const uint32_t h0 = *reinterpret_cast<const uint32_t*>(p0 + r * WP + 4);
-                        const uint32_t l1 = *reinterpret_cast<const uint32_t*>(p1 + r * WP);
-                        const uint32_t h1 = *reinterpret_cast<const uint32_t*>(p1 + r * WP + 4);
-                        a0 = sadacc<V>(__funnelshift_r(l0, h0, s0), cb[r], a0);
-                        a1 = sadacc<V>(__funnelshift_r(l1, h1, s1), cb[r], a1);
-                    }
-                    a0 += __shfl_xor_sync(FULL, a0, 1);
-                    a1 += __shfl_xor_sync(FULL, a1, 1);
-                    a0 += __shfl_xor_sync(FULL, a0, 2);
-                    a1 += __shfl_xor_sync(FULL, a1, 2);
-                    sad[i0] = a0;
-                    sad[i0 + 1] = a1;
+                // a DDSP round after a move has 3 new points, a step-4 round at most 2:
+                // evaluate them in one pass of 2 or 3 (a 4th, which the pattern
+                // geometry rules out after the HCSP, would take one more pass)
+                const bool three = __any_sync(FULL, ncand > 2);
+                if (three) {
+                    eval_points<3, V, RPL>(win, WP, wx0, wy0, qx, qy, cb, sad, 0);
+                    if (__any_sync(FULL, ncand > 3)) eval_points<1, V, RPL>(win, WP, wx0, wy0, qx, qy, cb, sad, 3);
+                } else {
+                    eval_points<2, V, RPL>(win, WP, wx0, wy0, qx, qy, cb, sad, 0);
                 }
 
                 // ---- (4) best point of the list, then switching strategies (Sec. III-B) ----
