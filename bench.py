@@ -47,11 +47,33 @@ def _args():
     return p.parse_args()
 
 
+def rank_seed(rank):
+    """Each rank generates its own sequence: the shards share no frame."""
+    return 2000 + 7 * rank
+
+
 def _frames(rank, npairs):
     """Seeded synthetic 1080p sequence; pair i = (frame i+1, frame i)."""
     from paper_0806_0689_gb300 import synth
-    seq = synth.workload_sequence("1080p", npairs + 1, seed=2000 + 7 * rank, max_motion=R_)
+    seq = synth.workload_sequence("1080p", npairs + 1, seed=rank_seed(rank), max_motion=R_)
     return seq
+
+
+def max_over_ranks(x, dist=None, device="cpu"):
+    """The slowest rank's time (all ranks receive it); x itself on one rank."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank_step, world, ms_total, steps):
+    """Whole-job throughput: the units all ranks processed per step over the
+    (slowest rank's) time per step.  Returns (units/s, ms per step)."""
+    ms_step = ms_total / steps
+    return units_per_rank_step * world / (ms_step * 1e-3), ms_step
 
 
 # ---------------------------------------------------------------- CPU oracle
@@ -242,8 +264,9 @@ def learned_leg(ctx, me, torch, dev, curs, refs, mv_plain, mv_fs, st_plain, nb, 
 # ---------------------------------------------------------------- reference arm
 
 def run_reference(a, rank, world):
+    """The reference arm (the CPU oracle): rank 0 alone runs and prints."""
     if rank != 0:
-        return
+        return None
     cb = cpu_baseline()
     line = {"impl": "reference", "metric": "DCDS macroblocks/s at 1080p", "value": cb["value"],
             "unit": "macroblocks/s", "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
@@ -253,6 +276,7 @@ def run_reference(a, rank, world):
             "e2e": {"value": cb["value"], "unit": "macroblocks/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+    return line
 
 
 # ---------------------------------------------------------------- our arm
@@ -364,13 +388,9 @@ def main():
     ctx.me_graph_launch(g_step)
     torch.cuda.synchronize()
     assert torch.equal(sums_sep, sums), "fused and separate evaluation sums differ"
-    if dist:
-        t = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
-    ms_step = ms_total / a.steps
+    ms_total = max_over_ranks(ms_total, dist, dev)
     mbs_step = npairs * nb
-    value = mbs_step * world / (ms_step * 1e-3)
+    value, ms_step = job_value(mbs_step, world, ms_total, a.steps)
 
     # ---- quality of the last step (identical every step) ----
     s_d = sums.cpu().numpy().view(np.uint64)
