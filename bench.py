@@ -449,39 +449,75 @@ def main():
                "speedup_vs_two_searches": (float(np.median(fs_ms)) + fs8_ms) / dual_ms}
 
     # ---- end to end through the C-ABI with host buffers ----
+    # me_estimate_host_batch uploads the frames (and the FS fields the sums
+    # need) from pinned host memory chunk by chunk, searches each chunk while
+    # the next uploads, and copies MV, SAD, NSP and the sums back.
     h_cur = torch.from_numpy(np.stack(seq[1:npairs + 1])).pin_memory()
     h_ref = torch.from_numpy(np.stack(seq[0:npairs])).pin_memory()
-    d_cur = torch.empty((npairs, H_, W_), dtype=torch.uint8, device=dev)
-    d_ref = torch.empty_like(d_cur)
+    h_fs = mv_fs.cpu().pin_memory()
+    h_fs_list = [h_fs[i] for i in range(npairs)]
     h_mv = torch.empty((npairs, nb, 2), dtype=torch.int16).pin_memory()
     h_sad = torch.empty((npairs, nb), dtype=torch.int32).pin_memory()
     h_nsp = torch.empty((npairs, nb), dtype=torch.int16).pin_memory()
     h_sums = torch.empty((npairs, me.ME_NSUMS), dtype=torch.int64).pin_memory()
-    de = me.Context.frame_descs((d_cur[i], d_ref[i], R_, mv[i], sad[i], nsp[i]) for i in range(npairs))
+    hd = me.Context.frame_descs((h_cur[i], h_ref[i], R_, h_mv[i], h_sad[i], h_nsp[i]) for i in range(npairs))
 
-    def e2e_step():
-        d_cur.copy_(h_cur, non_blocking=True)
-        d_ref.copy_(h_ref, non_blocking=True)
-        ctx.me_estimate_eval_batch(de, fs_list, B_, "dcds", sums)
-        h_mv.copy_(mv, non_blocking=True)
-        h_sad.copy_(sad, non_blocking=True)
-        h_nsp.copy_(nsp, non_blocking=True)
-        h_sums.copy_(sums, non_blocking=True)
+    stream_b = torch.cuda.Stream(device=dev)
 
+    def _e2e_ms(descs, chunk, k, two_streams=True):
+        """Steps issued on two streams in turn (the library alternates two
+        staging sets, so one step's uploads run while the previous step's
+        last chunk is searched), or all on one stream."""
+        streams = (stream, stream_b) if two_streams else (stream,)
+        step = lambda i: ctx.me_estimate_host_batch(descs, B_, "dcds", mv_fs=h_fs_list, sums=h_sums, chunk=chunk,
+                                                    stream=streams[i % len(streams)])
+        for i in range(4):
+            step(i)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        stream_b.wait_event(e0)
+        for i in range(k):
+            step(i)
+        eb = torch.cuda.Event()
+        eb.record(stream_b)
+        stream.wait_event(eb)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / k
+
+    # the host link's own rate: one pinned 100 MB upload, timed alone
+    d_tmp = torch.empty(h_cur.shape, dtype=torch.uint8, device=dev)
+    d_tmp.copy_(h_cur, non_blocking=True)
+    torch.cuda.synchronize()
+    l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0.record(stream)
     for _ in range(3):
-        e2e_step()
+        d_tmp.copy_(h_cur, non_blocking=True)
+    l1.record(stream)
     torch.cuda.synchronize()
-    k2 = max(5, min(50, a.steps // 4))
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(k2):
-        e2e_step()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / k2
-    h2d = 2 * npairs * H_ * W_
+    link_gbs = 3 * h_cur.numel() / (l0.elapsed_time(l1) * 1e-3) / 1e9
+    del d_tmp
+
+    k2 = max(6, min(50, a.steps // 4))
+    chunk_sweep = {str(ch): _e2e_ms(hd, ch, 6) for ch in (npairs, npairs // 2, npairs // 4, npairs // 8)
+                   if ch >= 1}
+    e2e_ms = _e2e_ms(hd, 0, k2)
+    e2e_one_stream_ms = _e2e_ms(hd, 0, k2, two_streams=False)
+    h2d = 2 * npairs * H_ * W_ + npairs * nb * 4
     d2h = npairs * nb * (4 + 4 + 2) + npairs * me.ME_NSUMS * 8
-    assert np.array_equal(h_mv.numpy(), mv.cpu().numpy())
+    assert np.array_equal(h_mv.numpy(), mv.cpu().numpy()), "host-batch field differs from the device call"
+    assert np.array_equal(h_sums.numpy(), sums.cpu().numpy()), "host-batch sums differ from the device call"
+    # the same pairs passed as one sequence: each frame is uploaded once
+    h_seq = torch.from_numpy(np.stack(seq[:npairs + 1])).pin_memory()
+    hs = me.Context.frame_descs((h_seq[i + 1], h_seq[i], R_, h_mv[i], h_sad[i], h_nsp[i]) for i in range(npairs))
+    seq_ms = _e2e_ms(hs, 0, k2)
+    assert np.array_equal(h_mv.numpy(), mv.cpu().numpy()), "sequence host-batch field differs"
+    e2e_seq = {"value": mbs_step * world / (seq_ms * 1e-3), "unit": "macroblocks/s",
+               "h2d_bytes_per_step": (npairs + 1) * H_ * W_ + npairs * nb * 4, "d2h_bytes_per_step": d2h,
+               "ms_per_step": seq_ms,
+               "input": f"the same {npairs} pairs passed as one {npairs + 1}-frame host sequence "
+                        "(ref of pair i+1 = cur of pair i, uploaded once)"}
 
     # ---- roofline of the dominant kernel (DCDS) ----
     peaks = {}
@@ -534,7 +570,12 @@ def main():
         "step_kernels": "dcds_kernel with the Sec. IV sums fused (one launch per step)",
         "search_only_ms": search_only_ms, "unfused_eval_ms": unfused_eval_ms,
         "e2e": {"value": mbs_step * world / (e2e_ms * 1e-3), "unit": "macroblocks/s",
-                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
+                "call": "me_estimate_host_batch (pinned host frames, FS fields and outputs; fused sums; "
+                        "default chunk; steps on two streams in turn)",
+                "one_stream_ms_per_step": e2e_one_stream_ms, "chunk_sweep_ms": chunk_sweep,
+                "host_link_gbs": link_gbs, "host_link_floor_ms": h2d / (link_gbs * 1e9) * 1e3},
+        "e2e_sequence": e2e_seq,
         "gpu_launches": a.steps,
         "clocks": clocks,
     }

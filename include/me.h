@@ -22,8 +22,9 @@
  *     = the number of distinct candidates evaluated ("number of search
  *     points", Sec. III-C and Table IX).
  *   - Every frame and output pointer is DEVICE memory owned by the caller
- *     (e.g. torch tensors).  The library owns only its context: scratch,
- *     descriptor tables, captured graphs and tuning results.
+ *     (e.g. torch tensors), except in me_estimate_host_batch, which takes
+ *     host memory.  The library owns only its context: scratch, descriptor
+ *     tables, captured graphs, tuning results and the host-batch staging.
  *   - Calls are asynchronous on `stream` (a cudaStream_t; NULL = the legacy
  *     default stream).  Outputs are valid once the stream has reached them.
  *   - Errors: every call returns an me_status; the reason is kept in
@@ -192,6 +193,41 @@ int me_estimate_eval_batch(me_ctx* ctx, const me_frame_desc* descs, const int16_
  * allocated while the graph exists. */
 int me_graph_create_eval(me_ctx* ctx, const me_frame_desc* descs, const int16_t* const* mv_fs, int n,
                          int block, int algo, uint64_t* sums, me_graph** out);
+
+/* me_estimate_host_batch: me_estimate_batch or, with `sums`, the fused
+ * search and evaluation of me_estimate_eval_batch, on frames and outputs in
+ * HOST memory.  Not in the paper: the upload of a batch, pipelined.  The
+ * library stages the batch in device memory it owns: a copy stream of its own
+ * uploads the frames of `chunk` pairs at a time, chunk k is searched on
+ * `stream` while chunk k+1 uploads, and a second copy stream brings chunk k's
+ * results back while later chunks upload and search.  A frame that several
+ * descriptors name by the same pointer (a sequence passed as consecutive
+ * pairs: ref of pair i+1 = cur of pair i) is uploaded once.  Copies of
+ * buffers that are adjacent on both sides are merged.
+ *   descs: HOST array; cur, ref, mv, sad and nsp (nullable) point to host
+ *          memory, page-locked (cudaHostAlloc, torch pin_memory) for the
+ *          copies to overlap; pageable memory gives the same results with the
+ *          copies blocking the calling thread.  A frame needs
+ *          (h - 1) * pitch + w readable bytes.  Device pointers also work
+ *          (the copies then stay on the device).
+ *   mv_fs: NULL, or a HOST array of n HOST pointers (entries may be NULL) to
+ *          full-search fields ([nb][2] int16); read only when sums is set.
+ *   sums:  NULL (search only, any algo but the learned one) or HOST uint64
+ *          [n][ME_NSUMS] (DCDS or DCDS^S): the sums me_estimate_eval_batch
+ *          writes.
+ *   chunk: pairs per chunk; 0 picks ceil(n / 4); negative: ME_ERR_ARG.
+ * Outputs are valid once `stream` has passed the call (for example after
+ * cudaStreamSynchronize(stream)); the uploads wait until `stream` reaches the
+ * call.  Two staging sets alternate between calls: a call's uploads also wait
+ * for the result copies of the call before the previous one, so that calls
+ * issued on two streams in turn overlap one call's uploads with the previous
+ * call's last search.  The staging grows to the largest batch seen and lives
+ * until me_free.  Results
+ * are identical to me_estimate_batch / me_estimate_eval_batch on device
+ * copies of the same data.  Argument errors as for those calls; ME_ERR_NOMEM
+ * when the staging cannot be allocated. */
+int me_estimate_host_batch(me_ctx* ctx, const me_frame_desc* descs, const int16_t* const* mv_fs, int n,
+                           int block, int algo, uint64_t* sums, int chunk, void* stream);
 
 /* ---------------------------------------------------------------------- */
 /* Learned start proposal.  Not in the paper: the task adds a small CNN that  */

@@ -14,6 +14,7 @@
 #include <map>
 #include <sstream>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 using me::EvalDev;
@@ -383,6 +384,17 @@ void me_free(me_ctx* c)
     }
     if (c->status) cudaFree(c->status);
     if (c->median_ws) me_proposal_free(c->median_ws);
+    me::HostPipe& P = c->pipe;
+    if (P.in) cudaStreamSynchronize(P.in);
+    if (P.out) cudaStreamSynchronize(P.out);
+    for (cudaEvent_t e : P.ev) cudaEventDestroy(e);
+    if (P.entry) cudaEventDestroy(P.entry);
+    if (P.in) cudaStreamDestroy(P.in);
+    if (P.out) cudaStreamDestroy(P.out);
+    for (me::HostStage& g : P.stage) {
+        if (g.done) cudaEventDestroy(g.done);
+        if (g.dev) cudaFree(g.dev);
+    }
     delete c;
 }
 
@@ -463,6 +475,214 @@ int validate_eval(me_ctx* c, const me_frame_desc* descs, const int16_t* const* m
         if (mv_fs[i] && !aligned(mv_fs[i], 4)) return fail(c, ME_ERR_ARG, "mv_fs entries must be 4-byte aligned");
     (void)descs;
     return ME_OK;
+}
+
+// Copies for one stream, adjacent ones merged when both sides are contiguous.
+struct CopyList {
+    struct Item { char* dst; const char* src; size_t bytes; };
+    std::vector<Item> v;
+    void add(void* dst, const void* src, size_t bytes)
+    {
+        char* d = static_cast<char*>(dst);
+        const char* s = static_cast<const char*>(src);
+        if (!v.empty() && v.back().dst + v.back().bytes == d && v.back().src + v.back().bytes == s)
+            v.back().bytes += bytes;
+        else
+            v.push_back({d, s, bytes});
+    }
+    cudaError_t issue(cudaStream_t st) const
+    {
+        for (const Item& it : v) {
+            cudaError_t e = cudaMemcpyAsync(it.dst, it.src, it.bytes, cudaMemcpyDefault, st);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
+};
+
+int pipe_ready(me_ctx* c, me::HostStage& g, size_t bytes, int nchunks)
+{
+    me::HostPipe& P = c->pipe;
+    cudaError_t e = cudaSuccess;
+    if (!P.in) e = cudaStreamCreateWithFlags(&P.in, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !P.out) e = cudaStreamCreateWithFlags(&P.out, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !P.entry) e = cudaEventCreateWithFlags(&P.entry, cudaEventDisableTiming);
+    if (e == cudaSuccess && !g.done) {
+        e = cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(g.done, P.out);
+    }
+    while (e == cudaSuccess && (int)P.ev.size() < 3 * nchunks) {
+        cudaEvent_t x = nullptr;
+        e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
+        if (e == cudaSuccess) P.ev.push_back(x);
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "host pipeline streams and events");
+    if (g.cap < bytes) {
+        // the last call that used this set has copied its results back (so its searches are done)
+        e = cudaEventSynchronize(g.done);
+        if (e != cudaSuccess) return cuda_fail(c, e, "cudaEventSynchronize");
+        if (g.dev) cudaFree(g.dev);
+        g.dev = nullptr;
+        g.cap = 0;
+        if (cudaMalloc(&g.dev, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, ME_ERR_NOMEM, "cudaMalloc of the host-batch staging failed");
+        }
+        g.cap = bytes;
+    }
+    return ME_OK;
+}
+
+// me_estimate_host_batch: stage the batch in device memory chunk by chunk.
+int host_batch(me_ctx* c, const me_frame_desc* d, const int16_t* const* mv_fs, int n, int block, int algo,
+               uint64_t* sums, int chunk, cudaStream_t st)
+{
+    if (chunk <= 0) chunk = (n + 3) / 4;
+    const int nchunks = (n + chunk - 1) / chunk;
+    auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
+
+    // frames, once per distinct host pointer, in the order of first use
+    struct Fr { const uint8_t* h; size_t bytes, span, off; };
+    std::vector<Fr> fr;
+    std::unordered_map<const uint8_t*, int> index;
+    std::vector<int> fc(n), frf(n);
+    auto frame = [&](const uint8_t* p, const me_frame_desc& f) {
+        const size_t bytes = (size_t)(f.h - 1) * f.pitch + f.w, span = (size_t)f.h * f.pitch;
+        auto it = index.find(p);
+        if (it != index.end()) {
+            Fr& x = fr[it->second];
+            x.bytes = std::max(x.bytes, bytes);
+            x.span = std::max(x.span, span);
+            return it->second;
+        }
+        index.emplace(p, (int)fr.size());
+        fr.push_back({p, bytes, span, 0});
+        return (int)fr.size() - 1;
+    };
+    for (int i = 0; i < n; ++i) { fc[i] = frame(d[i].cur, d[i]); frf[i] = frame(d[i].ref, d[i]); }
+    // Device layout: frames (16-byte multiples), then mv, sad, nsp, FS fields
+    // and sums.  The frames a chunk uploads first, and its FS fields, are
+    // placed in host-address order, so that buffers adjacent on the host are
+    // adjacent on the device and their copies merge into one.
+    std::vector<std::vector<int>> up_frames(nchunks), up_fs(nchunks);
+    std::vector<size_t> nb(n), o_mv(n), o_sad(n), o_nsp(n), o_fs(n, 0);
+    size_t off = 0;
+    {
+        std::vector<char> seen(fr.size(), 0);
+        for (int k = 0; k < nchunks; ++k) {
+            std::vector<int>& L = up_frames[k];
+            for (int i = k * chunk; i < std::min(n, (k + 1) * chunk); ++i)
+                for (int f : {fc[i], frf[i]})
+                    if (!seen[f]) { seen[f] = 1; L.push_back(f); }
+            std::sort(L.begin(), L.end(), [&](int a, int b) { return (uintptr_t)fr[a].h < (uintptr_t)fr[b].h; });
+            for (int f : L) { fr[f].off = off; off += fr[f].span; }
+        }
+    }
+    off = up(off);
+    for (int i = 0; i < n; ++i) { nb[i] = (size_t)(d[i].w / block) * (d[i].h / block); o_mv[i] = off; off += 4 * nb[i]; }
+    off = up(off);
+    for (int i = 0; i < n; ++i) { o_sad[i] = off; off += 4 * nb[i]; }
+    off = up(off);
+    for (int i = 0; i < n; ++i) { o_nsp[i] = off; off += 2 * nb[i]; }
+    off = up(off);
+    for (int k = 0; sums && mv_fs && k < nchunks; ++k) {
+        std::vector<int>& L = up_fs[k];
+        for (int i = k * chunk; i < std::min(n, (k + 1) * chunk); ++i)
+            if (mv_fs[i]) L.push_back(i);
+        std::sort(L.begin(), L.end(), [&](int a, int b) { return (uintptr_t)mv_fs[a] < (uintptr_t)mv_fs[b]; });
+        for (int i : L) { o_fs[i] = off; off += 4 * nb[i]; }
+    }
+    off = up(off);
+    const size_t o_sums = off;
+    off += sums ? sizeof(uint64_t) * ME_NSUMS * (size_t)n : 0;
+    me::HostPipe& P = c->pipe;
+    me::HostStage& G = P.stage[P.next];
+    int rc = pipe_ready(c, G, std::max<size_t>(off, 256), nchunks);
+    if (rc != ME_OK) return rc;
+    P.next ^= 1;
+    char* base = static_cast<char*>(G.dev);
+
+    int mr = 1, mw = 0, mh = 0;
+    for (int i = 0; i < n; ++i) { mr = std::max(mr, d[i].range); mw = std::max(mw, d[i].w); mh = std::max(mh, d[i].h); }
+    const Shape s = pick_shape(c, algo, block, mr, mw, mh);
+
+    // Every chunk's [queue head | descriptor table] goes up in one copy ahead
+    // of the frames: a small copy on the searching stream would queue behind
+    // the next chunk's frames on the copy engine and hold its search back.
+    const size_t per = kHeadBytes + sizeof(FrameDev) * (size_t)chunk;
+    Slot* slot = nullptr;
+    rc = take_slot(c, per * nchunks, &slot);
+    if (rc != ME_OK) return rc;
+    std::vector<me_frame_desc> dd(n);
+    std::vector<const int16_t*> fsd(n);
+    std::vector<int> ntiles(nchunks), mrange(nchunks);
+    for (int i = 0; i < n; ++i) {
+        me_frame_desc& x = dd[i];
+        x = d[i];
+        x.cur = reinterpret_cast<const uint8_t*>(base + fr[fc[i]].off);
+        x.ref = reinterpret_cast<const uint8_t*>(base + fr[frf[i]].off);
+        x.mv = reinterpret_cast<int16_t*>(base + o_mv[i]);
+        x.sad = reinterpret_cast<uint32_t*>(base + o_sad[i]);
+        x.nsp = d[i].nsp ? reinterpret_cast<uint16_t*>(base + o_nsp[i]) : nullptr;
+        fsd[i] = (sums && mv_fs && mv_fs[i]) ? reinterpret_cast<const int16_t*>(base + o_fs[i]) : nullptr;
+    }
+    std::vector<EvalArgs> eas(nchunks);
+    size_t max_chunk_blocks = 0;
+    for (int k = 0; k < nchunks; ++k) {
+        const int c0 = k * chunk, m = std::min(n, c0 + chunk) - c0;
+        eas[k].mv_fs = fsd.data() + c0;
+        eas[k].sums = sums ? reinterpret_cast<uint64_t*>(base + o_sums) + (size_t)ME_NSUMS * c0 : nullptr;
+        FrameDev* table = reinterpret_cast<FrameDev*>(static_cast<char*>(slot->host) + per * k + kHeadBytes);
+        ntiles[k] = build_table(dd.data() + c0, m, block, s, algo == ME_ALGO_FS, table, &mrange[k],
+                                sums ? &eas[k] : nullptr);
+        if (ntiles[k] < 0) return fail(c, ME_ERR_CUDA, "cuTensorMapEncodeTiled rejected a frame description");
+        max_chunk_blocks = std::max(max_chunk_blocks, total_blocks(dd.data() + c0, m, block));
+    }
+    if (algo != ME_ALGO_FS && s.kernel == 1 && !sums) {
+        rc = ensure_queue(c, &slot->queue, &slot->qcap, max_chunk_blocks);
+        if (rc != ME_OK) return rc;
+    }
+
+    // uploads start once the caller's stream reaches the call and the last
+    // call that used this staging set has its results back
+    cudaError_t e = cudaEventRecord(P.entry, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(P.in, P.entry, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(P.in, G.done, 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(slot->dev, slot->host, per * nchunks, cudaMemcpyHostToDevice, P.in);
+    if (e != cudaSuccess) return cuda_fail(c, e, "host pipeline ordering");
+    for (int k = 0; k < nchunks; ++k) {
+        const int c0 = k * chunk, c1 = std::min(n, c0 + chunk), m = c1 - c0;
+        cudaEvent_t ev_in = P.ev[3 * k], ev_run = P.ev[3 * k + 1], ev_out = P.ev[3 * k + 2];
+        CopyList in, out;
+        for (int f : up_frames[k]) in.add(base + fr[f].off, fr[f].h, fr[f].bytes);
+        for (int i : up_fs[k]) in.add(base + o_fs[i], mv_fs[i], 4 * nb[i]);
+        e = in.issue(P.in);
+        if (e == cudaSuccess) e = cudaEventRecord(ev_in, P.in);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev_in, 0);
+        if (e != cudaSuccess) return cuda_fail(c, e, "host-batch upload");
+        e = launch_search(c, static_cast<char*>(slot->dev) + per * k, slot->queue, slot->qcap, m, ntiles[k], block,
+                          algo, mrange[k], s, st, sums ? &eas[k] : nullptr);
+        if (e != cudaSuccess) return cuda_fail(c, e, "search launch");
+        e = cudaEventRecord(ev_run, st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(P.out, ev_run, 0);
+        if (e != cudaSuccess) return cuda_fail(c, e, "host pipeline ordering");
+        for (int i = c0; i < c1; ++i) out.add(d[i].mv, base + o_mv[i], 4 * nb[i]);
+        for (int i = c0; i < c1; ++i) out.add(d[i].sad, base + o_sad[i], 4 * nb[i]);
+        for (int i = c0; i < c1; ++i)
+            if (d[i].nsp) out.add(d[i].nsp, base + o_nsp[i], 2 * nb[i]);
+        if (sums)
+            out.add(sums + (size_t)ME_NSUMS * c0, base + o_sums + sizeof(uint64_t) * ME_NSUMS * c0,
+                    sizeof(uint64_t) * ME_NSUMS * m);
+        e = out.issue(P.out);
+        if (e == cudaSuccess) e = cudaEventRecord(ev_out, P.out);
+        if (e != cudaSuccess) return cuda_fail(c, e, "host-batch result copy");
+    }
+    e = cudaEventRecord(slot->done, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaEventRecord");
+    slot->used = true;
+    e = cudaEventRecord(G.done, P.out);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, G.done, 0);
+    return e == cudaSuccess ? ME_OK : cuda_fail(c, e, "host pipeline ordering");
 }
 
 }  // namespace
@@ -791,6 +1011,17 @@ int me_check_status(me_ctx* c, void* stream)
         return fail(c, ME_ERR_ARG, "a kernel rejected its input");
     }
     return ME_OK;
+}
+
+int me_estimate_host_batch(me_ctx* c, const me_frame_desc* descs, const int16_t* const* mv_fs, int n, int block,
+                           int algo, uint64_t* sums, int chunk, void* stream)
+{
+    if (!c) return ME_ERR_ARG;
+    int rc = validate_batch(c, descs, n, block, algo);
+    if (rc == ME_OK && sums) rc = validate_eval(c, descs, mv_fs, n, algo, sums);
+    if (rc != ME_OK) return rc;
+    if (chunk < 0) return fail(c, ME_ERR_ARG, "chunk must not be negative");
+    return host_batch(c, descs, sums ? mv_fs : nullptr, n, block, algo, sums, chunk, (cudaStream_t)stream);
 }
 
 }  // extern "C"

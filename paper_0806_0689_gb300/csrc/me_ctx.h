@@ -7,6 +7,7 @@
 
 #include <map>
 #include <string>
+#include <vector>
 
 namespace me {
 
@@ -24,6 +25,24 @@ struct Slot {
 
 constexpr size_t kHeadBytes = 256;  // queue head (int) and padding before the table
 
+// Staging of me_estimate_host_batch: two sets of device buffers for a
+// call's frames, FS fields and outputs (consecutive calls alternate, so one
+// call's uploads can run while the previous call still searches), the two
+// copy streams and the events that order them.
+struct HostStage {
+    void* dev = nullptr;
+    size_t cap = 0;
+    cudaEvent_t done = nullptr;   // the last result copy of the call that used this set
+};
+struct HostPipe {
+    HostStage stage[2];
+    int next = 0;
+    cudaStream_t in = nullptr;    // host-to-device copies
+    cudaStream_t out = nullptr;   // device-to-host copies
+    cudaEvent_t entry = nullptr;  // the caller's stream reached the call
+    std::vector<cudaEvent_t> ev;  // per chunk: inputs uploaded, search done, results copied
+};
+
 }  // namespace me
 
 struct me_ctx {
@@ -37,6 +56,7 @@ struct me_ctx {
     unsigned* status = nullptr;  // device word written by kernels
     unsigned* sink = nullptr;    // microbenchmark sink
     struct me_proposal* median_ws = nullptr;  // wavefront buffers of the neighbour-median start (lazy)
+    me::HostPipe pipe;                        // me_estimate_host_batch staging (lazy)
 };
 
 struct me_graph {

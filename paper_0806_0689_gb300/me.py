@@ -28,7 +28,7 @@ EXPORTS = ["me_init", "me_free", "me_last_error", "me_estimate", "me_estimate_ba
            "me_proposal_create", "me_proposal_free", "me_proposal_set_params", "me_proposal_get_params",
            "me_proposal_train_step", "me_proposal_logits", "me_estimate_learned_batch",
            "me_estimate_eval_batch", "me_graph_create_eval", "me_estimate_median_batch", "me_mvp_stats",
-           "me_fs_dual_batch"]
+           "me_fs_dual_batch", "me_estimate_host_batch"]
 ME_PROPOSAL_NPARAMS = 37532
 ME_PROPOSAL_NLOGITS = 68
 
@@ -101,6 +101,7 @@ def load(build_if_missing: bool = True):
                                                  ctypes.POINTER(ctypes.c_float), P, P]
             L.me_proposal_logits.argtypes = [P, P, ctypes.POINTER(FrameDesc), P, P]
             L.me_estimate_learned_batch.argtypes = [P, P, ctypes.POINTER(FrameDesc), I, P, P]
+            L.me_estimate_host_batch.argtypes = [P, ctypes.POINTER(FrameDesc), P, I, I, I, P, I, P]
             for n in EXPORTS:
                 if n not in ("me_free", "me_last_error", "me_graph_free", "me_proposal_free"):
                     getattr(L, n).restype = I
@@ -185,6 +186,17 @@ class Context:
         arr = self._fs_ptrs(mv_fs, len(descs))
         self._check(self.L.me_estimate_eval_batch(self.h, descs, arr, len(descs), block, ALGOS.get(algo, algo),
                                                   _ptr(sums), _stream(stream)))
+
+    def me_estimate_host_batch(self, descs, block, algo, mv_fs=None, sums=None, chunk=0, stream=None):
+        """The search (with sums: search and evaluation) on HOST tensors,
+        pinned for the copies to overlap; descs built by frame_descs from
+        host tensors; mv_fs: list of host tensors (or None entries) or None;
+        sums: host int64 [n][ME_NSUMS] or None; chunk: pairs per chunk (0:
+        the library's choice)."""
+        arr = self._fs_ptrs(mv_fs, len(descs))
+        self._check(self.L.me_estimate_host_batch(self.h, descs, ctypes.cast(arr, ctypes.c_void_p) if arr else None,
+                                                  len(descs), block, ALGOS.get(algo, algo), _ptr(sums), chunk,
+                                                  _stream(stream)))
 
     def me_graph_create_eval(self, descs, mv_fs, block, algo, sums):
         g = ctypes.c_void_p()
