@@ -43,6 +43,7 @@ def _args():
     p.add_argument("--pairs", type=int, default=NPAIRS)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-learned", action="store_true")
+    p.add_argument("--no-workloads", action="store_true", help="skip the mixed-stream and stress context lines")
     p.add_argument("--no-tune", action="store_true", help="use the library's default launch shapes")
     return p.parse_args()
 
@@ -109,6 +110,7 @@ def cpu_baseline(seconds_hint=20.0):
     mbs = sum(r[0] for r in res)
     busy = max(r[1] for r in res)
     return {"value": mbs / busy, "unit": "macroblocks/s", "cores": cores, "kind": "oracle",
+            "one_core_value": n / dt,
             "sample": f"{cores} processes x {reps} whole 1080p pairs each (DCDS + evaluation), "
                       f"{mbs} macroblocks in {busy:.1f} s (wall {wall:.1f} s)"}
 
@@ -180,6 +182,66 @@ class Clocks:
 
 
 # ---------------------------------------------------------------- learned proposal
+
+def other_workloads(ctx, me, torch, dev, hbm_peak, sad_peak):
+    """Context beside the headline: plain DCDS and FS on the mixed-stream
+    batch (8 streams: 2 QCIF, 2 CIF, 2 1280x720, 2 1920x1088, 30 pairs each,
+    16x16, +-16; one launch each) and on a 12-pair sample of the stress
+    workload (3840x2160, 8x8, +-32, motion scales 6/3), each with the
+    library's tuner run first, as a caller would."""
+    from paper_0806_0689_gb300 import synth
+    out = {}
+    cases = {
+        "mixed_streams_8x30_pairs_16x16_r16": (16, 16, [
+            (name, 2000 + k, 30, (2.0, 1.0)) for k, name in
+            enumerate(("qcif", "qcif", "cif", "cif", "720p", "720p", "1080p", "1080p"))]),
+        "stress_2160p_8x8_r32_12_pairs": (8, 32, [("2160p", 4000, 12, (6.0, 3.0))]),
+    }
+    for key, (B, R, streams) in cases.items():
+        seqs = [synth.workload_sequence(n, np_ + 1, seed=sd, max_motion=min(R, 16) if B == 16 else R, scale=sc)
+                for n, sd, np_, sc in streams]
+        frames = [(sq[t + 1], sq[t]) for t in range(max(x[2] for x in streams)) for sq in seqs if t + 1 < len(sq)]
+        items, keep = [], []
+        nblocks, fbytes, absdiff_fs = 0, 0, 0.0
+        for cur, ref in frames:
+            h, w = cur.shape
+            nb = (w // B) * (h // B)
+            c, r = torch.from_numpy(cur).to(dev), torch.from_numpy(ref).to(dev)
+            mv = torch.empty((nb, 2), dtype=torch.int16, device=dev)
+            sad = torch.empty((nb,), dtype=torch.int32, device=dev)
+            nsp = torch.empty((nb,), dtype=torch.int16, device=dev)
+            keep.append((c, r, mv, sad, nsp))
+            items.append((c, r, R, mv, sad, nsp))
+            nblocks += nb
+            fbytes += 2 * w * h
+        d = me.Context.frame_descs(items)
+        res = {"pairs": len(frames), "blocks_per_launch": nblocks, "input_bytes": fbytes}
+        for algo in ("dcds", "fs"):
+            ctx.me_tune_batch(d, B, algo)
+            g = ctx.me_graph_create(d, B, algo)
+            for _ in range(3):
+                ctx.me_graph_launch(g)
+            torch.cuda.synchronize()
+            reps = 20 if algo == "dcds" else 3
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                ctx.me_graph_launch(g)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            ctx.me_graph_free(g)
+            nsp_sum = float(sum(int(x[4].cpu().numpy().view(np.uint16).astype(np.int64).sum()) for x in keep))
+            r_ = {"launch_ms": ms, "blocks_per_s": nblocks / (ms * 1e-3), "nsp_per_block": nsp_sum / nblocks,
+                  "absdiff_frac_of_sad_rate": nsp_sum * B * B / (ms * 1e-3) / sad_peak}
+            if algo == "dcds":
+                alg = fbytes + nblocks * 10
+                r_["hbm_frac"] = alg / (ms * 1e-3) / 1e9 / hbm_peak
+            res[algo] = r_
+        out[key] = res
+        del items, keep
+    return out
+
 
 def learned_leg(ctx, me, torch, dev, curs, refs, mv_plain, mv_fs, st_plain, nb, npairs,
                 train_seqs=60, steps=3000):
@@ -383,6 +445,26 @@ def main():
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / reps
     search_only_ms = _time(lambda: ctx.me_graph_launch(g_dcds))
+    # L2 check: the same step over three copies of the inputs in turn (three
+    # times the bytes between reuses of any address), against one set
+    rot_sets, rot_graphs = [], [g_step]
+    for _ in range(2):
+        c2, r2 = [x.clone() for x in curs], [x.clone() for x in refs]
+        d2 = me.Context.frame_descs((c2[i], r2[i], R_, mv[i], sad[i], nsp[i]) for i in range(npairs))
+        rot_sets.append((c2, r2))
+        rot_graphs.append(ctx.me_graph_create_eval(d2, fs_list, B_, "dcds", sums))
+    rot_i = [0]
+
+    def _rot():
+        ctx.me_graph_launch(rot_graphs[rot_i[0] % 3])
+        rot_i[0] += 1
+    rot_ms = _time(_rot, reps=60)
+    single_ms = _time(lambda: ctx.me_graph_launch(g_step), reps=60)
+    for g in rot_graphs[1:]:
+        ctx.me_graph_free(g)
+    del rot_sets
+    l2_check = {"sets": 3, "bytes_between_reuses": 3 * 2 * npairs * W_ * H_, "ms_per_step": rot_ms,
+                "one_set_ms_per_step": single_ms}
     sums_sep = torch.zeros_like(sums)
     unfused_eval_ms = _time(lambda: ctx.me_eval_batch(e_dcds, B_, sums_sep))
     ctx.me_graph_launch(g_step)
@@ -569,6 +651,7 @@ def main():
         "tuned_shape_index": tuned,
         "step_kernels": "dcds_kernel with the Sec. IV sums fused (one launch per step)",
         "search_only_ms": search_only_ms, "unfused_eval_ms": unfused_eval_ms,
+        "l2_rotation_check": l2_check,
         "e2e": {"value": mbs_step * world / (e2e_ms * 1e-3), "unit": "macroblocks/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
                 "call": "me_estimate_host_batch (pinned host frames, FS fields and outputs; fused sums; "
@@ -583,6 +666,8 @@ def main():
         line["cpu_baseline"] = cb
     if not a.no_learned:
         line["learned"] = learned_leg(ctx, me, torch, dev, curs, refs, mv, mv_fs, st_d, nb, npairs)
+    if not a.no_workloads:
+        line["other_workloads"] = other_workloads(ctx, me, torch, dev, hbm_peak, sad_peak)
     ctx.me_graph_free(g_step)
     ctx.me_graph_free(g_dcds)
     ctx.me_graph_free(g_fs)
