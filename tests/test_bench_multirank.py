@@ -60,3 +60,22 @@ def test_two_rank_timing_and_sharding():
     assert st0 == 3.0
     assert seed0 != seed1  # disjoint shards
     assert ref1 is None and printed1 == ""
+
+
+def test_reference_arm_line():
+    """--impl reference times the oracle in bounded steps and prints the
+    contract's line with our arm's metric, unit and direction."""
+    import json
+    import subprocess
+    sys.path.insert(0, ROOT)
+    import bench
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "2",
+                        "--warmup", "1"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC
+    assert line["unit"] == "macroblocks/s" and line["higher_is_better"] is True
+    assert line["steps"] == 2 and line["warmup"] == 1 and line["value"] > 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"] == {"value": line["value"], "unit": "macroblocks/s", "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
