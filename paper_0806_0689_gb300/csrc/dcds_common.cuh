@@ -99,6 +99,8 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
 
 __device__ __forceinline__ int find_frame(const FrameDev* frames, int nframes, int t)
 {
+    const int u = frames[0].uniform_tiles;
+    if (u > 0) return min(t / u, nframes - 1);
     int lo = 0, hi = nframes - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;

@@ -239,6 +239,7 @@ int build_table(const me_frame_desc* d, int n, int block, const Shape& s, bool f
         tiles += f.tiles_x * f.tiles_y;
         table[i] = f;
     }
+    me::set_uniform_tiles(table, n);
     *max_range = mr;
     return tiles;
 }

@@ -27,7 +27,7 @@ struct __align__(128) FrameDev {
     int32_t nbx, nby;          // blocks per row / column
     int32_t tiles_x, tiles_y;  // tiles of this frame
     int32_t tile_base;         // first global tile index of this frame
-    int32_t pad_[1];
+    int32_t uniform_tiles;     // > 0: every frame of the table has this many tiles (tile t is in frame t / it)
     const int16_t* mv_fs;      // fused evaluation: the full-search field (may be null)
     unsigned long long* sums;  // fused evaluation: the frame's eight sums (null: no evaluation)
     int16_t* mv8;              // two-size full search: the 8x8 field (null: not requested)
@@ -38,6 +38,17 @@ struct __align__(128) FrameDev {
 // Encode the two tensor maps of `f` (its pointers, sizes and range must be
 // set).  Host code; returns false if the driver rejects the description.
 bool encode_frame_maps(FrameDev& f);
+
+// Host code, after a table's tile counts and bases are set: mark the table
+// uniform when every frame has the same number of tiles, so that the kernels
+// find a tile's frame with one division instead of a binary search.
+inline void set_uniform_tiles(FrameDev* table, int n)
+{
+    const int t0 = n > 0 ? table[0].tiles_x * table[0].tiles_y : 0;
+    bool same = t0 > 0;
+    for (int i = 1; i < n && same; ++i) same = table[i].tiles_x * table[i].tiles_y == t0;
+    for (int i = 0; i < n; ++i) table[i].uniform_tiles = same ? t0 : 0;
+}
 
 // Device-side view of one frame of an evaluation batch.
 struct __align__(64) EvalDev {

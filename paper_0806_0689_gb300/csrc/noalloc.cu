@@ -120,6 +120,7 @@ extern "C" int me_estimate_batch_noalloc(const me_frame_desc* d, int n, int bloc
         max_range = std::max(max_range, x.range);
         table[i] = f;
     }
+    me::set_uniform_tiles(table, n);
 
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
