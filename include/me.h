@@ -391,6 +391,18 @@ int me_absdiff_peak(me_ctx* ctx, int iters, double* out, int n_variants, int* us
  * recorded flag is cleared. */
 int me_check_status(me_ctx* ctx, void* stream);
 
+/* me_inject_wait_timeout: failure-detection test hook (not in the paper).
+ * While `on` is non-zero, every DCDS / DCDS^S launch of this context that
+ * runs the tile kernel (me_estimate, me_estimate_batch, the fused and host
+ * batches, graphs captured meanwhile) arms each CTA's first tile-copy barrier
+ * for 16 bytes more than the copy delivers.  The copies land, the barrier
+ * never completes, and each CTA's bounded wait (shortened to a few thousand
+ * polls) gives up, records the time-out and exits: the launch writes no
+ * output and the next me_check_status returns ME_ERR_TIMEOUT.  Nothing faults,
+ * traps or hangs, and the context stays usable: with `on` = 0 the next launch
+ * is a normal one.  Returns ME_ERR_ARG for a NULL context. */
+int me_inject_wait_timeout(me_ctx* ctx, int on);
+
 #ifdef __cplusplus
 }
 #endif

@@ -27,6 +27,7 @@ constexpr uint64_t kMidV = enc(0, -1, 0) | enc(0, 1, 1);
 constexpr uint32_t kUnknown = 0xfffffffeu;  // distant-point SAD not produced this round
 constexpr uint32_t kInvalid = 0xffffffffu;  // distant point outside window/frame
 constexpr uint32_t kWaitLimit = 1u << 20;   // bounded mbarrier waits (each try_wait call suspends briefly)
+constexpr uint32_t kShortWait = 1u << 12;   // the limit under the failure-detection test hook
 
 __device__ __forceinline__ void decode(uint64_t code, int k, int& ox, int& oy)
 {
@@ -70,9 +71,9 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity)
 // Wait for the phase with the given parity.  try_wait suspends the thread in
 // hardware for a bounded time per call; after kWaitLimit calls the wait gives
 // up and the caller reports a timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t limit = kWaitLimit)
 {
-    for (uint32_t i = 0; i < kWaitLimit; ++i)
+    for (uint32_t i = 0; i < limit; ++i)
         if (mbar_try(bar, parity)) return true;
     return false;
 }
@@ -120,8 +121,10 @@ __host__ __device__ inline int win_bytes_max(int max_range)
 // Thread 0: take tile t into stage `st`: publish its index and frame, then arm
 // the stage's mbarrier with the byte count and start the two TMA copies.  A
 // tile index past the end completes the phase with no data.
+// extra_tx > 0 arms the barrier for more bytes than the copies deliver (the
+// failure-detection test hook: the wait on this stage then runs out).
 __device__ inline void issue_tile(int t, const FrameDev* frames, int nframes, int ntiles, uint8_t* stage,
-                           int cur_off, uint64_t* bar, int* s_tile, int* s_frame)
+                           int cur_off, uint64_t* bar, int* s_tile, int* s_frame, uint32_t extra_tx = 0)
 {
     *s_tile = t;
     if (t >= ntiles) {
@@ -134,7 +137,7 @@ __device__ inline void issue_tile(int t, const FrameDev* frames, int nframes, in
     const int lt = t - F.tile_base;
     const int ty = lt / F.tiles_x, tx = lt - ty * F.tiles_x;
     const int rx = (F.range + 15) & ~15;
-    const uint32_t bytes = (uint32_t)((kTile + 2 * rx) * (kTile + 2 * F.range) + kTile * kTile);
+    const uint32_t bytes = (uint32_t)((kTile + 2 * rx) * (kTile + 2 * F.range) + kTile * kTile) + extra_tx;
     mbar_arrive_expect_tx(bar, bytes);
     tma_load_2d(stage, &F.tm_ref, tx * kTile - rx, ty * kTile - F.range, bar);
     tma_load_2d(stage + cur_off, &F.tm_cur, tx * kTile, ty * kTile, bar);

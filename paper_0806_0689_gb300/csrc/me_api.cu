@@ -269,6 +269,13 @@ cudaError_t launch_search(me_ctx* c, void* dev, void* queue, size_t qcap, int n,
     const FrameDev* table = reinterpret_cast<const FrameDev*>(reinterpret_cast<char*>(dev) + kHeadBytes);
     cudaError_t e = cudaMemsetAsync(head, 0, me::kCounterInts * sizeof(int), st);
     if (e != cudaSuccess) return e;
+    // failure-detection test hook: a non-zero last counter word makes the DCDS
+    // tile kernel arm its first copies for bytes that never arrive
+    const bool tile_kernel = algo != ME_ALGO_FS && (s.kernel == 0 || (ev && ev->sums));
+    if (c->inject_wait_timeout && tile_kernel) {
+        e = cudaMemsetAsync(head + me::kCounterInts - 1, 1, sizeof(int), st);
+        if (e != cudaSuccess) return e;
+    }
     if (ev && ev->sums) {
         // the fused evaluation runs in the tile-phase kernel; its sums accumulate from zero
         e = cudaMemsetAsync(ev->sums, 0, sizeof(uint64_t) * ME_NSUMS * (size_t)n, st);
@@ -995,6 +1002,13 @@ int me_absdiff_peak(me_ctx* c, int iters, double* out, int n_variants, int* used
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (used) *used = me::kSadVariant;
+    return ME_OK;
+}
+
+int me_inject_wait_timeout(me_ctx* c, int on)
+{
+    if (!c) return ME_ERR_ARG;
+    c->inject_wait_timeout = on ? 1 : 0;
     return ME_OK;
 }
 

@@ -57,6 +57,7 @@ struct me_ctx {
     unsigned* sink = nullptr;    // microbenchmark sink
     struct me_proposal* median_ws = nullptr;  // wavefront buffers of the neighbour-median start (lazy)
     me::HostPipe pipe;                        // me_estimate_host_batch staging (lazy)
+    int inject_wait_timeout = 0;              // failure-detection test hook (me_inject_wait_timeout)
 };
 
 struct me_graph {

@@ -41,7 +41,8 @@ struct Chunk {
 __global__ void static_setup_kernel(Chunk c, int first, int count, unsigned char* scratch)
 {
     me::FrameDev* table = reinterpret_cast<me::FrameDev*>(scratch + kHeadBytes);
-    if (first == 0 && threadIdx.x == 0) *reinterpret_cast<int*>(scratch) = 0;  // queue head starts at zero
+    // the queue head starts at zero, and so do the kernel's other counter words
+    if (first == 0 && threadIdx.x < me::kCounterInts) reinterpret_cast<int*>(scratch)[threadIdx.x] = 0;
     for (int i = threadIdx.x; i < count; i += blockDim.x) table[first + i] = c.f[i];
 }
 

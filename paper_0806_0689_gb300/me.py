@@ -28,7 +28,7 @@ EXPORTS = ["me_init", "me_free", "me_last_error", "me_estimate", "me_estimate_ba
            "me_proposal_create", "me_proposal_free", "me_proposal_set_params", "me_proposal_get_params",
            "me_proposal_train_step", "me_proposal_logits", "me_estimate_learned_batch",
            "me_estimate_eval_batch", "me_graph_create_eval", "me_estimate_median_batch", "me_mvp_stats",
-           "me_fs_dual_batch", "me_estimate_host_batch"]
+           "me_fs_dual_batch", "me_estimate_host_batch", "me_inject_wait_timeout"]
 ME_PROPOSAL_NPARAMS = 37532
 ME_PROPOSAL_NLOGITS = 68
 
@@ -304,6 +304,11 @@ class Context:
 
     def me_check_status(self, stream=None):
         self._check(self.L.me_check_status(self.h, _stream(stream)))
+
+    def me_inject_wait_timeout(self, on):
+        """Failure-detection test hook: while on, DCDS tile-kernel launches
+        give up their first copy's (bounded) wait and report ME_ERR_TIMEOUT."""
+        self._check(self.L.me_inject_wait_timeout(self.h, int(bool(on))))
 
 
 def proposal_init_params(seed=0):
