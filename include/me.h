@@ -256,6 +256,20 @@ void me_proposal_free(me_proposal* p);
  * parameters resets the optimiser state.  Both synchronise the device. */
 int me_proposal_set_params(me_ctx* ctx, me_proposal* p, const float* params);
 int me_proposal_get_params(me_ctx* ctx, me_proposal* p, float* params);
+/* Checkpoint and resume of training (not in the paper).  me_proposal_save
+ * synchronises the device and writes the parameters, both Adam moment vectors
+ * and the Adam step count to `path`: a 32-byte header (magic "MEPROP\0\1",
+ * version 1, ME_PROPOSAL_NPARAMS, ME_PROPOSAL_NLOGITS, step, CRC-32 of the
+ * payload, a reserved word; little-endian) followed by three float32 arrays of
+ * ME_PROPOSAL_NPARAMS values in parameter order.  It writes `path`.tmp and
+ * renames it over `path`, so a crash never leaves a half-written checkpoint.
+ * me_proposal_load restores all of it (training then continues exactly where
+ * the saved one stopped, up to the run-to-run rounding of the training
+ * kernels' atomics); a file of the wrong size, magic, version or shape, or
+ * whose CRC does not match, is rejected with ME_ERR_ARG and leaves `p`
+ * unchanged. */
+int me_proposal_save(me_ctx* ctx, me_proposal* p, const char* path);
+int me_proposal_load(me_ctx* ctx, me_proposal* p, const char* path);
 /* One training step over every 16x16 block of the n pairs: descs[i].mv (a
  * DEVICE motion field, e.g. the full-search field) gives the labels (dx, dy
  * clamped to +-16; H when |dx| >= |dy|) and the neighbour scalars.  The loss

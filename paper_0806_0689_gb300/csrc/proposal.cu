@@ -28,7 +28,9 @@
 
 #include <algorithm>
 #include <climits>
+#include <cstdio>
 #include <cstring>
+#include <string>
 #include <vector>
 
 using namespace me::cnn;
@@ -630,6 +632,97 @@ int me_proposal_set_params(me_ctx* c, me_proposal* P, const float* host)
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     P->step = 0;
     return e == cudaSuccess ? ME_OK : cuda_fail(c, e, "me_proposal_set_params");
+}
+
+}  // extern "C"
+
+namespace {
+
+// CRC-32 (the reflected polynomial 0xEDB88320 of IEEE 802.3 / zlib), bitwise.
+uint32_t crc32_update(uint32_t crc, const uint8_t* p, size_t n)
+{
+    crc = ~crc;
+    for (size_t i = 0; i < n; ++i) {
+        crc ^= p[i];
+        for (int k = 0; k < 8; ++k) crc = (crc >> 1) ^ (0xEDB88320u & (0u - (crc & 1u)));
+    }
+    return ~crc;
+}
+
+// Checkpoint layout: a 32-byte header, then the parameters and the two Adam
+// moment vectors (float32, parameter order, NPARAMS each).
+struct CkptHeader {
+    char magic[8];       // "MEPROP\0\1"
+    uint32_t version;    // 1
+    uint32_t nparams;    // ME_PROPOSAL_NPARAMS
+    uint32_t nlogits;    // ME_PROPOSAL_NLOGITS
+    int32_t step;        // Adam steps taken
+    uint32_t crc;        // CRC-32 of the payload
+    uint32_t reserved;
+};
+static_assert(sizeof(CkptHeader) == 32, "checkpoint header layout");
+const char kMagic[8] = {'M', 'E', 'P', 'R', 'O', 'P', 0, 1};
+
+}  // namespace
+
+extern "C" {
+
+int me_proposal_save(me_ctx* c, me_proposal* P, const char* path)
+{
+    if (!c || !P || !path) return ME_ERR_ARG;
+    std::vector<float> buf(3 * (size_t)NPARAMS);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(buf.data(), P->p, sizeof(float) * NPARAMS, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(buf.data() + NPARAMS, P->m, sizeof(float) * NPARAMS, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(buf.data() + 2 * NPARAMS, P->v, sizeof(float) * NPARAMS, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "me_proposal_save");
+    CkptHeader h{};
+    std::memcpy(h.magic, kMagic, 8);
+    h.version = 1;
+    h.nparams = NPARAMS;
+    h.nlogits = NLOGIT;
+    h.step = P->step;
+    h.crc = crc32_update(0u, reinterpret_cast<const uint8_t*>(buf.data()), sizeof(float) * buf.size());
+    // write a temporary file, then rename it over the target: a crash leaves the old checkpoint whole
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE* f = std::fopen(tmp.c_str(), "wb");
+    if (!f) return fail(c, ME_ERR_ARG, "cannot open " + tmp + " for writing");
+    bool ok = std::fwrite(&h, sizeof(h), 1, f) == 1 &&
+              std::fwrite(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+    ok = (std::fclose(f) == 0) && ok;
+    if (!ok || std::rename(tmp.c_str(), path) != 0) {
+        std::remove(tmp.c_str());
+        return fail(c, ME_ERR_ARG, std::string("cannot write the checkpoint ") + path);
+    }
+    return ME_OK;
+}
+
+int me_proposal_load(me_ctx* c, me_proposal* P, const char* path)
+{
+    if (!c || !P || !path) return ME_ERR_ARG;
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return fail(c, ME_ERR_ARG, std::string("cannot open ") + path);
+    CkptHeader h{};
+    std::vector<float> buf(3 * (size_t)NPARAMS);
+    const bool whole = std::fread(&h, sizeof(h), 1, f) == 1 &&
+                       std::fread(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+    const bool trailing = whole && std::fgetc(f) != EOF;
+    std::fclose(f);
+    if (!whole || trailing) return fail(c, ME_ERR_ARG, "not a proposal checkpoint (wrong size)");
+    if (std::memcmp(h.magic, kMagic, 8) != 0 || h.version != 1)
+        return fail(c, ME_ERR_ARG, "not a proposal checkpoint (magic or version)");
+    if (h.nparams != (uint32_t)NPARAMS || h.nlogits != (uint32_t)NLOGIT || h.step < 0)
+        return fail(c, ME_ERR_ARG, "checkpoint of a different network shape");
+    if (crc32_update(0u, reinterpret_cast<const uint8_t*>(buf.data()), sizeof(float) * buf.size()) != h.crc)
+        return fail(c, ME_ERR_ARG, "checkpoint payload damaged (CRC mismatch)");
+    cudaError_t e = cudaMemcpy(P->p, buf.data(), sizeof(float) * NPARAMS, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(P->m, buf.data() + NPARAMS, sizeof(float) * NPARAMS, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(P->v, buf.data() + 2 * NPARAMS, sizeof(float) * NPARAMS, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = repack(P, nullptr);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(c, e, "me_proposal_load");
+    P->step = h.step;
+    return ME_OK;
 }
 
 int me_proposal_get_params(me_ctx* c, me_proposal* P, float* host)

@@ -28,7 +28,8 @@ EXPORTS = ["me_init", "me_free", "me_last_error", "me_estimate", "me_estimate_ba
            "me_proposal_create", "me_proposal_free", "me_proposal_set_params", "me_proposal_get_params",
            "me_proposal_train_step", "me_proposal_logits", "me_estimate_learned_batch",
            "me_estimate_eval_batch", "me_graph_create_eval", "me_estimate_median_batch", "me_mvp_stats",
-           "me_fs_dual_batch", "me_estimate_host_batch", "me_inject_wait_timeout"]
+           "me_fs_dual_batch", "me_estimate_host_batch", "me_inject_wait_timeout", "me_proposal_save",
+           "me_proposal_load"]
 ME_PROPOSAL_NPARAMS = 37532
 ME_PROPOSAL_NLOGITS = 68
 
@@ -97,6 +98,8 @@ def load(build_if_missing: bool = True):
             L.me_proposal_free.restype = None
             L.me_proposal_set_params.argtypes = [P, P, P]
             L.me_proposal_get_params.argtypes = [P, P, P]
+            L.me_proposal_save.argtypes = [P, P, ctypes.c_char_p]
+            L.me_proposal_load.argtypes = [P, P, ctypes.c_char_p]
             L.me_proposal_train_step.argtypes = [P, P, ctypes.POINTER(FrameDesc), I, ctypes.c_float,
                                                  ctypes.POINTER(ctypes.c_float), P, P]
             L.me_proposal_logits.argtypes = [P, P, ctypes.POINTER(FrameDesc), P, P]
@@ -275,6 +278,12 @@ class Context:
         a = np.zeros(ME_PROPOSAL_NPARAMS, np.float32)
         self._check(self.L.me_proposal_get_params(self.h, prop, ctypes.c_void_p(a.ctypes.data)))
         return a
+
+    def me_proposal_save(self, prop, path):
+        self._check(self.L.me_proposal_save(self.h, prop, os.fsencode(path)))
+
+    def me_proposal_load(self, prop, path):
+        self._check(self.L.me_proposal_load(self.h, prop, os.fsencode(path)))
 
     def me_proposal_train_step(self, prop, descs, lr, want_grad=False, stream=None):
         loss = ctypes.c_float(0.0)
