@@ -401,8 +401,9 @@ int me_tune_batch(me_ctx* ctx, const me_frame_desc* descs, int n, int block, int
 int me_absdiff_peak(me_ctx* ctx, int iters, double* out, int n_variants, int* used, void* stream);
 
 /* me_check_status: synchronise `stream` and report a device-side error that
- * a kernel recorded (ME_ERR_TIMEOUT for a bounded wait that gave up); the
- * recorded flag is cleared. */
+ * a kernel recorded (ME_ERR_TIMEOUT for a bounded wait that gave up;
+ * ME_ERR_CUDA for an access the bounds-check build, compiled with ME_CHECK,
+ * refused); the recorded flags are cleared. */
 int me_check_status(me_ctx* ctx, void* stream);
 
 /* me_inject_wait_timeout: failure-detection test hook (not in the paper).

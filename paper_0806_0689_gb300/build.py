@@ -39,23 +39,47 @@ def _deps():
         os.path.join(INCLUDE, "me.h")]
 
 
-def is_stale() -> bool:
-    if not os.path.exists(LIB):
+# Library variants: the default build, and "check", whose DCDS tile kernel
+# bounds-checks every shared-memory access and records a violation in the
+# status word instead of making it (a stand-in for a memory sanitizer).
+VARIANTS = {"": [], "check": ["-DME_CHECK"]}
+
+
+def variant() -> str:
+    """The variant this process loads: $ME_LIB_VARIANT, default ""."""
+    v = os.environ.get("ME_LIB_VARIANT", "")
+    if v not in VARIANTS:
+        raise ValueError(f"ME_LIB_VARIANT must be one of {sorted(VARIANTS)}, not {v!r}")
+    return v
+
+
+def paths(v: str = ""):
+    """(build directory, library path) of variant v."""
+    d = BUILD if not v else os.path.join(HERE, f"_build_{v}")
+    return d, os.path.join(d, "libme.so")
+
+
+def is_stale(v: str = "") -> bool:
+    lib = paths(v)[1]
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(p) > t for p in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    if not force and not is_stale():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra_flags=(), variant_name=None) -> str:
+    v = variant() if variant_name is None else variant_name
+    bdir, lib = paths(v)
+    if not force and not is_stale(v):
+        return lib
+    os.makedirs(bdir, exist_ok=True)
     cc = nvcc()
     objs = []
+    flags = [*VARIANTS[v], *extra_flags]
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-        cmd = [cc, *ARCH, *NVCC_FLAGS, *extra_flags, "-c", src, "-o", obj]
+        obj = os.path.join(bdir, os.path.basename(src)[:-3] + ".o")
+        cmd = [cc, *ARCH, *NVCC_FLAGS, *flags, "-c", src, "-o", obj]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -67,13 +91,13 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
 
     with concurrent.futures.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
         objs = list(ex.map(compile_one, sources()))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -47,6 +47,55 @@ namespace {
 
 using namespace dcds;
 
+// Bounds-check build (-DME_CHECK, the stand-in for a memory sanitizer): every
+// shared-memory word the search reads from a staged tile is checked against
+// the region it belongs to (the tile's reference window, or its current
+// blocks), and every ring and bitmap index against its array; an access
+// outside is skipped (a read gives 0) and recorded in the status word
+// (STATUS_BOUNDS).  The default build compiles the checks away.
+struct Region {
+#ifdef ME_CHECK
+    const uint8_t* lo;
+    const uint8_t* hi;
+    unsigned* status;
+#endif
+};
+
+__device__ __forceinline__ Region region(const uint8_t* lo, size_t bytes, unsigned* status)
+{
+#ifdef ME_CHECK
+    return Region{lo, lo + bytes, status};
+#else
+    (void)lo; (void)bytes; (void)status;
+    return Region{};
+#endif
+}
+
+__device__ __forceinline__ bool index_ok(int i, int n, unsigned* status)
+{
+#ifdef ME_CHECK
+    if (i >= 0 && i < n) return true;
+    if (status) atomicOr(status, STATUS_BOUNDS);
+    return false;
+#else
+    (void)i; (void)n; (void)status;
+    return true;
+#endif
+}
+
+__device__ __forceinline__ uint32_t ld_word(const uint8_t* p, const Region& g)
+{
+#ifdef ME_CHECK
+    if (p < g.lo || p + 4 > g.hi || (reinterpret_cast<uintptr_t>(p) & 3u)) {
+        if (g.status) atomicOr(g.status, STATUS_BOUNDS);
+        return 0u;
+    }
+#else
+    (void)g;
+#endif
+    return *reinterpret_cast<const uint32_t*>(p);
+}
+
 // Sec. IV measures of one finished block into the thread's sums.
 // SADs of NP candidates (slots i0 .. i0 + NP - 1 of qx / qy) of a 4-lane group:
 // lane l4 holds RPL rows of one 4-byte column of the block (cb); the loads of
@@ -54,7 +103,8 @@ using namespace dcds;
 // group (every lane of the warp takes part in the shuffles).
 template <int NP, int V, int RPL>
 __device__ __forceinline__ void eval_points(const uint8_t* win, int WP, int wx0, int wy0, const int (&qx)[4],
-                                            const int (&qy)[4], const uint32_t (&cb)[RPL], uint32_t (&sad)[4], int i0)
+                                            const int (&qy)[4], const uint32_t (&cb)[RPL], uint32_t (&sad)[4], int i0,
+                                            const Region& gw)
 {
     const uint8_t* p[NP];
     unsigned sh[NP];
@@ -70,8 +120,8 @@ __device__ __forceinline__ void eval_points(const uint8_t* win, int WP, int wx0,
     for (int r = 0; r < RPL; ++r) {
 #pragma unroll
         for (int k = 0; k < NP; ++k) {
-            const uint32_t l = *reinterpret_cast<const uint32_t*>(p[k] + r * WP);
-            const uint32_t h = *reinterpret_cast<const uint32_t*>(p[k] + r * WP + 4);
+            const uint32_t l = ld_word(p[k] + r * WP, gw);
+            const uint32_t h = ld_word(p[k] + r * WP + 4, gw);
             a[k] = sadacc<V>(__funnelshift_r(l, h, sh[k]), cb[r], a[k]);
         }
     }
@@ -181,6 +231,8 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
         const int WP = kTile + 2 * rx;  // window row pitch
         const uint8_t* win = stage;
         const uint8_t* curS = stage + cur_off;
+        const Region gw = region(win, (size_t)WP * (kTile + 2 * R), status);  // this tile's window rows
+        const Region gc = region(curS, (size_t)kTile * kTile, status);       // its current blocks
 
         // ------------------------------------------------ phase A: HCSP
         for (int row = warp; row < TXB; row += nwarps) {
@@ -192,7 +244,7 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
             uint32_t cw[B];
             const uint32_t* cp = reinterpret_cast<const uint32_t*>(curS + (row * B) * kTile + g * B + 4 * w);
 #pragma unroll
-            for (int r = 0; r < B; ++r) cw[r] = cp[r * (kTile / 4)];
+            for (int r = 0; r < B; ++r) cw[r] = ld_word(reinterpret_cast<const uint8_t*>(cp + r * (kTile / 4)), gc);
             const uint8_t* base = win + (row * B + R - 1) * WP + rx + g * B + 4 * w - 4;
             uint32_t acc[7];
             uint32_t sq0 = 0u;  // sum of squared errors at (0,0), EVAL only
@@ -200,10 +252,10 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
             for (int k = 0; k < 7; ++k) acc[k] = 0u;
 #pragma unroll
             for (int jj = -1; jj <= B; ++jj) {
-                const uint32_t* rp = reinterpret_cast<const uint32_t*>(base + (jj + 1) * WP);
-                const uint32_t b = rp[1];
+                const uint8_t* rp = base + (jj + 1) * WP;
+                const uint32_t b = ld_word(rp + 4, gw);
                 if (jj >= 0 && jj < B) {
-                    const uint32_t a = rp[0], c = rp[2];
+                    const uint32_t a = ld_word(rp, gw), c = ld_word(rp + 8, gw);
                     if constexpr (EVAL) {
                         const uint32_t d0 = __vabsdiffu4(b, cw[jj]);
                         sq0 = __dp4a(d0, d0, sq0);
@@ -258,7 +310,7 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
                 int rbase = 0;
                 if (lane == first) rbase = atomicAdd(&s_ring_n, __popc(bal));
                 rbase = __shfl_sync(FULL, rbase, first);
-                if (cont) {
+                if (cont && index_ok(rbase + __popc(bal & ((1u << lane) - 1u)), NMB, status)) {
                     const int rank = __popc(bal & ((1u << lane) - 1u));
                     ring[rbase + rank] = make_uint2((uint32_t)(row * TXB + g) | ((uint32_t)best << 8) |
                                                         ((uint32_t)__popc(vmask) << 11),
@@ -306,7 +358,7 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
                     int idx = base + __popc(need & ((1u << lane) - 1u));
                     idx = __shfl_sync(FULL, idx, lead);
                     if (act == 0) {
-                        if (idx >= nring) {
+                        if (idx >= nring || !index_ok(idx, NMB, status)) {
                             act = 2;
                         } else {
                             const uint2 e = ring[idx];
@@ -324,7 +376,8 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
                             const uint32_t* cp = reinterpret_cast<const uint32_t*>(
                                 curS + (byl * B + rb * RPL) * kTile + bxl * B + 4 * wb);
 #pragma unroll
-                            for (int r = 0; r < RPL; ++r) cb[r] = cp[r * (kTile / 4)];
+                            for (int r = 0; r < RPL; ++r)
+                                cb[r] = ld_word(reinterpret_cast<const uint8_t*>(cp + r * (kTile / 4)), gc);
                             decode(kHcsp, hb, cx, cy);
                             bxp = cx; byp = cy; bsad = e.y;
                             nsp = (int)((e.x >> 11) & 7u);
@@ -338,7 +391,7 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
                                 decode(kHcsp, k, ox, oy);
                                 if (ox >= dxlo && ox <= dxhi && oy >= dylo && oy <= dyhi) {
                                     const int bit = (oy + R) * side + (ox + R);
-                                    atomicOr(&bm[bit >> 5], 1u << (bit & 31));
+                                    if (index_ok(bit >> 5, nwb, status)) atomicOr(&bm[bit >> 5], 1u << (bit & 31));
                                     wmin = min(wmin, bit >> 5);
                                     wmax = max(wmax, bit >> 5);
                                 }
@@ -370,7 +423,7 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
                     if (valid) {
                         if (counted) {
                             bit = (y + R) * side + (x + R);
-                            fresh = ((bm[bit >> 5] >> (bit & 31)) & 1u) == 0u;
+                            fresh = index_ok(bit >> 5, nwb, status) && ((bm[bit >> 5] >> (bit & 31)) & 1u) == 0u;
                         } else {
                             fresh = (l4 == 0 ? ds0 : ds1) == kUnknown;
                         }
@@ -379,7 +432,7 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
                 const unsigned vb = (__ballot_sync(FULL, valid) >> lead) & 15u;
                 const unsigned nb = (__ballot_sync(FULL, fresh) >> lead) & 15u;
                 if (counted && fresh) {
-                    atomicOr(&bm[bit >> 5], 1u << (bit & 31));
+                    if (index_ok(bit >> 5, nwb, status)) atomicOr(&bm[bit >> 5], 1u << (bit & 31));
                     wmin = min(wmin, bit >> 5);
                     wmax = max(wmax, bit >> 5);
                 }
@@ -409,10 +462,10 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
                 // geometry rules out after the HCSP, would take one more pass)
                 const bool three = __any_sync(FULL, ncand > 2);
                 if (three) {
-                    eval_points<3, V, RPL>(win, WP, wx0, wy0, qx, qy, cb, sad, 0);
-                    if (__any_sync(FULL, ncand > 3)) eval_points<1, V, RPL>(win, WP, wx0, wy0, qx, qy, cb, sad, 3);
+                    eval_points<3, V, RPL>(win, WP, wx0, wy0, qx, qy, cb, sad, 0, gw);
+                    if (__any_sync(FULL, ncand > 3)) eval_points<1, V, RPL>(win, WP, wx0, wy0, qx, qy, cb, sad, 3, gw);
                 } else {
-                    eval_points<2, V, RPL>(win, WP, wx0, wy0, qx, qy, cb, sad, 0);
+                    eval_points<2, V, RPL>(win, WP, wx0, wy0, qx, qy, cb, sad, 0, gw);
                 }
 
                 // ---- (4) best point of the list, then switching strategies (Sec. III-B) ----
@@ -446,11 +499,12 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
                             out_sad[blk] = bsad;
                             if (out_nsp) out_nsp[blk] = (uint16_t)nsp;
                         }
-                        for (int i = wmin; i <= wmax; ++i) bm[i] = 0u;
+                        for (int i = wmin; i <= wmax; ++i)
+                            if (index_ok(i, nwb, status)) bm[i] = 0u;
                         wmin = INT_MAX; wmax = -1;
                         act = 0;
                         // the ring entry now holds the final result for the evaluation pass
-                        if (EVAL && l4 == 0)
+                        if (EVAL && l4 == 0 && index_ok(ridx, NMB, status))
                             ring[ridx] = make_uint2((uint32_t)rmb | ((uint32_t)(bxp + 32) << 8) |
                                                         ((uint32_t)(byp + 32) << 16),
                                                     bsad | ((uint32_t)nsp << 16));
@@ -470,7 +524,7 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
                 const bool ok = i < nring;
                 uint32_t q = 0u, fw = 0u, fsad = 0u;
                 int dx = 0, dy = 0, fnsp = 0;
-                if (ok) {
+                if (ok && index_ok(i, NMB, status)) {
                     const uint2 e = ring[i];
                     const int mb = (int)(e.x & 255u);
                     dx = (int)((e.x >> 8) & 255u) - 32;
@@ -486,9 +540,10 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
                                                                            bxl * B + 4 * wb);
 #pragma unroll
                     for (int r = 0; r < RPL; ++r) {
-                        const uint32_t l0 = *reinterpret_cast<const uint32_t*>(p0 + r * WP);
-                        const uint32_t h0 = *reinterpret_cast<const uint32_t*>(p0 + r * WP + 4);
-                        const uint32_t d = __vabsdiffu4(__funnelshift_r(l0, h0, s0), cp[r * (kTile / 4)]);
+                        const uint32_t l0 = ld_word(p0 + r * WP, gw);
+                        const uint32_t h0 = ld_word(p0 + r * WP + 4, gw);
+                        const uint32_t cw0 = ld_word(reinterpret_cast<const uint8_t*>(cp + r * (kTile / 4)), gc);
+                        const uint32_t d = __vabsdiffu4(__funnelshift_r(l0, h0, s0), cw0);
                         q = __dp4a(d, d, q);
                     }
                 }

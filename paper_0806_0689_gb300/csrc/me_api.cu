@@ -1023,6 +1023,7 @@ int me_check_status(me_ctx* c, void* stream)
     if (st) {
         cudaMemset(c->status, 0, sizeof(unsigned));
         if (st & me::STATUS_TIMEOUT) return fail(c, ME_ERR_TIMEOUT, "a bounded device-side wait gave up");
+        if (st & me::STATUS_BOUNDS) return fail(c, ME_ERR_CUDA, "a bounds check failed (ME_CHECK build)");
         return fail(c, ME_ERR_ARG, "a kernel rejected its input");
     }
     return ME_OK;

@@ -72,7 +72,7 @@ struct Shape {
 };
 
 // Status bits a kernel may record (read back by me_check_status).
-enum : unsigned { STATUS_TIMEOUT = 1u, STATUS_BAD_ARG = 2u };
+enum : unsigned { STATUS_TIMEOUT = 1u, STATUS_BAD_ARG = 2u, STATUS_BOUNDS = 4u };
 
 // Bitmap of visited points: one row per dy in [-R, R], this many 32-bit
 // words per row (one bit per dx in [-R, R]).

@@ -61,7 +61,7 @@ _lib = None
 
 
 def lib_path():
-    return _build.LIB
+    return _build.paths(_build.variant())[1]
 
 
 def load(build_if_missing: bool = True):
@@ -69,7 +69,7 @@ def load(build_if_missing: bool = True):
     global _lib
     with _lock:
         if _lib is None:
-            path = _build.build() if build_if_missing else _build.LIB
+            path = _build.build() if build_if_missing else lib_path()
             if not os.path.exists(path):
                 raise FileNotFoundError(f"{path} is missing; run paper_0806_0689_gb300.build")
             L = ctypes.CDLL(path)

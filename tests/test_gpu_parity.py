@@ -191,6 +191,41 @@ def test_graph_replay_and_determinism(ctx, cif):
         ctx.me_graph_free(g)
 
 
+@pytest.mark.parametrize("algo", ["dcds", "fs"])
+def test_queue_order_does_not_change_results(ctx, qcif, cif, algo):
+    """The same frames in shuffled batch orders (so different CTAs take
+    different tiles in a different order from the work queue): every frame's
+    outputs, and for DCDS its fused evaluation sums, are byte-identical."""
+    pairs = [(qcif[t], qcif[t - 1], 7) for t in range(1, 6)] + [(cif[t], cif[t - 1], 16) for t in range(1, 5)]
+    keep, _ = _batch(ctx, [(c, r) for c, r, _ in pairs], 16, algo, [R for _, _, R in pairs])
+    ref_out, ref_sums = None, None
+    for seed in range(4):
+        order = np.random.default_rng(seed).permutation(len(pairs)) if seed else np.arange(len(pairs))
+        for (_, _, mv, sad, nsp) in keep:
+            mv.fill_(-7); sad.fill_(-1); nsp.fill_(-1)
+        items = [(keep[i][0], keep[i][1], pairs[i][2], keep[i][2], keep[i][3], keep[i][4]) for i in order]
+        descs = me.Context.frame_descs(items)
+        sums = None
+        if algo == "dcds":
+            sums = torch.zeros((len(pairs), me.ME_NSUMS), dtype=torch.int64, device="cuda")
+            ctx.me_estimate_eval_batch(descs, None, 16, algo, sums)
+        else:
+            ctx.me_estimate_batch(descs, 16, algo)
+        out = [_host(mv, sad, nsp) for (_, _, mv, sad, nsp) in keep]
+        if sums is not None:
+            s = sums.cpu().numpy()
+            sums_by_frame = np.empty_like(s)
+            sums_by_frame[order] = s
+        if ref_out is None:
+            ref_out = out
+            ref_sums = sums_by_frame if sums is not None else None
+        else:
+            for a, b2 in zip(ref_out, out):
+                assert_same(b2, a, f"order {seed}")
+            if sums is not None:
+                assert np.array_equal(sums_by_frame, ref_sums)
+
+
 def test_full_1080p_batch_sampled(ctx):
     """The benchmark's workload and launch path (captured batch of 1080p
     pairs, 16x16, +-16): sampled blocks against the oracle, and the
