@@ -17,6 +17,8 @@
 #include <unordered_map>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 using me::EvalDev;
 using me::FrameDev;
 using me::Shape;
@@ -51,6 +53,26 @@ int cuda_fail(me_ctx* c, cudaError_t e, const char* what)
 }
 
 bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+// Tracing of a public call (me_set_tracing): an NVTX range around its host
+// part and CUDA events around its work on its stream.
+struct Trace {
+    me_ctx* c;
+    cudaStream_t st;
+    Trace(me_ctx* ctx, const char* name, cudaStream_t stream) : c(ctx), st(stream)
+    {
+        if (!c || !c->tracing) return;
+        nvtxRangePushA(name);
+        cudaEventRecord(c->trace0, st);
+    }
+    ~Trace()
+    {
+        if (!c || !c->tracing) return;
+        cudaEventRecord(c->trace1, st);
+        c->traced = true;
+        nvtxRangePop();
+    }
+};
 
 std::string shape_key(int algo, int block, int range, int w, int h)
 {
@@ -392,6 +414,8 @@ void me_free(me_ctx* c)
     }
     if (c->status) cudaFree(c->status);
     if (c->median_ws) me_proposal_free(c->median_ws);
+    if (c->trace0) cudaEventDestroy(c->trace0);
+    if (c->trace1) cudaEventDestroy(c->trace1);
     me::HostPipe& P = c->pipe;
     if (P.in) cudaStreamSynchronize(P.in);
     if (P.out) cudaStreamSynchronize(P.out);
@@ -412,6 +436,7 @@ int me_estimate(me_ctx* c, const uint8_t* cur, const uint8_t* ref, int w, int h,
                 int16_t* mv, uint32_t* sad, uint16_t* nsp, void* stream)
 {
     if (!c) return ME_ERR_ARG;
+    Trace trace(c, "me_estimate", (cudaStream_t)stream);
     me_frame_desc d{cur, ref, w, h, w, range, mv, sad, nsp};
     int rc = validate_batch(c, &d, 1, block, algo);
     if (rc != ME_OK) return rc;
@@ -421,6 +446,7 @@ int me_estimate(me_ctx* c, const uint8_t* cur, const uint8_t* ref, int w, int h,
 int me_estimate_batch(me_ctx* c, const me_frame_desc* descs, int n, int block, int algo, void* stream)
 {
     if (!c) return ME_ERR_ARG;
+    Trace trace(c, "me_estimate_batch", (cudaStream_t)stream);
     int rc = validate_batch(c, descs, n, block, algo);
     if (rc != ME_OK) return rc;
     int mr = 1, mw = 0, mh = 0;
@@ -724,6 +750,7 @@ int me_estimate_eval_batch(me_ctx* c, const me_frame_desc* descs, const int16_t*
                            int algo, uint64_t* sums, void* stream)
 {
     if (!c) return ME_ERR_ARG;
+    Trace trace(c, "me_estimate_eval_batch", (cudaStream_t)stream);
     int rc = validate_batch(c, descs, n, block, algo);
     if (rc == ME_OK) rc = validate_eval(c, descs, mv_fs, n, algo, sums);
     if (rc != ME_OK) return rc;
@@ -738,6 +765,7 @@ int me_estimate_eval_batch(me_ctx* c, const me_frame_desc* descs, const int16_t*
 int me_fs_dual_batch(me_ctx* c, const me_frame_desc* d16, const me_frame_desc* d8, int n, void* stream)
 {
     if (!c) return ME_ERR_ARG;
+    Trace trace(c, "me_fs_dual_batch", (cudaStream_t)stream);
     int rc = validate_batch(c, d16, n, 16, ME_ALGO_FS);
     if (rc != ME_OK) return rc;
     if (!d8) return fail(c, ME_ERR_ARG, "d8 must not be NULL");
@@ -761,6 +789,7 @@ int me_fs_dual_batch(me_ctx* c, const me_frame_desc* d16, const me_frame_desc* d
 int me_graph_launch(me_ctx* c, me_graph* g, void* stream)
 {
     if (!c || !g) return ME_ERR_ARG;
+    Trace trace(c, "me_graph_launch", (cudaStream_t)stream);
     cudaError_t e = cudaGraphLaunch(g->exec, (cudaStream_t)stream);
     return e == cudaSuccess ? ME_OK : cuda_fail(c, e, "cudaGraphLaunch");
 }
@@ -778,6 +807,7 @@ void me_graph_free(me_graph* g)
 int me_eval_batch(me_ctx* c, const me_eval_desc* d, int n, int block, uint64_t* sums, void* stream)
 {
     if (!c) return ME_ERR_ARG;
+    Trace trace(c, "me_eval_batch", (cudaStream_t)stream);
     if (!d || n <= 0 || !sums) return fail(c, ME_ERR_ARG, "descs and sums must not be NULL, n positive");
     if (!aligned(sums, 8)) return fail(c, ME_ERR_ARG, "sums must be 8-byte aligned");
     if (n > 65535) return fail(c, ME_ERR_ARG, "at most 65535 frames per evaluation batch");
@@ -815,6 +845,7 @@ int me_eval_batch(me_ctx* c, const me_eval_desc* d, int n, int block, uint64_t* 
 int me_mvp_stats(me_ctx* c, const me_frame_desc* d, int n, int range, uint64_t* out, void* stream)
 {
     if (!c) return ME_ERR_ARG;
+    Trace trace(c, "me_mvp_stats", (cudaStream_t)stream);
     if (!d || n <= 0 || !out) return fail(c, ME_ERR_ARG, "descs and out must not be NULL, n positive");
     if (!aligned(out, 8)) return fail(c, ME_ERR_ARG, "out must be 8-byte aligned");
     if (range < 1 || range > ME_MAX_RANGE) return fail(c, ME_ERR_ARG, "range must be in 1..32");
@@ -1005,6 +1036,27 @@ int me_absdiff_peak(me_ctx* c, int iters, double* out, int n_variants, int* used
     return ME_OK;
 }
 
+int me_set_tracing(me_ctx* c, int on)
+{
+    if (!c) return ME_ERR_ARG;
+    if (on && !c->trace0) {
+        cudaError_t e = cudaEventCreate(&c->trace0);
+        if (e == cudaSuccess) e = cudaEventCreate(&c->trace1);
+        if (e != cudaSuccess) return cuda_fail(c, e, "cudaEventCreate");
+    }
+    c->tracing = on ? 1 : 0;
+    return ME_OK;
+}
+
+int me_last_call_ms(me_ctx* c, float* ms)
+{
+    if (!c || !ms) return ME_ERR_ARG;
+    if (!c->traced) return fail(c, ME_ERR_UNSUPPORTED, "no traced call yet (me_set_tracing)");
+    cudaError_t e = cudaEventSynchronize(c->trace1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(ms, c->trace0, c->trace1);
+    return e == cudaSuccess ? ME_OK : cuda_fail(c, e, "me_last_call_ms");
+}
+
 int me_inject_wait_timeout(me_ctx* c, int on)
 {
     if (!c) return ME_ERR_ARG;
@@ -1033,6 +1085,7 @@ int me_estimate_host_batch(me_ctx* c, const me_frame_desc* descs, const int16_t*
                            int algo, uint64_t* sums, int chunk, void* stream)
 {
     if (!c) return ME_ERR_ARG;
+    Trace trace(c, "me_estimate_host_batch", (cudaStream_t)stream);
     int rc = validate_batch(c, descs, n, block, algo);
     if (rc == ME_OK && sums) rc = validate_eval(c, descs, mv_fs, n, algo, sums);
     if (rc != ME_OK) return rc;

@@ -58,6 +58,9 @@ struct me_ctx {
     struct me_proposal* median_ws = nullptr;  // wavefront buffers of the neighbour-median start (lazy)
     me::HostPipe pipe;                        // me_estimate_host_batch staging (lazy)
     int inject_wait_timeout = 0;              // failure-detection test hook (me_inject_wait_timeout)
+    int tracing = 0;                          // me_set_tracing: NVTX ranges and CUDA events per call
+    cudaEvent_t trace0 = nullptr, trace1 = nullptr;
+    bool traced = false;                      // a traced call has recorded its events
 };
 
 struct me_graph {

@@ -29,7 +29,7 @@ EXPORTS = ["me_init", "me_free", "me_last_error", "me_estimate", "me_estimate_ba
            "me_proposal_train_step", "me_proposal_logits", "me_estimate_learned_batch",
            "me_estimate_eval_batch", "me_graph_create_eval", "me_estimate_median_batch", "me_mvp_stats",
            "me_fs_dual_batch", "me_estimate_host_batch", "me_inject_wait_timeout", "me_proposal_save",
-           "me_proposal_load"]
+           "me_proposal_load", "me_set_tracing", "me_last_call_ms"]
 ME_PROPOSAL_NPARAMS = 37532
 ME_PROPOSAL_NLOGITS = 68
 
@@ -313,6 +313,14 @@ class Context:
 
     def me_check_status(self, stream=None):
         self._check(self.L.me_check_status(self.h, _stream(stream)))
+
+    def me_set_tracing(self, on):
+        self._check(self.L.me_set_tracing(self.h, int(bool(on))))
+
+    def me_last_call_ms(self):
+        ms = ctypes.c_float(0.0)
+        self._check(self.L.me_last_call_ms(self.h, ctypes.byref(ms)))
+        return ms.value
 
     def me_inject_wait_timeout(self, on):
         """Failure-detection test hook: while on, DCDS tile-kernel launches
