@@ -139,10 +139,36 @@ __device__ __forceinline__ void st_release(int* p, int v)
 constexpr uint32_t kSpinLimit = 1u << 22;
 
 struct WarpBlock {
-    const uint8_t* ref;
-    int pitch, px, py, dxlo, dxhi, dylo, dyhi, R;
+    const uint32_t* win;  // the block's reference window, staged in this warp's shared memory
+    int ww, rx;           // window words per row; columns left of the block (R rounded up to 4)
+    int px, py, dxlo, dxhi, dylo, dyhi, R;
     uint32_t c0, c1;  // this lane's 8 current pixels (row lane/2, half lane%2)
 };
+
+// Reference-window geometry of a 16x16 block at range R: rows py - R ..
+// py + 15 + R; words from column px - rx (rx = R rounded up to 4), wide enough
+// for the three aligned words an unaligned 8-pixel segment can touch.
+__host__ __device__ inline int win_rx(int R) { return (R + 3) & ~3; }
+__host__ __device__ inline int win_words(int R) { return win_rx(R) / 2 + 5; }
+__host__ __device__ inline int win_rows(int R) { return 16 + 2 * R; }
+
+// Stage the window of the block at (px, py) into `win` (the whole warp):
+// coalesced word loads, issued together; words outside the frame (never
+// read, candidates stay inside the frame) are set to zero.
+__device__ __forceinline__ void stage_window(uint32_t* win, const uint8_t* ref, int pitch, int w, int h, int px,
+                                             int py, int R, int lane)
+{
+    const int ww = win_words(R), rows = win_rows(R), x0 = px - win_rx(R), y0 = py - R;
+    for (int i = lane; i < rows * ww; i += 32) {
+        const int r = i / ww, c = i - r * ww;
+        const int y = y0 + r, x = x0 + 4 * c;
+        uint32_t v = 0u;
+        if (y >= 0 && y < h && x >= 0 && x + 4 <= w)
+            v = __ldg(reinterpret_cast<const uint32_t*>(ref + (size_t)y * pitch + x));
+        win[i] = v;
+    }
+    __syncwarp();
+}
 
 // Visit the points (qx[i], qy[i]) of one pattern list: a point outside the
 // window/frame or visited before is skipped; the others are marked, counted
@@ -178,12 +204,13 @@ __device__ __forceinline__ unsigned visit_many(const WarpBlock& b, uint32_t* bm,
         w0[i] = w1[i] = w2[i] = 0u;
         sh[i] = 0u;
         if ((fresh >> i) & 1u) {
-            const long g = (long)(b.py + qy[i] + r) * b.pitch + b.px + qx[i] + 8 * hh;
-            const uint32_t* wp = reinterpret_cast<const uint32_t*>(b.ref + (g & ~3l));
-            sh[i] = (unsigned)(g & 3) * 8u;
-            w0[i] = __ldg(wp);
-            w1[i] = __ldg(wp + 1);
-            if (sh[i]) w2[i] = __ldg(wp + 2);  // inside the row whenever the segment is unaligned
+            // byte column of this lane's segment in the window (its alignment equals the frame's)
+            const int x = b.rx + qx[i] + 8 * hh;
+            const uint32_t* wp = b.win + (qy[i] + b.R + r) * b.ww + (x >> 2);
+            sh[i] = (unsigned)(x & 3) * 8u;
+            w0[i] = wp[0];
+            w1[i] = wp[1];
+            if (sh[i]) w2[i] = wp[2];  // inside the staged row whenever the segment is unaligned
         }
     }
 #pragma unroll
@@ -258,6 +285,8 @@ __global__ void __launch_bounds__(256) learned_dcds_kernel(const PropFrame* __re
     const int side_max = 2 * max_range + 1;
     const int nwb = (side_max * side_max + 31) / 32;
     uint32_t* bm = bm_all + warp * nwb;
+    // after the 8 bitmaps: one reference window per warp
+    uint32_t* win = bm_all + 8 * nwb + warp * win_rows(max_range) * win_words(max_range);
     for (int i = lane; i < nwb; i += 32) bm[i] = 0u;
     __syncwarp();
     int wmin = INT_MAX, wmax = -1;
@@ -272,8 +301,10 @@ __global__ void __launch_bounds__(256) learned_dcds_kernel(const PropFrame* __re
         const int bx = k % F.nbx, by = k / F.nbx;
         // ---- work that does not depend on the neighbours: the block, the origin's SAD ----
         const int R = F.range, px = bx * 16, py = by * 16;
+        // the window does not depend on the neighbours: its loads overlap the wait below
+        stage_window(win, F.ref, F.pitch, F.w, F.h, px, py, R, lane);
         WarpBlock b;
-        b.ref = F.ref; b.pitch = F.pitch; b.px = px; b.py = py; b.R = R;
+        b.win = win; b.ww = win_words(R); b.rx = win_rx(R); b.px = px; b.py = py; b.R = R;
         b.dxlo = max(-R, -px); b.dxhi = min(R, F.w - 16 - px);
         b.dylo = max(-R, -py); b.dyhi = min(R, F.h - 16 - py);
         {
@@ -857,9 +888,14 @@ int wavefront_batch(me_ctx* c, me_proposal* P, const me_frame_desc* d, int n, in
     int max_range = 1;
     for (int i = 0; i < n; ++i) max_range = std::max(max_range, d[i].range);
     const int side = 2 * max_range + 1;
-    const size_t smem = (size_t)8 * ((side * side + 31) / 32) * 4;
+    const size_t smem = (size_t)8 * ((side * side + 31) / 32) * 4 +
+                        (size_t)8 * win_rows(max_range) * win_words(max_range) * 4;
+    int per_sm = 0;
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(learned_dcds_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, learned_dcds_kernel, 256, smem);
     if (e == cudaSuccess) {
-        learned_dcds_kernel<<<c->num_sms * 4, 256, smem, st>>>(P->frames, n, P->order, (int)total,
+        learned_dcds_kernel<<<c->num_sms * std::max(1, std::min(per_sm, 4)), 256, smem, st>>>(P->frames, n, P->order, (int)total,
                                                               median ? nullptr : zpart, P->p + P_FW, done, counter,
                                                               starts, c->status, max_range);
         e = cudaGetLastError();
