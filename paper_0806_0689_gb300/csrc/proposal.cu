@@ -49,6 +49,7 @@ struct me_proposal {
     int frames_cap = 0;
     int* order = nullptr;  // wavefront order
     long order_cap = 0;
+    std::vector<int> order_key;  // the (nbx, nby) of every frame the order on the device was built for
 };
 
 namespace {
@@ -124,16 +125,20 @@ __global__ void feat_kernel(const PropFrame* __restrict__ fr, int nframes, long 
 // ------------------------------------------------------------------ learned-start search
 __device__ __forceinline__ int med3(int a, int b, int c) { return max(min(a, b), min(max(a, b), c)); }
 
-__device__ __forceinline__ int ld_acquire(const int* p)
+// The wavefront hand-off word of a block: done bit << 32 | its MV.  The waiter
+// needs nothing but this word (the MV travels in it, and the blocks' other
+// outputs are read only after the kernel), so the flag is written and polled
+// with relaxed gpu-scope accesses: no fence on either side of the hand-off.
+__device__ __forceinline__ unsigned long long ld_relaxed64(const unsigned long long* p)
 {
-    int v;
-    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
 
-__device__ __forceinline__ void st_release(int* p, int v)
+__device__ __forceinline__ void st_relaxed64(unsigned long long* p, unsigned long long v)
 {
-    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
 constexpr uint32_t kSpinLimit = 1u << 22;
@@ -275,7 +280,8 @@ __global__ void __launch_bounds__(256) learned_dcds_kernel(const PropFrame* __re
                                                            const int* __restrict__ order, int total,
                                                            const float* __restrict__ zpart,
                                                            const float* __restrict__ fw,
-                                                           int* __restrict__ done, int* __restrict__ counter,
+                                                           unsigned long long* __restrict__ done,
+                                                           int* __restrict__ counter,
                                                            int16_t* __restrict__ starts, unsigned* __restrict__ status,
                                                            int max_range)
 {
@@ -331,12 +337,13 @@ __global__ void __launch_bounds__(256) learned_dcds_kernel(const PropFrame* __re
             if (ax >= 0 && ax < F.nbx && ay >= 0) {
                 const int nk = ay * F.nbx + ax;
                 uint32_t it = 0;
-                while (ld_acquire(done + F.base + nk) == 0) {
+                unsigned long long fl;
+                // the neighbour publishes its MV with its done bit: one load brings both
+                while (((fl = ld_relaxed64(done + F.base + nk)) >> 32) == 0ull) {
                     if (++it > kSpinLimit) { late = true; break; }
-                    __nanosleep(64);
                 }
                 if (!late) {
-                    const uint32_t m = __ldcg(reinterpret_cast<const uint32_t*>(F.mv) + nk);
+                    const uint32_t m = (uint32_t)fl;
                     nmx = (int)(int16_t)(m & 0xffffu);
                     nmy = (int)(int16_t)(m >> 16);
                     mvx = (float)nmx * (1.f / 16.f);
@@ -452,8 +459,7 @@ __global__ void __launch_bounds__(256) learned_dcds_kernel(const PropFrame* __re
             }
             for (int i = wmin; i <= wmax; ++i) bm[i] = 0u;
             wmin = INT_MAX; wmax = -1;
-            __threadfence();
-            st_release(done + gid, 1);
+            st_relaxed64(done + gid, (1ull << 32) | ((uint64_t)(uint16_t)byp << 16) | (uint16_t)bxp);
         }
         __syncwarp();
     }
@@ -840,7 +846,7 @@ int wavefront_batch(me_ctx* c, me_proposal* P, const me_frame_desc* d, int n, in
     // buffers after the trunk workspace: conv-4 features, done flags, counter
     Ws w;
     const size_t trunk = ws_layout(nullptr, kChunk, false, &w);
-    const size_t need = al(trunk) + al((size_t)total * 128 * 2) + al((size_t)total * 4) + 256 +
+    const size_t need = al(trunk) + al((size_t)total * 128 * 2) + al((size_t)total * 8) + 256 +
                         al((size_t)total * NLOGIT * 4);
     if (P->ws_cap < need) {
         cudaFree(P->ws);
@@ -851,32 +857,46 @@ int wavefront_batch(me_ctx* c, me_proposal* P, const me_frame_desc* d, int n, in
     }
     ws_layout(P->ws, kChunk, false, &w);
     __nv_bfloat16* a4all = reinterpret_cast<__nv_bfloat16*>(P->ws + al(trunk));
-    int* done = reinterpret_cast<int*>(P->ws + al(trunk) + al((size_t)total * 128 * 2));
-    int* counter = done + ((al((size_t)total * 4)) / 4);
-    float* zpart = reinterpret_cast<float*>(P->ws + al(trunk) + al((size_t)total * 128 * 2) + al((size_t)total * 4) + 256);
-    // wavefront order: t = bx + 2 by ascending, frames interleaved
-    std::vector<int> ord;
-    ord.reserve(total);
-    {
-        std::vector<PropFrame> t(n);
-        cudaMemcpy(t.data(), P->frames, sizeof(PropFrame) * n, cudaMemcpyDeviceToHost);
+    uint8_t* flags = P->ws + al(trunk) + al((size_t)total * 128 * 2);
+    unsigned long long* done = reinterpret_cast<unsigned long long*>(flags);  // per block: done bit << 32 | MV
+    int* counter = reinterpret_cast<int*>(flags + al((size_t)total * 8));
+    float* zpart = reinterpret_cast<float*>(flags + al((size_t)total * 8) + 256);
+    // wavefront order: t = bx + 2 by ascending, frames interleaved.  It depends
+    // only on the frames' block grids, so it is kept on the device and rebuilt
+    // only when they change.
+    std::vector<int> key(2 * (size_t)n);
+    for (int i = 0; i < n; ++i) { key[2 * i] = d[i].w / 16; key[2 * i + 1] = d[i].h / 16; }
+    cudaError_t e = cudaSuccess;
+    if (key != P->order_key || P->order_cap < total) {
+        std::vector<int> ord;
+        ord.reserve(total);
+        std::vector<long> base(n);
+        long b0 = 0;
         int tmax = 0;
-        for (auto& f : t) tmax = std::max(tmax, (f.nbx - 1) + 2 * (f.nby - 1));
+        for (int i = 0; i < n; ++i) {
+            base[i] = b0;
+            b0 += (long)key[2 * i] * key[2 * i + 1];
+            tmax = std::max(tmax, (key[2 * i] - 1) + 2 * (key[2 * i + 1] - 1));
+        }
         for (int tt = 0; tt <= tmax; ++tt)
-            for (auto& f : t)
-                for (int by = 0; by < f.nby; ++by) {
+            for (int i = 0; i < n; ++i) {
+                const int nbx = key[2 * i], nby = key[2 * i + 1];
+                for (int by = 0; by < nby; ++by) {
                     const int bx = tt - 2 * by;
-                    if (bx >= 0 && bx < f.nbx) ord.push_back(f.base + by * f.nbx + bx);
+                    if (bx >= 0 && bx < nbx) ord.push_back((int)(base[i] + (long)by * nbx + bx));
                 }
+            }
+        if (P->order_cap < total) {
+            cudaFree(P->order);
+            P->order = nullptr;
+            P->order_cap = 0;
+            if (cudaMalloc(&P->order, sizeof(int) * total) != cudaSuccess) return fail(c, ME_ERR_NOMEM, "order table");
+            P->order_cap = total;
+        }
+        P->order_key.clear();  // invalid until the upload below has gone through
+        e = cudaMemcpy(P->order, ord.data(), sizeof(int) * total, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) P->order_key = key;
     }
-    if (P->order_cap < total) {
-        cudaFree(P->order);
-        P->order = nullptr;
-        P->order_cap = 0;
-        if (cudaMalloc(&P->order, sizeof(int) * total) != cudaSuccess) return fail(c, ME_ERR_NOMEM, "order table");
-        P->order_cap = total;
-    }
-    cudaError_t e = cudaMemcpyAsync(P->order, ord.data(), sizeof(int) * total, cudaMemcpyHostToDevice, st);
     // the trunk builds the features itself: one launch over every block of the batch
     if (!median && e == cudaSuccess) e = forward_infer(P, n, 0, w, (int)total, a4all, false, st);
     if (!median && e == cudaSuccess) {
@@ -884,7 +904,7 @@ int wavefront_batch(me_ctx* c, me_proposal* P, const me_frame_desc* d, int n, in
         zpart_kernel<<<zb, 4 * NLOGIT, 0, st>>>(a4all, total, P->p + P_FW, P->p + P_FB, zpart);
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess) e = cudaMemsetAsync(done, 0, al((size_t)total * 4) + 256, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(flags, 0, al((size_t)total * 8) + 256, st);
     int max_range = 1;
     for (int i = 0; i < n; ++i) max_range = std::max(max_range, d[i].range);
     const int side = 2 * max_range + 1;
