@@ -527,6 +527,21 @@ def main():
     st_f = [ctx.me_stats_from_sums(s_f[i]) for i in range(npairs)]
     mean = lambda rows, k: float(np.mean([r[k] for r in rows]))
 
+    # ---- DCDS^S (Sec. IV-C) on the same batch, fused the same way: Table X's comparison ----
+    mv_s, sad_s, nsp_s = torch.empty_like(mv), torch.empty_like(sad), torch.empty_like(nsp)
+    sums_s = torch.zeros_like(sums)
+    d_s = me.Context.frame_descs((curs[i], refs[i], R_, mv_s[i], sad_s[i], nsp_s[i]) for i in range(npairs))
+    g_s = ctx.me_graph_create_eval(d_s, fs_list, B_, "dcds_s", sums_s)
+    simpl_ms = _time(lambda: ctx.me_graph_launch(g_s))
+    ctx.me_graph_free(g_s)
+    s_s = sums_s.cpu().numpy().view(np.uint64)
+    st_s = [ctx.me_stats_from_sums(s_s[i]) for i in range(npairs)]
+    simpl_line = {"launch_ms": simpl_ms, "macroblocks_per_s": mbs_step / (simpl_ms * 1e-3),
+                  "nsp_per_mb": mean(st_s, "nsp"), "psnr_db": mean(st_s, "psnr"),
+                  "nsp_minus_dcds": mean(st_s, "nsp") - mean(st_d, "nsp"),
+                  "psnr_minus_dcds_db": mean(st_s, "psnr") - mean(st_d, "psnr"),
+                  "paper_table_x": "NSP -0.16 to -0.36, PSNR -0.014 to -0.364 dB on its sequences"}
+
     # ---- Sec. II-C statistics of the FS field (the directional model's inputs) ----
     from paper_0806_0689_gb300 import mvp
     mvp_counts = torch.zeros(35 * (2 * R_ + 1) ** 2, dtype=torch.int64, device=dev)
@@ -694,6 +709,7 @@ def main():
         "fs_two_sizes_one_sweep": fs_dual,
         "absdiff_peak_per_s": {"variants": rates, "used": used},
         "mvp_statistics_fs_field": mvp_line,
+        "dcds_s": simpl_line,
         "tuned_shape_index": tuned,
         "step_kernels": "dcds_kernel with the Sec. IV sums fused (one launch per step)",
         "search_only_ms": search_only_ms, "unfused_eval_ms": unfused_eval_ms,
