@@ -670,7 +670,7 @@ def main():
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
-    dcds_launch_ms = float(np.median(step_ms))
+    dcds_launch_ms = float(np.mean(step_ms))  # average launch duration over the timed steps
     # frames once, MV/SAD/NSP out, the FS field in, eight sums out
     alg_bytes = npairs * (2 * W_ * H_ + nb * 10 + nb * 4 + me.ME_NSUMS * 8)
     achieved = alg_bytes / (dcds_launch_ms * 1e-3) / 1e9
