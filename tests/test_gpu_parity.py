@@ -250,6 +250,48 @@ def test_full_1080p_batch_sampled(ctx):
                 assert (got[2] <= 33 * 33).all() and (got[2] >= 17 * 17).all()
 
 
+def test_full_1080p_fused_step_sampled(ctx):
+    """The benchmark's timed step itself: the captured fused search +
+    evaluation over a 1080p batch (16x16, +-16, the FS field as mv_fs).
+    Sampled blocks against the oracle's DCDS; the sums against the separate
+    evaluation kernel on the same field and, for one frame, against the
+    oracle's evaluation (Sec. IV)."""
+    seq = synth.workload_sequence("1080p", 7, seed=3, max_motion=16)
+    pairs = [(seq[t], seq[t - 1]) for t in range(1, len(seq))]
+    n = len(pairs)
+    fs_keep, fs_descs = _batch(ctx, pairs, 16, "fs", [16] * n)
+    ctx.me_estimate_batch(fs_descs, 16, "fs")
+    keep, descs = _batch(ctx, pairs, 16, "dcds", [16] * n)
+    sums = torch.zeros((n, me.ME_NSUMS), dtype=torch.int64, device="cuda")
+    fs_fields = [k[2] for k in fs_keep]
+    g = ctx.me_graph_create_eval(descs, fs_fields, 16, "dcds", sums)
+    try:
+        for _ in range(2):  # replays refill the sums from zero
+            ctx.me_graph_launch(g)
+        torch.cuda.synchronize()
+    finally:
+        ctx.me_graph_free(g)
+    rs = np.random.default_rng(9)
+    for (cur, ref), (c, r, mv, sad, nsp) in zip(pairs, keep):
+        got = _host(mv, sad, nsp)
+        idx = np.sort(rs.choice(len(got[1]), 96, replace=False))
+        idx[:4] = [0, 119, len(got[1]) - 120, len(got[1]) - 1]
+        assert_same(tuple(x[idx] for x in got), oracle.dcds_blocks(cur, ref, 16, 16, idx), "fused 1080p")
+    e = me.Context.eval_descs((k[0], k[1], k[2], f, k[4]) for k, f in zip(keep, fs_fields))
+    sep = torch.zeros_like(sums)
+    ctx.me_eval_batch(e, 16, sep)
+    torch.cuda.synchronize()
+    assert torch.equal(sums, sep)
+    cur, ref = pairs[0]
+    mv0, _, nsp0 = _host(keep[0][2], keep[0][3], keep[0][4])
+    want = oracle.evaluate(cur, ref, 16, mv0, fs_keep[0][2].cpu().numpy(), nsp0)
+    got = ctx.me_stats_from_sums(sums[0].cpu().numpy().view(np.uint64))
+    for k in ("mad", "mse", "nsp", "probability"):
+        assert got[k] == want[k], k
+    assert abs(got["psnr"] - want["psnr"]) < 1e-9
+    assert abs(got["distance"] - want["distance"]) < 1e-7  # per-block distances summed in 2^-24 units
+
+
 def test_eval_matches_oracle(ctx, cif):
     B, R = 16, 7
     for t in (1, 2):
