@@ -454,3 +454,61 @@ def test_fs_dual_sizes_match_oracle(ctx, cif, qcif, R):
     for cur, ref, o16, o8 in keep:
         assert_same(_host(*o16), oracle.fs(cur, ref, 16, R), f"dual 16x16 R{R}")
         assert_same(_host(*o8), oracle.fs(cur, ref, 8, R), f"dual 8x8 R{R}")
+
+
+@pytest.mark.parametrize("B,pad", [(16, 16), (8, 48)])
+def test_padded_pitch(ctx, qcif, cif, B, pad):
+    """Frames whose rows are wider than the image (pitch = w + pad): every
+    search, the fused evaluation and the host-memory batch read only the
+    image, with results bit-exact with the oracle on the unpadded frames."""
+    pairs = [(qcif[2], qcif[1], 7), (cif[2], cif[1], 16), (cif[3], cif[2], 32)]
+
+    def padded(a, device):
+        h, w = a.shape
+        t = torch.full((h, w + pad), 255, dtype=torch.uint8)
+        t[:, :w] = torch.from_numpy(a)
+        t = t.to(device) if device == "cuda" else t.pin_memory()
+        return t[:, :w]
+
+    for algo in ("dcds", "dcds_s", "fs"):
+        items, keep = [], []
+        for cur, ref, R in pairs:
+            h, w = cur.shape
+            c, r = padded(cur, "cuda"), padded(ref, "cuda")
+            assert c.stride(0) == w + pad
+            mv, sad, nsp = _outs(h, w, B)
+            keep.append((mv, sad, nsp))
+            items.append((c, r, R, mv, sad, nsp))
+        ctx.me_estimate_batch(me.Context.frame_descs(items), B, algo)
+        for (cur, ref, R), (mv, sad, nsp) in zip(pairs, keep):
+            assert_same(_host(mv, sad, nsp), oracle_search(cur, ref, B, R, algo), f"{algo} pitch {pad}")
+    # fused evaluation against the separate kernel on the same padded frames
+    items, keep = [], []
+    for cur, ref, R in pairs:
+        h, w = cur.shape
+        c, r = padded(cur, "cuda"), padded(ref, "cuda")
+        mv, sad, nsp = _outs(h, w, B)
+        keep.append((c, r, mv, sad, nsp))
+        items.append((c, r, R, mv, sad, nsp))
+    sums = torch.zeros((len(pairs), me.ME_NSUMS), dtype=torch.int64, device="cuda")
+    ctx.me_estimate_eval_batch(me.Context.frame_descs(items), None, B, "dcds", sums)
+    sep = torch.zeros_like(sums)
+    ctx.me_eval_batch(me.Context.eval_descs((c, r, mv, None, nsp) for c, r, mv, sad, nsp in keep), B, sep)
+    torch.cuda.synchronize()
+    assert torch.equal(sums, sep)
+    # host-memory batch from padded pinned frames
+    items, keep = [], []
+    for cur, ref, R in pairs:
+        h, w = cur.shape
+        c, r = padded(cur, "cpu"), padded(ref, "cpu")
+        nb = (w // B) * (h // B)
+        mv = torch.empty((nb, 2), dtype=torch.int16).pin_memory()
+        sad = torch.empty((nb,), dtype=torch.int32).pin_memory()
+        nsp = torch.empty((nb,), dtype=torch.int16).pin_memory()
+        keep.append((c, r, mv, sad, nsp))
+        items.append((c, r, R, mv, sad, nsp))
+    ctx.me_estimate_host_batch(me.Context.frame_descs(items), B, "dcds", chunk=2)
+    torch.cuda.synchronize()
+    for (cur, ref, R), (_, _, mv, sad, nsp) in zip(pairs, keep):
+        got = (mv.numpy(), sad.numpy().view(np.uint32), nsp.numpy().view(np.uint16))
+        assert_same(got, oracle_search(cur, ref, B, R, "dcds"), f"host pitch {pad}")
