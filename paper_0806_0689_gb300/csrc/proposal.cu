@@ -276,6 +276,7 @@ __constant__ int8_t kFirstV[6][2] = {{0, -1}, {0, 1}, {-1, 0}, {1, 0}, {0, -2}, 
 __constant__ int8_t kDd[2][4][2] = {{{0, -1}, {0, 1}, {-2, 0}, {2, 0}}, {{-1, 0}, {1, 0}, {0, -2}, {0, 2}}};
 __constant__ int8_t kMid[2][2][2] = {{{-1, 0}, {1, 0}}, {{0, -1}, {0, 1}}};
 
+template <bool LEARNED>
 __global__ void __launch_bounds__(256) learned_dcds_kernel(const PropFrame* __restrict__ fr, int nframes,
                                                            const int* __restrict__ order, int total,
                                                            const float* __restrict__ zpart,
@@ -286,7 +287,6 @@ __global__ void __launch_bounds__(256) learned_dcds_kernel(const PropFrame* __re
                                                            int max_range)
 {
     extern __shared__ uint32_t bm_all[];
-    __shared__ float s_logit[8][NLOGIT];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int side_max = 2 * max_range + 1;
     const int nwb = (side_max * side_max + 31) / 32;
@@ -296,6 +296,13 @@ __global__ void __launch_bounds__(256) learned_dcds_kernel(const PropFrame* __re
     for (int i = lane; i < nwb; i += 32) bm[i] = 0u;
     __syncwarp();
     int wmin = INT_MAX, wmax = -1;
+    // learned start: the head's neighbour weights (6 per logit), staged once per CTA
+    __shared__ float s_wh[LEARNED ? NLOGIT * 6 : 1];
+    if (LEARNED) {
+        for (int i = threadIdx.x; i < NLOGIT * 6; i += blockDim.x)
+            s_wh[i] = __ldg(fw + (size_t)(i / 6) * NFEAT + 128 + i % 6);
+        __syncthreads();
+    }
     for (;;) {
         int idx = 0;
         if (lane == 0) idx = atomicAdd(counter, 1);
@@ -326,6 +333,13 @@ __global__ void __launch_bounds__(256) learned_dcds_kernel(const PropFrame* __re
             uint32_t v[1];
             visit_many<1>(b, bm, wmin, wmax, nsp, qx, qy, v, lane);  // the origin is always a candidate
             cval = v[0];
+        }
+        float zr[3] = {0.f, 0.f, 0.f};  // this lane's conv-feature logit parts (learned start)
+        if (LEARNED) {
+            const float* zp = zpart + (size_t)gid * NLOGIT;
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+                if (lane + 32 * j < NLOGIT) zr[j] = __ldg(zp + lane + 32 * j);
         }
         // ---- wait until the causal neighbours are final ----
         const int nbdx[3] = {-1, 0, 1}, nbdy[3] = {0, -1, -1};
@@ -359,32 +373,48 @@ __global__ void __launch_bounds__(256) learned_dcds_kernel(const PropFrame* __re
             mvf[2 * q + 1] = __shfl_sync(0xffffffffu, mvy, q);
         }
         int sx = 0, sy = 0, pv = 0;
-        if (zpart) {
-        // ---- head: the conv-feature part of the logits was computed for every block
-        //      beforehand (zpart = bias + conv terms, in the head's order); add the
-        //      neighbours' terms ----
-        const float* zp = zpart + (size_t)gid * NLOGIT;
-        for (int o = lane; o < NLOGIT; o += 32) {
-            const float* wr = fw + (size_t)o * NFEAT;
-            float acc = zp[o];
+        if constexpr (LEARNED) {
+            // ---- head: the conv-feature part of the logits (zpart, fetched before the
+            //      wait) plus the neighbours' terms, in the head's order.  Lane l holds
+            //      logits l, l + 32 and l + 64: dx classes 0-31 in its first, dx class 32
+            //      (lane 0) and dy classes 0-30 (lanes 1-31) in its second, dy classes 31
+            //      and 32 (lanes 0, 1) and the H/V pair (lanes 2, 3) in its third ----
+            float z[3];
 #pragma unroll
-            for (int q = 0; q < 6; ++q) acc += wr[128 + q] * mvf[q];
-            s_logit[warp][o] = acc;
-        }
-        __syncwarp();
-        {
-            // argmax with ties to the class nearest the centre: 0, -1, +1, -2, +2, ...
-            const float* z = s_logit[warp];
-            float bvx = z[16], bvy = z[33 + 16];
-            for (int a = 1; a <= 16; ++a) {
-                if (z[16 - a] > bvx) { bvx = z[16 - a]; sx = -a; }
-                if (z[16 + a] > bvx) { bvx = z[16 + a]; sx = a; }
-                if (z[49 - a] > bvy) { bvy = z[49 - a]; sy = -a; }
-                if (z[49 + a] > bvy) { bvy = z[49 + a]; sy = a; }
+            for (int j = 0; j < 3; ++j) {
+                float acc = zr[j];
+                const int o = min(lane + 32 * j, NLOGIT - 1);  // lanes past the last logit compute a copy, unused
+#pragma unroll
+                for (int q = 0; q < 6; ++q) acc += s_wh[o * 6 + q] * mvf[q];
+                z[j] = acc;
             }
-            pv = z[67] > z[66] ? 1 : 0;
-        }
-        __syncwarp();  // s_logit is reused by the next block of this warp
+            // argmax with ties to the class nearest the centre: 0, -1, +1, -2, +2, ...
+            // = the largest logit, then the smallest rank among equal ones
+            auto rank = [](int cls) { const int a = cls - 16; return a == 0 ? 0 : (a < 0 ? -2 * a - 1 : 2 * a); };
+            auto better = [](float v, int r, float v2, int r2) { return v > v2 || (v == v2 && r < r2); };
+            float vx = z[0];
+            int cx_ = lane;
+            if (lane == 0 && better(z[1], rank(32), vx, rank(cx_))) { vx = z[1]; cx_ = 32; }
+            float vy = z[1];  // lanes 1-31: dy class lane - 1; lane 0 replaces it below
+            int cy_ = lane - 1;
+            if (lane <= 1) {
+                const int c2 = 31 + lane;
+                if (lane == 0 || better(z[2], rank(c2), vy, rank(cy_))) { vy = z[2]; cy_ = c2; }
+            }
+            int rx_ = rank(cx_), ry_ = rank(cy_);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float v2 = __shfl_xor_sync(0xffffffffu, vx, o);
+                const int c2 = __shfl_xor_sync(0xffffffffu, cx_, o), r2 = __shfl_xor_sync(0xffffffffu, rx_, o);
+                if (better(v2, r2, vx, rx_)) { vx = v2; cx_ = c2; rx_ = r2; }
+                const float w2 = __shfl_xor_sync(0xffffffffu, vy, o);
+                const int d2 = __shfl_xor_sync(0xffffffffu, cy_, o), s2 = __shfl_xor_sync(0xffffffffu, ry_, o);
+                if (better(w2, s2, vy, ry_)) { vy = w2; cy_ = d2; ry_ = s2; }
+            }
+            sx = cx_ - 16;
+            sy = cy_ - 16;
+            const float zh = __shfl_sync(0xffffffffu, z[2], 2), zv = __shfl_sync(0xffffffffu, z[2], 3);
+            pv = zv > zh ? 1 : 0;
         } else {
             // neighbour-median start (absent neighbours count as (0,0))
             int ax[3], ay[3];
@@ -911,13 +941,14 @@ int wavefront_batch(me_ctx* c, me_proposal* P, const me_frame_desc* d, int n, in
     const size_t smem = (size_t)8 * ((side * side + 31) / 32) * 4 +
                         (size_t)8 * win_rows(max_range) * win_words(max_range) * 4;
     int per_sm = 0;
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(learned_dcds_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   (int)smem);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, learned_dcds_kernel, 256, smem);
+    auto kern = median ? learned_dcds_kernel<false> : learned_dcds_kernel<true>;
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
     if (e == cudaSuccess) {
-        learned_dcds_kernel<<<c->num_sms * std::max(1, std::min(per_sm, 4)), 256, smem, st>>>(P->frames, n, P->order, (int)total,
-                                                              median ? nullptr : zpart, P->p + P_FW, done, counter,
-                                                              starts, c->status, max_range);
+        kern<<<c->num_sms * std::max(1, std::min(per_sm, 4)), 256, smem, st>>>(P->frames, n, P->order, (int)total,
+                                                                             median ? nullptr : zpart, P->p + P_FW,
+                                                                             done, counter, starts, c->status,
+                                                                             max_range);
         e = cudaGetLastError();
     }
     // the host-side tables are reused by the next call: wait for this one
