@@ -149,7 +149,9 @@ int me_estimate_batch_noalloc(const me_frame_desc* descs, int n, int block, int 
 /* A captured batch: the descriptor table is uploaded once and the launch
  * sequence (queue reset + search kernel) is captured in a CUDA graph that
  * me_graph_launch replays.  The frame and output buffers named by `descs`
- * must stay allocated while the graph exists. */
+ * must stay allocated while the graph exists.  Replays of one graph share its
+ * work-queue counters, so they must not overlap on the GPU: replay it on one
+ * stream, or order the streams (distinct graphs may run concurrently). */
 typedef struct me_graph me_graph;
 int me_graph_create(me_ctx* ctx, const me_frame_desc* descs, int n, int block, int algo,
                     me_graph** out);
