@@ -1,0 +1,62 @@
+"""The oracle's pins catch plausible mistakes.  Each case plants one mistake
+in a copy of the oracle's C source -- the step-1 centre losing ties, a switching
+rule swapped, a pattern point on the wrong axis, the displacement's sign,
+revisited points counted, the search window dropped, the full-search tie
+key reordered, the evaluation's distance components swapped, the frame
+border off by one -- and the pin suite (tests/test_oracle.py: Table VII,
+the Sec. III-C-1 counts, brute force, closed forms) must fail on the copy.
+An unmodified copy must pass, so the failures are the mistakes' own."""
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+MUTATIONS = [
+    ("step-1 centre loses ties", "int k = best_of(&s, cx, cy, &first[1], 6, cval, &bx, &by, &bval);",
+     "int k = best_of(&s, cx, cy, &first[1], 6, cval + 1, &bx, &by, &bval);"),
+    ("switching strategy two swapped", "if (k <= 2) pat = 1 - pat;", "if (k > 2) pat = 1 - pat;"),
+    ("HDSP near points on the wrong axis", "{{0, -1}, {0, 1}, {-2, 0}, {2, 0}},",
+     "{{-1, 0}, {1, 0}, {-2, 0}, {2, 0}},"),
+    ("switching strategy one on dx", "int pat = (by == cy) ? PAT_H : PAT_V;",
+     "int pat = (bx == cx) ? PAT_H : PAT_V;"),
+    ("displacement sign", "int b = ref[(long)(by + dy + r) * pitch + (bx + dx + c)];",
+     "int b = ref[(long)(by - dy + r) * pitch + (bx - dx + c)];"),
+    ("revisits counted", "s->nsp += 1;", "s->nsp += 1; } else { s->nsp += 1;"),
+    ("no search window", "return iabs_(dx) <= s->range && iabs_(dy) <= s->range &&", "return 1 &&"),
+    ("full-search tie key reordered", "else if (dy != bdy) better = dy < bdy;",
+     "else if (dx != bdx) better = dx < bdx;"),
+    ("distance components swapped", "double ex = dx - mv_fs[2 * k], ey = dy - mv_fs[2 * k + 1];",
+     "double ex = dx - mv_fs[2 * k + 1], ey = dy - mv_fs[2 * k];"),
+    ("frame border off by one", "if (bx + dx < 0 || bx + dx > w - block) continue;",
+     "if (bx + dx < 0 || bx + dx > w - block - 1) continue;"),
+]
+
+
+def _run_pins(tmp_path, old=None, new=None):
+    for d in ("oracle", "tests", "paper_0806_0689_gb300"):
+        shutil.copytree(os.path.join(ROOT, d), tmp_path / d,
+                        ignore=shutil.ignore_patterns("_build*", "__pycache__", "*.so", "*.o"))
+    if old is not None:
+        src = tmp_path / "oracle" / "me_oracle.c"
+        text = src.read_text()
+        assert text.count(old) == 1, "the mutation's anchor must occur exactly once"
+        src.write_text(text.replace(old, new))
+    return subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                           "tests/test_oracle.py"], cwd=tmp_path, capture_output=True, text=True, timeout=600)
+
+
+def test_unmodified_copy_passes(tmp_path):
+    r = _run_pins(tmp_path)
+    assert r.returncode == 0, r.stdout[-2000:]
+
+
+@pytest.mark.parametrize("name,old,new", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_pins_catch_the_mistake(tmp_path, name, old, new):
+    r = _run_pins(tmp_path, old, new)
+    tail = r.stdout.strip().splitlines()[-1] if r.stdout.strip() else ""
+    # a failed pin, not a build or collection error
+    assert r.returncode == 1 and "failed" in tail, (name, r.stdout[-2000:], r.stderr[-1000:])
