@@ -15,6 +15,7 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
+# (name, anchor, replacement) in me_oracle.c, checked by tests/test_oracle.py
 MUTATIONS = [
     ("step-1 centre loses ties", "int k = best_of(&s, cx, cy, &first[1], 6, cval, &bx, &by, &bval);",
      "int k = best_of(&s, cx, cy, &first[1], 6, cval + 1, &bx, &by, &bval);"),
@@ -36,27 +37,58 @@ MUTATIONS = [
 ]
 
 
-def _run_pins(tmp_path, old=None, new=None):
+# the same for the proposal network's oracle (cnn_oracle.c), checked by
+# tests/test_oracle_learned.py (impulse responses, closed forms of the
+# features and the loss, finite-difference gradients)
+CNN_MUTATIONS = [
+    ("kernel taps transposed", "s += wt[((o * cin + c) * 3 + ky) * 3 + kx] * in[(c * hin + y) * hin + x];",
+     "s += wt[((o * cin + c) * 3 + kx) * 3 + ky] * in[(c * hin + y) * hin + x];"),
+    ("padding dropped in the forward pass",
+     "int y = 2 * i + ky - 1, x = 2 * j + kx - 1;\n"
+     "                            if (y < 0 || y >= hin || x < 0 || x >= hin) continue;\n"
+     "                            s += wt[",
+     "int y = 2 * i + ky, x = 2 * j + kx;\n"
+     "                            if (y < 0 || y >= hin || x < 0 || x >= hin) continue;\n"
+     "                            s += wt["),
+    ("layer-3 ReLU dropped", "memcpy(a->a3, a->z3, sizeof a->z3); relu(a->a3, C * 16);",
+     "memcpy(a->a3, a->z3, sizeof a->z3);"),
+    ("current block scaled wrongly", "v0 = (cur[(long)(py + i - 8) * pitch + (px + j - 8)] - 128.0) / 128.0;",
+     "v0 = (cur[(long)(py + i - 8) * pitch + (px + j - 8)] - 128.0) / 256.0;"),
+    ("neighbour MV scale", "vx = nbr[2 * ((long)ay * nbx + ax)] / 16.0;", "vx = nbr[2 * ((long)ay * nbx + ax)] / 8.0;"),
+]
+
+
+def _run_pins(tmp_path, src_name="me_oracle.c", suite="tests/test_oracle.py", old=None, new=None):
     for d in ("oracle", "tests", "paper_0806_0689_gb300"):
         shutil.copytree(os.path.join(ROOT, d), tmp_path / d,
                         ignore=shutil.ignore_patterns("_build*", "__pycache__", "*.so", "*.o"))
     if old is not None:
-        src = tmp_path / "oracle" / "me_oracle.c"
+        src = tmp_path / "oracle" / src_name
         text = src.read_text()
         assert text.count(old) == 1, "the mutation's anchor must occur exactly once"
         src.write_text(text.replace(old, new))
-    return subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                           "tests/test_oracle.py"], cwd=tmp_path, capture_output=True, text=True, timeout=600)
+    return subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", suite],
+                          cwd=tmp_path, capture_output=True, text=True, timeout=600)
 
 
-def test_unmodified_copy_passes(tmp_path):
-    r = _run_pins(tmp_path)
+def _caught(r):
+    tail = r.stdout.strip().splitlines()[-1] if r.stdout.strip() else ""
+    return r.returncode == 1 and "failed" in tail  # a failed pin, not a build or collection error
+
+
+@pytest.mark.parametrize("suite", ["tests/test_oracle.py", "tests/test_oracle_learned.py"])
+def test_unmodified_copy_passes(tmp_path, suite):
+    r = _run_pins(tmp_path, suite=suite)
     assert r.returncode == 0, r.stdout[-2000:]
 
 
 @pytest.mark.parametrize("name,old,new", MUTATIONS, ids=[m[0] for m in MUTATIONS])
 def test_pins_catch_the_mistake(tmp_path, name, old, new):
-    r = _run_pins(tmp_path, old, new)
-    tail = r.stdout.strip().splitlines()[-1] if r.stdout.strip() else ""
-    # a failed pin, not a build or collection error
-    assert r.returncode == 1 and "failed" in tail, (name, r.stdout[-2000:], r.stderr[-1000:])
+    r = _run_pins(tmp_path, old=old, new=new)
+    assert _caught(r), (name, r.stdout[-2000:], r.stderr[-1000:])
+
+
+@pytest.mark.parametrize("name,old,new", CNN_MUTATIONS, ids=[m[0] for m in CNN_MUTATIONS])
+def test_network_pins_catch_the_mistake(tmp_path, name, old, new):
+    r = _run_pins(tmp_path, "cnn_oracle.c", "tests/test_oracle_learned.py", old, new)
+    assert _caught(r), (name, r.stdout[-2000:], r.stderr[-1000:])
