@@ -5,7 +5,9 @@ revisited points counted, the search window dropped, the full-search tie
 key reordered, the evaluation's distance components swapped, the frame
 border off by one -- and the pin suite (tests/test_oracle.py: Table VII,
 the Sec. III-C-1 counts, brute force, closed forms) must fail on the copy.
-An unmodified copy must pass, so the failures are the mistakes' own."""
+The same is done for the network's oracle and for the host reductions of
+the Sec. II-C statistics.  An unmodified copy must pass each suite, so the
+failures are the mistakes' own."""
 import os
 import shutil
 import subprocess
@@ -58,12 +60,23 @@ CNN_MUTATIONS = [
 ]
 
 
-def _run_pins(tmp_path, src_name="me_oracle.c", suite="tests/test_oracle.py", old=None, new=None):
+# the host reductions of the Sec. II-C statistics (mvp.py), checked by
+# tests/test_mvp_stats.py against the paper's printed Fig. 3 and Tables II-III
+MVP_MUTATIONS = [
+    ("Table II folded transposed", "T[abs(iy - R), abs(ix - R)] += P[iy, ix]", "T[abs(ix - R), abs(iy - R)] += P[iy, ix]"),
+    ("axes swapped", '"Ax": P.sum(axis=0), "Ay": P.sum(axis=1)', '"Ax": P.sum(axis=1), "Ay": P.sum(axis=0)'),
+    ("diamond too small", "if abs(x) + abs(y) <= 2", "if abs(x) + abs(y) <= 1"),
+    ("population deviation", "v.std(ddof=1)", "v.std(ddof=0)"),
+    ("HCSP region missing a point", "(-2, 0), (2, 0))),", "(-2, 0))),"),
+]
+
+
+def _run_pins(tmp_path, src_name="oracle/me_oracle.c", suite="tests/test_oracle.py", old=None, new=None):
     for d in ("oracle", "tests", "paper_0806_0689_gb300"):
         shutil.copytree(os.path.join(ROOT, d), tmp_path / d,
                         ignore=shutil.ignore_patterns("_build*", "__pycache__", "*.so", "*.o"))
     if old is not None:
-        src = tmp_path / "oracle" / src_name
+        src = tmp_path / src_name
         text = src.read_text()
         assert text.count(old) == 1, "the mutation's anchor must occur exactly once"
         src.write_text(text.replace(old, new))
@@ -76,7 +89,7 @@ def _caught(r):
     return r.returncode == 1 and "failed" in tail  # a failed pin, not a build or collection error
 
 
-@pytest.mark.parametrize("suite", ["tests/test_oracle.py", "tests/test_oracle_learned.py"])
+@pytest.mark.parametrize("suite", ["tests/test_oracle.py", "tests/test_oracle_learned.py", "tests/test_mvp_stats.py"])
 def test_unmodified_copy_passes(tmp_path, suite):
     r = _run_pins(tmp_path, suite=suite)
     assert r.returncode == 0, r.stdout[-2000:]
@@ -90,5 +103,11 @@ def test_pins_catch_the_mistake(tmp_path, name, old, new):
 
 @pytest.mark.parametrize("name,old,new", CNN_MUTATIONS, ids=[m[0] for m in CNN_MUTATIONS])
 def test_network_pins_catch_the_mistake(tmp_path, name, old, new):
-    r = _run_pins(tmp_path, "cnn_oracle.c", "tests/test_oracle_learned.py", old, new)
+    r = _run_pins(tmp_path, "oracle/cnn_oracle.c", "tests/test_oracle_learned.py", old, new)
+    assert _caught(r), (name, r.stdout[-2000:], r.stderr[-1000:])
+
+
+@pytest.mark.parametrize("name,old,new", MVP_MUTATIONS, ids=[m[0] for m in MVP_MUTATIONS])
+def test_statistics_pins_catch_the_mistake(tmp_path, name, old, new):
+    r = _run_pins(tmp_path, "paper_0806_0689_gb300/mvp.py", "tests/test_mvp_stats.py", old, new)
     assert _caught(r), (name, r.stdout[-2000:], r.stderr[-1000:])
