@@ -250,3 +250,51 @@ def test_training_gain(ctx):
         assert np.mean(ps_l) > np.mean(ps_d) - 0.05
     finally:
         ctx.me_proposal_free(prop)
+
+
+def test_wavefront_search_mixed_ranges(ctx):
+    """Both start-predicted searches over one batch whose pairs have different
+    ranges (1, 7, 16, 32: the staged windows are sized by the largest): the
+    median-start search against the oracle, the learned-start search against
+    the oracle's search from the same starts; MVs, SADs and counts bit-exact."""
+    pairs = []
+    for (name, seed), R in zip((("cif", 51), ("qcif", 52), ("cif", 53), ("qcif", 54)), (1, 7, 16, 32)):
+        s = synth.workload_sequence(name, 2, seed=seed, scale=(6.0, 3.0), max_motion=min(R, 16))
+        pairs.append((s[1], s[0], R))
+
+    def run(fn):
+        keep, items = [], []
+        for cur, ref, R in pairs:
+            c, r, mv, sad, nsp = _pair(ctx, cur, ref, R, algo=None)
+            keep.append((mv, sad, nsp))
+            items.append((c, r, R, mv, sad, nsp))
+        total = sum(k[0].shape[0] for k in keep)
+        starts = torch.zeros((total, 3), dtype=torch.int16, device="cuda")
+        fn(me.Context.frame_descs(items), starts)
+        torch.cuda.synchronize()
+        ctx.me_check_status()
+        outs = [(mv.cpu().numpy(), sad.cpu().numpy().view(np.uint32), nsp.cpu().numpy().view(np.uint16))
+                for mv, sad, nsp in keep]
+        return outs, starts.cpu().numpy()
+
+    outs, st = run(lambda d, s: ctx.me_estimate_median_batch(d, s))
+    base = 0
+    for (cur, ref, R), (mv, sad, nsp) in zip(pairs, outs):
+        nb = mv.shape[0]
+        m2, s2, n2, st2 = oracle.median_dcds(cur, ref, R)
+        assert np.array_equal(mv, m2) and np.array_equal(sad, s2) and np.array_equal(nsp, n2), R
+        assert np.array_equal(st[base:base + nb], st2), R
+        base += nb
+    prop = ctx.me_proposal_create()
+    try:
+        ctx.me_proposal_set_params(prop, me.proposal_init_params(7))
+        outs, st = run(lambda d, s: ctx.me_estimate_learned_batch(prop, d, s))
+    finally:
+        ctx.me_proposal_free(prop)
+    base = 0
+    for (cur, ref, R), (mv, sad, nsp) in zip(pairs, outs):
+        nb = mv.shape[0]
+        m2, s2, n2 = oracle.dcds_from_starts(cur, ref, 16, R, st[base:base + nb])
+        assert np.array_equal(mv, m2) and np.array_equal(sad, s2) and np.array_equal(nsp, n2), R
+        assert (np.abs(mv) <= R).all()
+        base += nb
