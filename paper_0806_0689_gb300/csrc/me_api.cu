@@ -209,8 +209,6 @@ int ensure_queue(me_ctx* c, void** q, size_t* qcap, size_t entries)
     return ME_OK;
 }
 
-// Fill the device-side table (tiles per frame, TMA maps for DCDS) into
-// `table`; returns the number of tiles, or -1 if a tensor map is rejected.
 // Fused evaluation of a DCDS batch: mv_fs (host array of n device pointers,
 // nullable) and the device sums [n][ME_NSUMS].  d8 (FS only): the 8x8 outputs
 // of the two-size full search.
@@ -220,6 +218,8 @@ struct EvalArgs {
     const me_frame_desc* d8 = nullptr;
 };
 
+// Fill the device-side table (tiles per frame, TMA maps for DCDS) into
+// `table`; returns the number of tiles, or -1 if a tensor map is rejected.
 int build_table(const me_frame_desc* d, int n, int block, const Shape& s, bool fs, FrameDev* table,
                 int* max_range, const EvalArgs* ev = nullptr)
 {
@@ -963,9 +963,13 @@ int me_tune_batch(me_ctx* c, const me_frame_desc* descs, int n, int block, int a
             }
         }
     }
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t ce = cudaEventCreate(&e0);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+    if (ce != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return cuda_fail(c, ce, "cudaEventCreate");
+    }
     float best = 1e30f;
     int bi = -1;
     for (size_t i = 0; i < cands.size(); ++i) {
@@ -1011,9 +1015,13 @@ int me_absdiff_peak(me_ctx* c, int iters, double* out, int n_variants, int* used
     if (!c || !out || n_variants <= 0 || iters <= 0) return ME_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     const int threads = 256, blocks = c->num_sms * 8;
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t ce = cudaEventCreate(&e0);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+    if (ce != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return cuda_fail(c, ce, "cudaEventCreate");
+    }
     for (int v = 0; v < n_variants; ++v) {
         out[v] = 0.0;
         if (v >= me::SAD_NVARIANTS) continue;
@@ -1039,9 +1047,10 @@ int me_absdiff_peak(me_ctx* c, int iters, double* out, int n_variants, int* used
 int me_set_tracing(me_ctx* c, int on)
 {
     if (!c) return ME_ERR_ARG;
-    if (on && !c->trace0) {
-        cudaError_t e = cudaEventCreate(&c->trace0);
-        if (e == cudaSuccess) e = cudaEventCreate(&c->trace1);
+    if (on) {
+        cudaError_t e = cudaSuccess;
+        if (!c->trace0) e = cudaEventCreate(&c->trace0);
+        if (e == cudaSuccess && !c->trace1) e = cudaEventCreate(&c->trace1);
         if (e != cudaSuccess) return cuda_fail(c, e, "cudaEventCreate");
     }
     c->tracing = on ? 1 : 0;
