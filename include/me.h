@@ -282,7 +282,8 @@ int me_proposal_load(me_ctx* ctx, me_proposal* p, const char* path);
 int me_proposal_train_step(me_ctx* ctx, me_proposal* p, const me_frame_desc* descs, int n, float lr,
                            float* loss, float* grad, void* stream);
 /* Logits of every block of one pair (DEVICE float [nb][68]), the neighbour
- * scalars taken from desc->mv (a DEVICE motion field). */
+ * scalars taken from desc->mv (a DEVICE motion field).  Synchronises
+ * `stream`. */
 int me_proposal_logits(me_ctx* ctx, me_proposal* p, const me_frame_desc* desc, float* logits, void* stream);
 /* Learned-start DCDS over n pairs: blocks run in wavefront order so that the
  * left, top and top-right blocks are final first; the head turns their MVs

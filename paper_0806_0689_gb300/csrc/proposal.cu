@@ -853,7 +853,9 @@ int me_proposal_logits(me_ctx* c, me_proposal* P, const me_frame_desc* d, float*
             e = cudaMemcpyAsync(logits + s0 * NLOGIT, w.logits, sizeof(float) * ns * NLOGIT, cudaMemcpyDeviceToDevice, st);
         if (e != cudaSuccess) return cuda_fail(c, e, "me_proposal_logits");
     }
-    return ME_OK;
+    // the frame table and workspace are rewritten by the next call on this proposal
+    const cudaError_t e = cudaStreamSynchronize(st);
+    return e == cudaSuccess ? ME_OK : cuda_fail(c, e, "me_proposal_logits");
 }
 
 }  // extern "C"
