@@ -244,8 +244,17 @@ def other_workloads(ctx, me, torch, dev, hbm_peak, sad_peak):
     return out
 
 
+def cnn_flop_per_block():
+    """Forward FLOPs of the start proposal per 16x16 block (2 per
+    multiply-add): four 3x3 stride-2 convolutions (2 -> 32 channels at 16x16
+    outputs, then 32 -> 32 at 8x8, 4x4 and 2x2) and the linear head (128
+    conv features + 6 neighbour scalars -> 68 logits)."""
+    conv = sum(2 * o * o * 32 * cin * 9 for o, cin in ((16, 2), (8, 32), (4, 32), (2, 32)))
+    return conv + 2 * (128 + 6) * 68
+
+
 def learned_leg(ctx, me, torch, dev, curs, refs, mv_plain, mv_fs, st_plain, nb, npairs,
-                train_seqs=60, steps=3000):
+                tensor_peak=None, train_seqs=60, steps=3000):
     """Train the start proposal on full-search fields of synthetic CIF pairs
     with the benchmark's motion statistics (seeds from 100000, disjoint from
     the benchmark's), then run the learned-start search on the benchmark
@@ -278,6 +287,24 @@ def learned_leg(ctx, me, torch, dev, curs, refs, mv_plain, mv_fs, st_plain, nb, 
     sad_l = torch.empty((npairs, nb), dtype=torch.int32, device=dev)
     nsp_l = torch.empty((npairs, nb), dtype=torch.int16, device=dev)
     d_l = me.Context.frame_descs((curs[i], refs[i], R_, mv_l[i], sad_l[i], nsp_l[i]) for i in range(npairs))
+    # the CNN forward alone (features, trunk, head) on one pair, timed by the
+    # library's own per-call events, against the sustained bf16 tensor peak
+    logits = torch.empty((nb, me.ME_PROPOSAL_NLOGITS), dtype=torch.float32, device=dev)
+    d_one = me.Context.frame_descs([(curs[0], refs[0], R_, mv_plain[0], sad_l[0], None)])
+    ctx.me_set_tracing(True)
+    tf = []
+    for rep in range(11):
+        ctx.me_proposal_logits(prop, d_one, logits)
+        if rep > 0:
+            tf.append(ctx.me_last_call_ms())
+    ctx.me_set_tracing(False)
+    fwd_ms = float(np.median(tf))
+    fwd_tflops = cnn_flop_per_block() * nb / (fwd_ms * 1e-3) / 1e12
+    cnn_forward = {"blocks": nb, "ms": fwd_ms, "flop_per_block": cnn_flop_per_block(),
+                   "bound": "tensor", "achieved": fwd_tflops, "unit": "TFLOP/s",
+                   "peak": tensor_peak, "frac": fwd_tflops / tensor_peak if tensor_peak else None,
+                   "peak_source": "bf16 sustained of measured" if tensor_peak else None,
+                   "call": "me_proposal_logits on one 1080p pair (median of 10, me_last_call_ms)"}
     ctx.me_estimate_learned_batch(prop, d_l)  # warm-up
     ts = []
     for _ in range(3):
@@ -321,6 +348,7 @@ def learned_leg(ctx, me, torch, dev, curs, refs, mv_plain, mv_fs, st_plain, nb, 
             "distance_to_fs": mean(st, "distance"), "probability_fs": mean(st, "probability"),
             "training": {"pairs": len(items), "steps": steps, "final_loss": float(np.mean(losses[-50:])),
                          "seconds": t_train, "labels": "full-search fields from this library (CIF, seeds >= 100000)"},
+            "cnn_forward": cnn_forward,
             "median_start_control": median}
 
 
@@ -727,7 +755,8 @@ def main():
     if cb is not None:
         line["cpu_baseline"] = cb
     if not a.no_learned:
-        line["learned"] = learned_leg(ctx, me, torch, dev, curs, refs, mv, mv_fs, st_d, nb, npairs)
+        line["learned"] = learned_leg(ctx, me, torch, dev, curs, refs, mv, mv_fs, st_d, nb, npairs,
+                                      tensor_peak=peaks.get("bf16_tflops_sustained"))
     if not a.no_workloads:
         line["other_workloads"] = other_workloads(ctx, me, torch, dev, hbm_peak, sad_peak)
     ctx.me_graph_free(g_step)

@@ -410,13 +410,16 @@ int me_absdiff_peak(me_ctx* ctx, int iters, double* out, int n_variants, int* us
 int me_check_status(me_ctx* ctx, void* stream);
 
 /* Tracing (not in the paper).  me_set_tracing(ctx, 1) makes every launching
- * call of this context in me_api (me_estimate, me_estimate_batch,
+ * call of this context (me_estimate, me_estimate_batch,
  * me_estimate_eval_batch, me_estimate_host_batch, me_fs_dual_batch,
- * me_graph_launch, me_eval_batch, me_mvp_stats) open an NVTX range named after
- * the call around its host part (visible to Nsight tools, free without one)
- * and record CUDA events around its work on its stream.  me_last_call_ms
- * waits for the last traced call's work and returns its device time in ms
- * (ME_ERR_UNSUPPORTED before any traced call).  Off by default. */
+ * me_graph_launch, me_eval_batch, me_mvp_stats, me_proposal_train_step,
+ * me_proposal_logits, me_estimate_learned_batch, me_estimate_median_batch)
+ * open an NVTX range named after the call around its host part (visible to
+ * Nsight tools, free without one) and record CUDA events around its work on
+ * its stream; a call that ends by synchronising its stream records the
+ * closing event before that wait.  me_last_call_ms waits for the last traced
+ * call's work and returns its device time in ms (ME_ERR_UNSUPPORTED before
+ * any traced call).  Off by default. */
 int me_set_tracing(me_ctx* ctx, int on);
 int me_last_call_ms(me_ctx* ctx, float* ms);
 

@@ -17,12 +17,11 @@
 #include <unordered_map>
 #include <vector>
 
-#include <nvtx3/nvToolsExt.h>
-
 using me::EvalDev;
 using me::FrameDev;
 using me::Shape;
 using me::Slot;
+using me::Trace;
 using me::kHeadBytes;
 
 #ifndef ME_DCDS_STAGES
@@ -53,26 +52,6 @@ int cuda_fail(me_ctx* c, cudaError_t e, const char* what)
 }
 
 bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
-
-// Tracing of a public call (me_set_tracing): an NVTX range around its host
-// part and CUDA events around its work on its stream.
-struct Trace {
-    me_ctx* c;
-    cudaStream_t st;
-    Trace(me_ctx* ctx, const char* name, cudaStream_t stream) : c(ctx), st(stream)
-    {
-        if (!c || !c->tracing) return;
-        nvtxRangePushA(name);
-        cudaEventRecord(c->trace0, st);
-    }
-    ~Trace()
-    {
-        if (!c || !c->tracing) return;
-        cudaEventRecord(c->trace1, st);
-        c->traced = true;
-        nvtxRangePop();
-    }
-};
 
 std::string shape_key(int algo, int block, int range, int w, int h)
 {

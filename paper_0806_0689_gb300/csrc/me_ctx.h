@@ -9,6 +9,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace me {
 
 // One reusable upload slot: a device buffer [queue head | descriptor table],
@@ -62,6 +64,38 @@ struct me_ctx {
     cudaEvent_t trace0 = nullptr, trace1 = nullptr;
     bool traced = false;                      // a traced call has recorded its events
 };
+
+namespace me {
+
+// Tracing of a public call (me_set_tracing): an NVTX range around its host
+// part and CUDA events around its work on its stream.  A call that ends by
+// synchronising its stream closes the trace first, so that the events time
+// the device work and not the wait.
+struct Trace {
+    me_ctx* c;
+    cudaStream_t st;
+    bool open = false;
+    Trace(me_ctx* ctx, const char* name, cudaStream_t stream) : c(ctx), st(stream)
+    {
+        if (!c || !c->tracing) return;
+        nvtxRangePushA(name);
+        cudaEventRecord(c->trace0, st);
+        open = true;
+    }
+    void close()
+    {
+        if (!open) return;
+        cudaEventRecord(c->trace1, st);
+        c->traced = true;
+        nvtxRangePop();
+        open = false;
+    }
+    ~Trace() { close(); }
+    Trace(const Trace&) = delete;
+    Trace& operator=(const Trace&) = delete;
+};
+
+}  // namespace me
 
 struct me_graph {
     me_ctx* ctx = nullptr;

@@ -78,6 +78,36 @@ __device__ __forceinline__ int find_frame(const PropFrame* fr, int nframes, long
     return lo;
 }
 
+// The neighbour inputs of block (bx, by): the MVs of its left, top and
+// top-right blocks in the frame's neighbour field, scaled by 1/16; (0,0) for
+// a block outside the frame or without a neighbour field.
+__device__ __forceinline__ void nbr_scalars(const PropFrame& F, int bx, int by, float* __restrict__ out)
+{
+    const int nbdx[3] = {-1, 0, 1}, nbdy[3] = {0, -1, -1};
+    for (int q = 0; q < 3; ++q) {
+        const int ax = bx + nbdx[q], ay = by + nbdy[q];
+        float vx = 0.f, vy = 0.f;
+        if (F.nbr && ax >= 0 && ax < F.nbx && ay >= 0) {
+            const int m = ay * F.nbx + ax;
+            vx = F.nbr[2 * m] * (1.f / 16.f);
+            vy = F.nbr[2 * m + 1] * (1.f / 16.f);
+        }
+        out[2 * q] = vx;
+        out[2 * q + 1] = vy;
+    }
+}
+
+// Inference needs only the neighbour inputs: the fused trunk reads the pixels itself.
+__global__ void mvf_kernel(const PropFrame* __restrict__ fr, int nframes, long s0, int n, float* __restrict__ mvf)
+{
+    for (long s = blockIdx.x * (long)blockDim.x + threadIdx.x; s < n; s += (long)gridDim.x * blockDim.x) {
+        const long gid = s0 + s;
+        const PropFrame& F = fr[find_frame(fr, nframes, gid)];
+        const int k = (int)(gid - F.base);
+        nbr_scalars(F, k % F.nbx, k / F.nbx, mvf + s * 6);
+    }
+}
+
 // features of samples [s0, s0 + n): x NHWC [n][32][32][2] bf16, mvf [n][6], labels [n][3]
 __global__ void feat_kernel(const PropFrame* __restrict__ fr, int nframes, long s0, int n,
                             __nv_bfloat16* __restrict__ x, float* __restrict__ mvf, int* __restrict__ labels)
@@ -99,18 +129,7 @@ __global__ void feat_kernel(const PropFrame* __restrict__ fr, int nframes, long 
         x[idx * 2] = __float2bfloat16_rn(v0);
         x[idx * 2 + 1] = __float2bfloat16_rn(v1);
         if (pix == 0) {
-            const int nbdx[3] = {-1, 0, 1}, nbdy[3] = {0, -1, -1};
-            for (int q = 0; q < 3; ++q) {
-                const int ax = bx + nbdx[q], ay = by + nbdy[q];
-                float vx = 0.f, vy = 0.f;
-                if (F.nbr && ax >= 0 && ax < F.nbx && ay >= 0) {
-                    const int m = ay * F.nbx + ax;
-                    vx = F.nbr[2 * m] * (1.f / 16.f);
-                    vy = F.nbr[2 * m + 1] * (1.f / 16.f);
-                }
-                mvf[s * 6 + 2 * q] = vx;
-                mvf[s * 6 + 2 * q + 1] = vy;
-            }
+            nbr_scalars(F, bx, by, mvf + s * 6);
             if (labels) {
                 int mx = 0, my = 0;
                 if (F.nbr) { mx = F.nbr[2 * k]; my = F.nbr[2 * k + 1]; }
@@ -812,6 +831,7 @@ int me_proposal_train_step(me_ctx* c, me_proposal* P, const me_frame_desc* d, in
     if (rc != ME_OK) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     const int ns = (int)total;
+    me::Trace trace(c, "me_proposal_train_step", st);
     cudaError_t e = cudaMemsetAsync(w.loss_sum, 0, sizeof(double), st);
     if (e == cudaSuccess) {
         feat_kernel<<<nblk((long)ns * 1024), 256, 0, st>>>(P->frames, n, 0, ns, w.x, w.mvf, w.labels);
@@ -828,6 +848,7 @@ int me_proposal_train_step(me_ctx* c, me_proposal* P, const me_frame_desc* d, in
     if (e == cudaSuccess) e = cudaMemcpyAsync(&ls, w.loss_sum, sizeof(double), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess && grad_out)
         e = cudaMemcpyAsync(grad_out, P->g, sizeof(float) * NPARAMS, cudaMemcpyDeviceToHost, st);
+    trace.close();
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(c, e, "me_proposal_train_step");
     if (loss_out) *loss_out = (float)(ls / ns);
@@ -841,12 +862,13 @@ int me_proposal_logits(me_ctx* c, me_proposal* P, const me_frame_desc* d, float*
     int rc = ensure_frames(P, d, 1, true, &total);
     if (rc != ME_OK) return rc;
     cudaStream_t st = (cudaStream_t)stream;
+    me::Trace trace(c, "me_proposal_logits", st);
     for (long s0 = 0; s0 < total; s0 += kChunk) {
         const int ns = (int)std::min<long>(kChunk, total - s0);
         Ws w;
         rc = ensure_ws(P, kChunk, false, &w);
         if (rc != ME_OK) return rc;
-        feat_kernel<<<nblk((long)ns * 1024), 256, 0, st>>>(P->frames, 1, s0, ns, w.x, w.mvf, nullptr);
+        mvf_kernel<<<nblk(ns), 256, 0, st>>>(P->frames, 1, s0, ns, w.mvf);
         cudaError_t e = cudaGetLastError();
         if (e == cudaSuccess) e = forward_infer(P, 1, s0, w, ns, w.a[3], true, st);
         if (e == cudaSuccess)
@@ -854,6 +876,7 @@ int me_proposal_logits(me_ctx* c, me_proposal* P, const me_frame_desc* d, float*
         if (e != cudaSuccess) return cuda_fail(c, e, "me_proposal_logits");
     }
     // the frame table and workspace are rewritten by the next call on this proposal
+    trace.close();
     const cudaError_t e = cudaStreamSynchronize(st);
     return e == cudaSuccess ? ME_OK : cuda_fail(c, e, "me_proposal_logits");
 }
@@ -875,6 +898,7 @@ int wavefront_batch(me_ctx* c, me_proposal* P, const me_frame_desc* d, int n, in
     int rc = ensure_frames(P, d, n, false, &total);
     if (rc != ME_OK) return rc;
     cudaStream_t st = (cudaStream_t)stream;
+    me::Trace trace(c, median ? "me_estimate_median_batch" : "me_estimate_learned_batch", st);
     // buffers after the trunk workspace: conv-4 features, done flags, counter
     Ws w;
     const size_t trunk = ws_layout(nullptr, kChunk, false, &w);
@@ -954,6 +978,7 @@ int wavefront_batch(me_ctx* c, me_proposal* P, const me_frame_desc* d, int n, in
         e = cudaGetLastError();
     }
     // the host-side tables are reused by the next call: wait for this one
+    trace.close();
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     return e == cudaSuccess ? ME_OK : cuda_fail(c, e, "me_estimate_learned_batch");
 }
