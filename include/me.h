@@ -232,7 +232,7 @@ int me_estimate_host_batch(me_ctx* ctx, const me_frame_desc* descs, const int16_
                            int block, int algo, uint64_t* sums, int chunk, void* stream);
 
 /* ---------------------------------------------------------------------- */
-/* Learned start proposal.  Not in the paper: the task adds a small CNN that  */
+/* Learned start proposal.  Not in the paper: libme adds a small CNN that    */
 /* proposes a start point and a horizontal/vertical prior for DCDS, in the    */
 /* spirit of the paper's directional conditional MVP model (Sec. II-C-2,      */
 /* Sec. II-D).  16x16 blocks only.                                            */

@@ -1,7 +1,7 @@
 /*
  * cnn_oracle.c -- TEST INFRASTRUCTURE ONLY.
  *
- * Plain fp64 CPU restatement of the learned start proposal that the task adds
+ * Plain fp64 CPU restatement of the learned start proposal that libme adds
  * to DCDS (it is not in the paper; the paper motivates it through the
  * directional conditional MVP distribution, Sec. II-C-2 and Sec. II-D):
  *

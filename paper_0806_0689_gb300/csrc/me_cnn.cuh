@@ -1,5 +1,5 @@
 // me_cnn.cuh -- the learned start proposal: sizes, parameter layout and the
-// host launchers of cnn.cu.  (Not in the paper; added by the task.)
+// host launchers of cnn.cu.  (Not in the paper: an extension of DCDS.)
 #pragma once
 
 #include <cuda_bf16.h>

@@ -36,7 +36,7 @@ struct __align__(128) FrameDev {
 };
 
 // Encode the two tensor maps of `f` (its pointers, sizes and range must be
-// set).  Host code; returns false if the driver rejects the description.
+// set).  Host code; returns false if the CUDA driver rejects the description.
 bool encode_frame_maps(FrameDev& f);
 
 // Host code, after a table's tile counts and bases are set: mark the table
@@ -172,8 +172,8 @@ FsGeom fs_geom(int block, int max_range, int tx, int k);
 
 // Encode the FS tensor maps of `f`: the reference frame as a 3-D tensor
 // (16 bytes x w/16 chunks x h rows, box 16 x nch x rows) and the current
-// frame as 2-D (box cur_w x block).  Host code; false if the driver rejects
-// the description.
+// frame as 2-D (box cur_w x block).  Host code; false if the CUDA driver
+// rejects the description.
 bool encode_fs_maps(FrameDev& f, int nch, int rows, int cur_w, int block);
 
 cudaError_t launch_eval(const EvalDev* frames, int nframes, int block, int max_blocks, int num_sms,

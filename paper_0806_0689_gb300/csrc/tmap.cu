@@ -1,5 +1,5 @@
 // tmap.cu -- host-side encoding of the TMA tensor maps of a frame pair.
-// The driver entry point is looked up through the runtime, so libme does not
+// The CUDA driver's entry point is looked up through the runtime, so libme does not
 // link libcuda directly.
 #include "me_internal.cuh"
 
