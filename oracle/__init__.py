@@ -18,8 +18,10 @@ Search Algorithm for Fast Block Motion Estimation"):
                      distance and probability relative to FS).
 
 Parity: FS, DCDS and evaluate are pinned by the tests (brute force, Table
-VII, the counts of Sec. III-C-1, Table VI, closed forms).  DCDS^S is
-"parity unpinned": the paper prints only sequence averages for it.
+VII, the counts of Sec. III-C-1, Table VI, closed forms).  The paper prints
+only sequence averages for DCDS^S; it is pinned by examples worked by hand
+from Sec. IV-C on the ideal surface (which fix its side rule, its tie rule
+and what it counts) and by its exact recovery of every interior MV there.
 """
 from __future__ import annotations
 

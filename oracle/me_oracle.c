@@ -19,8 +19,9 @@
  *     (Sec. II-C, Sec. IV); MAD = SAD / N^2, so every argmin is identical.
  *
  * Parity pins (what fixes each function independently of this file) are
- * listed in the test suite; the one function with no pin is marked
- * "parity unpinned" below.
+ * listed in the test suite.  DCDS^S, for which the paper prints only
+ * sequence averages, is pinned by examples worked by hand from Sec. IV-C on
+ * the ideal surface of Sec. III-C-2.
  */
 #include <stdint.h>
 #include <stdlib.h>

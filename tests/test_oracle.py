@@ -49,6 +49,51 @@ def test_table7_all_cells(sx, sy):
             assert nsp == t7[y, x], (mx, my, nsp, t7[y, x])
 
 
+# DCDS^S (Sec. IV-C) on the ideal surface, worked by hand from the text: the
+# last step checks only the middle point on the side of the distant point
+# with the smaller distortion; equal distant points take the negative side, a
+# distant point outside the window counts as +infinity, and a distant point
+# already evaluated is compared without being counted again.
+DCDS_S_WORKED = {
+    (0, 0): ((0, 0), 7),     # the centre wins the HCSP: step 4 is never reached
+    (1, 0): ((1, 0), 10),    # HDSP at (1,0): 3 new; (-1,0) ties (3,0) -> middle (0,0), seen
+    (-1, 0): ((-1, 0), 10),  # (-3,0) ties (1,0) -> middle (-2,0), seen in the HCSP
+    (0, 1): ((0, 1), 10),    # VDSP at (0,1): 3 new; (0,-1) ties (0,3) -> middle (0,0), seen (DCDS 11)
+    (0, -1): ((0, -1), 11),  # (0,-3) ties (0,1) -> middle (0,-2), new
+    (2, 0): ((2, 0), 10),    # (0,0) (from the HCSP) ties (4,0) -> middle (1,0), seen (DCDS 11)
+    (-2, 0): ((-2, 0), 11),  # (-4,0) ties (0,0) -> middle (-3,0), new
+    (3, 0): ((3, 0), 11),    # (2,0) keeps its tie with (4,0); (4,0) is nearer -> middle (3,0), new
+    (0, 2): ((0, 2), 11),    # (0,1) keeps its tie with (0,3); (0,3) is nearer -> middle (0,2), new
+    (7, 0): ((6, 0), 16),    # edge: (8,0) is outside, so (4,0)'s side is taken and (7,0) is never
+                             # checked (DCDS ends on (7,0) with 17)
+}
+
+
+@pytest.mark.parametrize("mv", sorted(DCDS_S_WORKED))
+def test_dcds_s_worked_examples(mv):
+    want_mv, want_nsp = DCDS_S_WORKED[mv]
+    rx, ry, val, nsp = oracle.search(_ideal(*mv), 7, simplified=True)
+    assert (rx, ry) == want_mv and nsp == want_nsp
+    assert val == (rx - mv[0]) ** 2 + (ry - mv[1]) ** 2
+
+
+def test_dcds_s_interior_recovery():
+    """Sec. IV-C's premise holds exactly on the ideal surface (the middle point
+    on the nearer distant point's side is the nearer middle point), so DCDS^S
+    ends on every MV strictly inside the window, as DCDS does (Table VII),
+    with at most one point fewer; at the window's edge it may stop one short."""
+    R = 7
+    for my in range(-R, R + 1):
+        for mx in range(-R, R + 1):
+            s = oracle.search(_ideal(mx, my), R, simplified=True)
+            d = oracle.search(_ideal(mx, my), R)
+            assert 0 <= d[3] - s[3] <= 1, (mx, my, d, s)
+            if abs(mx) < R and abs(my) < R:
+                assert s[:3] == (mx, my, 0), (mx, my, s)
+            else:
+                assert s[2] <= 1, (mx, my, s)
+
+
 def test_halfway_stop_counts():
     """Sec. III-C-1: 7 points for a zero MV, 10 for (+-1,0), 11 for (0,+-1)."""
     want = SCALARS["halfway_counts"]["value"]

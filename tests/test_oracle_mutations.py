@@ -3,8 +3,9 @@ in a copy of the oracle's C source -- the step-1 centre losing ties, a switching
 rule swapped, a pattern point on the wrong axis, the displacement's sign,
 revisited points counted, the search window dropped, the full-search tie
 key reordered, the evaluation's distance components swapped, the frame
-border off by one -- and the pin suite (tests/test_oracle.py: Table VII,
-the Sec. III-C-1 counts, brute force, closed forms) must fail on the copy.
+border off by one, DCDS^S's side reversed or its ties sent the other way --
+and the pin suite (tests/test_oracle.py: Table VII, the Sec. III-C-1 counts,
+the DCDS^S worked examples, brute force, closed forms) must fail on the copy.
 The same is done for the network's oracle and for the host reductions of
 the Sec. II-C statistics.  An unmodified copy must pass each suite, so the
 failures are the mistakes' own."""
@@ -36,6 +37,9 @@ MUTATIONS = [
      "double ex = dx - mv_fs[2 * k + 1], ey = dy - mv_fs[2 * k];"),
     ("frame border off by one", "if (bx + dx < 0 || bx + dx > w - block) continue;",
      "if (bx + dx < 0 || bx + dx > w - block - 1) continue;"),
+    ("DCDS^S side reversed", "int side = (!hm) ? 1 : (!hp) ? 0 : (vp < vm ? 1 : 0);",
+     "int side = (!hm) ? 1 : (!hp) ? 0 : (vp < vm ? 0 : 1);"),
+    ("DCDS^S ties to the positive side", "(vp < vm ? 1 : 0)", "(vp <= vm ? 1 : 0)"),
 ]
 
 
