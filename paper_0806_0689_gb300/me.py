@@ -105,6 +105,16 @@ def load(build_if_missing: bool = True):
             L.me_proposal_logits.argtypes = [P, P, ctypes.POINTER(FrameDesc), P, P]
             L.me_estimate_learned_batch.argtypes = [P, P, ctypes.POINTER(FrameDesc), I, P, P]
             L.me_estimate_host_batch.argtypes = [P, ctypes.POINTER(FrameDesc), P, I, I, I, P, I, P]
+            L.me_estimate_eval_batch.argtypes = [P, ctypes.POINTER(FrameDesc), P, I, I, I, P, P]
+            L.me_graph_create_eval.argtypes = [P, ctypes.POINTER(FrameDesc), P, I, I, I, P, ctypes.POINTER(P)]
+            L.me_fs_dual_batch.argtypes = [P, ctypes.POINTER(FrameDesc), ctypes.POINTER(FrameDesc), I, P]
+            L.me_mvp_stats.argtypes = [P, ctypes.POINTER(FrameDesc), I, I, P, P]
+            L.me_estimate_median_batch.argtypes = [P, ctypes.POINTER(FrameDesc), I, P, P]
+            L.me_inject_wait_timeout.argtypes = [P, I]
+            L.me_set_tracing.argtypes = [P, I]
+            L.me_last_call_ms.argtypes = [P, ctypes.POINTER(ctypes.c_float)]
+            missing = [n for n in EXPORTS if getattr(L, n).argtypes is None]
+            assert not missing, f"argument types not declared for {missing}"
             for n in EXPORTS:
                 if n not in ("me_free", "me_last_error", "me_graph_free", "me_proposal_free"):
                     getattr(L, n).restype = I
@@ -197,7 +207,7 @@ class Context:
         sums: host int64 [n][ME_NSUMS] or None; chunk: pairs per chunk (0:
         the library's choice)."""
         arr = self._fs_ptrs(mv_fs, len(descs))
-        self._check(self.L.me_estimate_host_batch(self.h, descs, ctypes.cast(arr, ctypes.c_void_p) if arr else None,
+        self._check(self.L.me_estimate_host_batch(self.h, descs, arr,
                                                   len(descs), block, ALGOS.get(algo, algo), _ptr(sums), chunk,
                                                   _stream(stream)))
 
