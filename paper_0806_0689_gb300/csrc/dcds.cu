@@ -13,8 +13,8 @@
 //     mbarrier).  With two stages the next tile is fetched while this one is
 //     searched.
 //   * Phase A (step 1 for every block, warp-uniform): a warp takes one tile
-//     row of blocks, B/4 lanes per block, lane w holding 4-pixel column w of
-//     the block.  The five horizontal HCSP points share each reference row
+//     row of blocks per pass (two rows for the search alone), B/4 lanes per
+//     block, lane w holding 4-pixel column w of the block.  The five horizontal HCSP points share each reference row
 //     (three aligned words and four funnel shifts), the two vertical points
 //     reuse the neighbouring rows, so the 7 SADs cost 18 rows of reads.
 //     Blocks whose centre wins are finished (the half-way stop, Sec. III-C);
@@ -41,6 +41,7 @@
 
 #include <algorithm>
 #include <climits>
+#include <type_traits>
 
 namespace me {
 namespace {
@@ -235,88 +236,119 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
         const Region gc = region(curS, (size_t)kTile * kTile, status);       // its current blocks
 
         // ------------------------------------------------ phase A: HCSP
-        for (int row = warp; row < TXB; row += nwarps) {
+        // A warp takes NR tile rows of blocks per pass (the search alone: two
+        // while the tile has at least two rows per warp left): the rows' loads
+        // and SADs are independent, so one pass keeps twice as many in flight.
+        auto hcsp_rows = [&](int row0, int rstep, auto nr_c) {
+            constexpr int NR = decltype(nr_c)::value;
             const int g = lane / GA, w = lane % GA;
-            const int bxg = bx0 + g, byg = by0 + row;
-            const bool exists = bxg < NBX && byg < NBY;
-            uint32_t fw0 = 0u;  // the FS vector, fetched now so its latency hides behind the SADs
-            if (EVAL && mv_fs && exists && w == 0) fw0 = __ldg(mv_fs + (size_t)byg * NBX + bxg);
-            uint32_t cw[B];
-            const uint32_t* cp = reinterpret_cast<const uint32_t*>(curS + (row * B) * kTile + g * B + 4 * w);
+            const int bxg = bx0 + g;
+            uint32_t fw0[NR];  // the FS vectors, fetched now so their latency hides behind the SADs
+            uint32_t cw[NR][B];
+            uint32_t acc[NR][7];
+            uint32_t sq0[NR];  // sum of squared errors at (0,0), EVAL only
+            const uint8_t* base[NR];
 #pragma unroll
-            for (int r = 0; r < B; ++r) cw[r] = ld_word(reinterpret_cast<const uint8_t*>(cp + r * (kTile / 4)), gc);
-            const uint8_t* base = win + (row * B + R - 1) * WP + rx + g * B + 4 * w - 4;
-            uint32_t acc[7];
-            uint32_t sq0 = 0u;  // sum of squared errors at (0,0), EVAL only
+            for (int q = 0; q < NR; ++q) {
+                const int row = row0 + q * rstep, byg = by0 + row;
+                fw0[q] = 0u;
+                if (EVAL && mv_fs && bxg < NBX && byg < NBY && w == 0) fw0[q] = __ldg(mv_fs + (size_t)byg * NBX + bxg);
+                const uint32_t* cp = reinterpret_cast<const uint32_t*>(curS + (row * B) * kTile + g * B + 4 * w);
 #pragma unroll
-            for (int k = 0; k < 7; ++k) acc[k] = 0u;
+                for (int r = 0; r < B; ++r)
+                    cw[q][r] = ld_word(reinterpret_cast<const uint8_t*>(cp + r * (kTile / 4)), gc);
+                base[q] = win + (row * B + R - 1) * WP + rx + g * B + 4 * w - 4;
+                sq0[q] = 0u;
+#pragma unroll
+                for (int k = 0; k < 7; ++k) acc[q][k] = 0u;
+            }
 #pragma unroll
             for (int jj = -1; jj <= B; ++jj) {
-                const uint8_t* rp = base + (jj + 1) * WP;
-                const uint32_t b = ld_word(rp + 4, gw);
-                if (jj >= 0 && jj < B) {
-                    const uint32_t a = ld_word(rp, gw), c = ld_word(rp + 8, gw);
-                    if constexpr (EVAL) {
-                        const uint32_t d0 = __vabsdiffu4(b, cw[jj]);
-                        sq0 = __dp4a(d0, d0, sq0);
+#pragma unroll
+                for (int q = 0; q < NR; ++q) {
+                    const uint8_t* rp = base[q] + (jj + 1) * WP;
+                    const uint32_t b = ld_word(rp + 4, gw);
+                    if (jj >= 0 && jj < B) {
+                        const uint32_t a = ld_word(rp, gw), c = ld_word(rp + 8, gw);
+                        if constexpr (EVAL) {
+                            const uint32_t d0 = __vabsdiffu4(b, cw[q][jj]);
+                            sq0[q] = __dp4a(d0, d0, sq0[q]);
+                        }
+                        acc[q][0] = sadacc<V>(b, cw[q][jj], acc[q][0]);
+                        acc[q][1] = sadacc<V>(__funnelshift_r(a, b, 24), cw[q][jj], acc[q][1]);
+                        acc[q][2] = sadacc<V>(__funnelshift_r(b, c, 8), cw[q][jj], acc[q][2]);
+                        acc[q][5] = sadacc<V>(__funnelshift_r(a, b, 16), cw[q][jj], acc[q][5]);
+                        acc[q][6] = sadacc<V>(__funnelshift_r(b, c, 16), cw[q][jj], acc[q][6]);
                     }
-                    acc[0] = sadacc<V>(b, cw[jj], acc[0]);
-                    acc[1] = sadacc<V>(__funnelshift_r(a, b, 24), cw[jj], acc[1]);
-                    acc[2] = sadacc<V>(__funnelshift_r(b, c, 8), cw[jj], acc[2]);
-                    acc[5] = sadacc<V>(__funnelshift_r(a, b, 16), cw[jj], acc[5]);
-                    acc[6] = sadacc<V>(__funnelshift_r(b, c, 16), cw[jj], acc[6]);
+                    if (jj + 1 >= 0 && jj + 1 < B) acc[q][3] = sadacc<V>(b, cw[q][jj + 1], acc[q][3]);  // (0,-1)
+                    if (jj - 1 >= 0 && jj - 1 < B) acc[q][4] = sadacc<V>(b, cw[q][jj - 1], acc[q][4]);  // (0,+1)
                 }
-                if (jj + 1 >= 0 && jj + 1 < B) acc[3] = sadacc<V>(b, cw[jj + 1], acc[3]);  // (0,-1)
-                if (jj - 1 >= 0 && jj - 1 < B) acc[4] = sadacc<V>(b, cw[jj - 1], acc[4]);  // (0,+1)
             }
 #pragma unroll
             for (int o = 1; o < GA; o <<= 1) {
 #pragma unroll
-                for (int k = 0; k < 7; ++k) acc[k] += __shfl_xor_sync(FULL, acc[k], o);
-                if constexpr (EVAL) sq0 += __shfl_xor_sync(FULL, sq0, o);
-            }
-            const int px = bxg * B, py = byg * B;
-            unsigned vmask = 0x7fu;  // all 7 HCSP points inside the window and the frame
-            if (R < 2 || px < 2 || px > W - B - 2 || py < 1 || py > H - B - 1) {
-                vmask = 0;
+                for (int q = 0; q < NR; ++q) {
 #pragma unroll
-                for (int k = 0; k < 7; ++k) {
-                    int ox, oy;
-                    decode(kHcsp, k, ox, oy);
-                    const bool v = abs(ox) <= R && abs(oy) <= R && px + ox >= 0 && px + ox <= W - B &&
-                                   py + oy >= 0 && py + oy <= H - B;
-                    vmask |= (unsigned)v << k;
+                    for (int k = 0; k < 7; ++k) acc[q][k] += __shfl_xor_sync(FULL, acc[q][k], o);
+                    if constexpr (EVAL) sq0[q] += __shfl_xor_sync(FULL, sq0[q], o);
                 }
             }
-            int best = 0;
-            uint32_t bs = acc[0];
 #pragma unroll
-            for (int k = 1; k < 7; ++k)
-                if (((vmask >> k) & 1u) && acc[k] < bs) { best = k; bs = acc[k]; }
-            const bool leader = (w == 0) && exists;
-            if (leader && best == 0) {
-                const size_t blk = (size_t)byg * NBX + bxg;
-                out_mv[blk] = 0u;
-                out_sad[blk] = bs;
-                if (out_nsp) out_nsp[blk] = (uint16_t)__popc(vmask);
-                if constexpr (EVAL)
-                    eval_block(0, 0, bs, sq0, __popc(vmask), out_nsp != nullptr, mv_fs != nullptr, fw0, B * B, esum,
-                               edist);
-            }
-            const bool cont = leader && best != 0;
-            const unsigned bal = __ballot_sync(FULL, cont);
-            if (bal) {
-                const int first = __ffs(bal) - 1;
-                int rbase = 0;
-                if (lane == first) rbase = atomicAdd(&s_ring_n, __popc(bal));
-                rbase = __shfl_sync(FULL, rbase, first);
-                if (cont && index_ok(rbase + __popc(bal & ((1u << lane) - 1u)), NMB, status)) {
-                    const int rank = __popc(bal & ((1u << lane) - 1u));
-                    ring[rbase + rank] = make_uint2((uint32_t)(row * TXB + g) | ((uint32_t)best << 8) |
-                                                        ((uint32_t)__popc(vmask) << 11),
-                                                    bs);
+            for (int q = 0; q < NR; ++q) {
+                const int row = row0 + q * rstep, byg = by0 + row;
+                const bool exists = bxg < NBX && byg < NBY;
+                const int px = bxg * B, py = byg * B;
+                unsigned vmask = 0x7fu;  // all 7 HCSP points inside the window and the frame
+                if (R < 2 || px < 2 || px > W - B - 2 || py < 1 || py > H - B - 1) {
+                    vmask = 0;
+#pragma unroll
+                    for (int k = 0; k < 7; ++k) {
+                        int ox, oy;
+                        decode(kHcsp, k, ox, oy);
+                        const bool v = abs(ox) <= R && abs(oy) <= R && px + ox >= 0 && px + ox <= W - B &&
+                                       py + oy >= 0 && py + oy <= H - B;
+                        vmask |= (unsigned)v << k;
+                    }
+                }
+                int best = 0;
+                uint32_t bs = acc[q][0];
+#pragma unroll
+                for (int k = 1; k < 7; ++k)
+                    if (((vmask >> k) & 1u) && acc[q][k] < bs) { best = k; bs = acc[q][k]; }
+                const bool leader = (w == 0) && exists;
+                if (leader && best == 0) {
+                    const size_t blk = (size_t)byg * NBX + bxg;
+                    out_mv[blk] = 0u;
+                    out_sad[blk] = bs;
+                    if (out_nsp) out_nsp[blk] = (uint16_t)__popc(vmask);
+                    if constexpr (EVAL)
+                        eval_block(0, 0, bs, sq0[q], __popc(vmask), out_nsp != nullptr, mv_fs != nullptr, fw0[q],
+                                   B * B, esum, edist);
+                }
+                const bool cont = leader && best != 0;
+                const unsigned bal = __ballot_sync(FULL, cont);
+                if (bal) {
+                    const int first = __ffs(bal) - 1;
+                    int rbase = 0;
+                    if (lane == first) rbase = atomicAdd(&s_ring_n, __popc(bal));
+                    rbase = __shfl_sync(FULL, rbase, first);
+                    if (cont && index_ok(rbase + __popc(bal & ((1u << lane) - 1u)), NMB, status)) {
+                        const int rank = __popc(bal & ((1u << lane) - 1u));
+                        ring[rbase + rank] = make_uint2((uint32_t)(row * TXB + g) | ((uint32_t)best << 8) |
+                                                            ((uint32_t)__popc(vmask) << 11),
+                                                        bs);
+                    }
                 }
             }
+        };
+        {
+            int row = warp;
+            // two rows per pass measured faster for the search alone, slower with
+            // the evaluation fused (its registers are at the four-CTA limit)
+            if constexpr (!EVAL)
+                for (; row + nwarps < TXB; row += 2 * nwarps)
+                    hcsp_rows(row, nwarps, std::integral_constant<int, 2>{});
+            for (; row < TXB; row += nwarps) hcsp_rows(row, 0, std::integral_constant<int, 1>{});
         }
         __syncthreads();
 
