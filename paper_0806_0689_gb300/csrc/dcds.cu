@@ -146,9 +146,8 @@ __device__ __forceinline__ void eval_block(int dx, int dy, uint32_t sad, uint32_
     if (has_nsp) e[2] += (unsigned)nsp;
     if (has_fs) {
         const int ex = dx - (int)(int16_t)(fw & 0xffffu), ey = dy - (int)(int16_t)(fw >> 16);
-        // most blocks find the FS vector: skip the (slow) fp64 square root for them
         if (ex == 0 && ey == 0) e[3] += 1u;
-        else dist += (unsigned long long)__double2ll_rn(sqrt((double)(ex * ex + ey * ey)) * 16777216.0);
+        else dist += dist_q24(ex, ey);
     }
     e[4] += (unsigned)bb;
 }

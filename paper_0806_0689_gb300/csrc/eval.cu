@@ -97,8 +97,8 @@ __global__ void __launch_bounds__(256) eval_kernel(const EvalDev* __restrict__ f
                 if (fsw) {
                     const uint32_t fw = __ldg(fsw + k);
                     const int ex = dx - (int)(int16_t)(fw & 0xffffu), ey = dy - (int)(int16_t)(fw >> 16);
-                    if (ex == 0 && ey == 0) s_eq += 1;  // no fp64 square root for the common case
-                    else s_dist += (unsigned long long)__double2ll_rn(sqrt((double)(ex * ex + ey * ey)) * 16777216.0);
+                    if (ex == 0 && ey == 0) s_eq += 1;
+                    else s_dist += dist_q24(ex, ey);
                 }
             }
         }

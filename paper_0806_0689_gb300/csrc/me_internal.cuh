@@ -105,6 +105,34 @@ __device__ __forceinline__ uint32_t sadacc(uint32_t a, uint32_t b, uint32_t c)
 // Variant the search kernels are compiled with: the PTX vabsdiff4 with
 // accumulate measured fastest on GB300 (about 77 T byte-absdiffs/s against
 // 68 T for dp4a and 52 T for __vsadu4 plus an add).
+// round(sqrt(n) * 2^24) for 0 < n < 2^14 (the squared length of an MV
+// difference; |dx|, |dy| <= 64 gives n <= 8192), in integer arithmetic: a
+// single-precision estimate, one Newton step on the integer residual
+// N - s^2 with N = n * 2^48, then exact integer corrections (one step at most
+// over the whole range, checked exhaustively), and rounding from the
+// residual: sqrt(N) >= s + 1/2 exactly when N - s^2 > s.  It keeps the
+// GPU's slow double-precision units off the evaluation's path.
+__device__ __forceinline__ unsigned long long sqrt_q24(unsigned n)
+{
+    const long long N = (long long)n << 48;
+    long long s = (long long)(sqrtf((float)n) * 16777216.0f);
+    s += (long long)rintf((float)(N - s * s) / (2.0f * (float)s));
+    if (s * s > N) --s;
+    if (s * s > N) --s;
+    if ((s + 1) * (s + 1) <= N) ++s;
+    if ((s + 1) * (s + 1) <= N) ++s;
+    return (unsigned long long)(s + ((N - s * s > s) ? 1 : 0));
+}
+
+// Q24 length of an MV difference (ex, ey) != (0, 0); differences beyond the
+// search ranges (a caller's out-of-range FS field) take the double path.
+__device__ __forceinline__ unsigned long long dist_q24(int ex, int ey)
+{
+    const unsigned n = (unsigned)(ex * ex + ey * ey);
+    if (n < (1u << 14)) return sqrt_q24(n);
+    return (unsigned long long)__double2ll_rn(sqrt((double)n) * 16777216.0);
+}
+
 #ifndef ME_SAD_VARIANT
 #define ME_SAD_VARIANT 1
 #endif

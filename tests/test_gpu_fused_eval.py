@@ -3,6 +3,8 @@ me_graph_create_eval): the motion field is bit-identical to the plain
 search, the eight sums are bit-identical to me_eval_batch on that field, and
 the six measures equal the oracle's evaluation of the oracle's DCDS field
 (Sec. IV: MAD, MSE, NSP, PSNR, distance and probability against FS)."""
+import math
+
 import numpy as np
 import pytest
 
@@ -18,6 +20,16 @@ def ctx():
     c = me.Context(0)
     yield c
     c.close()
+
+
+SUM_DIST_Q24 = 4  # ME_SUM_DIST_Q24 of include/me.h
+
+
+def _q24(n):
+    """round(sqrt(n) * 2^24), exactly: sqrt(N) >= s + 1/2 iff N - s^2 > s."""
+    big = n << 48
+    s = math.isqrt(big)
+    return s + (1 if big - s * s > s else 0)
 
 
 def _dev(a):
@@ -99,6 +111,10 @@ def test_fused_sums_equal_eval_batch(ctx, B, algo, with_fs, with_nsp, graph):
             assert got[k] == want[k], (i, k)
         assert abs(got["psnr"] - want["psnr"]) < 1e-9
         assert abs(got["distance"] - want["distance"]) < 1e-7
+        if f is not None:  # the distance counter is the exactly rounded Q24 sum
+            e = mv.cpu().numpy().astype(np.int64) - f.cpu().numpy().astype(np.int64)
+            n = (e * e).sum(axis=1)
+            assert int(arr[i][SUM_DIST_Q24]) == sum(_q24(int(v)) for v in n if v), i
 
 
 def test_fused_rejects_fs_and_bad_sums(ctx):
