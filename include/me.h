@@ -142,9 +142,29 @@ int me_estimate_batch(me_ctx* ctx, const me_frame_desc* descs, int n, int block,
  * memory read before the call returns.  algo: ME_ALGO_DCDS or
  * ME_ALGO_DCDS_S (ME_ERR_UNSUPPORTED otherwise).  The launch shape is the
  * library default.  Results are identical to me_estimate_batch.
- * err (nullable) receives a message of at most err_len bytes on failure. */
+ * err (nullable) receives a message of at most err_len bytes on failure.
+ *
+ * The first call on a device also loads every kernel this path launches
+ * (with CUDA's lazy module loading a kernel is otherwise loaded, which may
+ * allocate, at its first launch), so after that first call no later call
+ * allocates, whatever its block size or algo.
+ *
+ * A failure the search detects on the device (a bounded wait that gave up:
+ * the tiles it had not reached keep their old output) is recorded in a
+ * status word inside the same fixed array.  The word accumulates over calls
+ * until me_noalloc_check_status reads and clears it; the call itself has
+ * already returned ME_OK by then. */
 int me_estimate_batch_noalloc(const me_frame_desc* descs, int n, int block, int algo, void* stream,
                               char* err, int err_len);
+
+/* me_noalloc_check_status: the companion of me_estimate_batch_noalloc (no
+ * counterpart in the paper).  Synchronises `stream`, reads the no-allocation
+ * path's status word of the current device with one 4-byte device-to-host
+ * copy, clears it, and returns ME_ERR_TIMEOUT if a bounded device-side wait
+ * of any call since the last check gave up (ME_ERR_CUDA for a refused access
+ * in the bounds-check build), else ME_OK.  Allocates nothing.  err (nullable)
+ * receives a message of at most err_len bytes on failure. */
+int me_noalloc_check_status(void* stream, char* err, int err_len);
 
 /* A captured batch: the descriptor table is uploaded once and the launch
  * sequence (queue reset + search kernel) is captured in a CUDA graph that
@@ -432,7 +452,9 @@ int me_last_call_ms(me_ctx* ctx, float* ms);
  * polls) gives up, records the time-out and exits: the launch writes no
  * output and the next me_check_status returns ME_ERR_TIMEOUT.  Nothing faults,
  * traps or hangs, and the context stays usable: with `on` = 0 the next launch
- * is a normal one.  Returns ME_ERR_ARG for a NULL context. */
+ * is a normal one.  The no-allocation path has no context: ctx = NULL arms
+ * the same hook for every later me_estimate_batch_noalloc call in the
+ * process (its time-out is then reported by me_noalloc_check_status). */
 int me_inject_wait_timeout(me_ctx* ctx, int on);
 
 #ifdef __cplusplus

@@ -683,6 +683,16 @@ int dcds_ctas_per_sm(int block, int max_range, bool simplified, const Shape& s)
                       : (two ? occupancy_t<8, false, 2>(max_range, s) : occupancy_t<8, false, 1>(max_range, s));
 }
 
+cudaError_t dcds_preload()
+{
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, dcds_kernel<16, false, 1, false>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, dcds_kernel<16, true, 1, false>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, dcds_kernel<8, false, 1, false>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, dcds_kernel<8, true, 1, false>);
+    return e;
+}
+
 cudaError_t launch_dcds(const FrameDev* frames, int nframes, int ntiles, int block, int max_range,
                         bool simplified, const Shape& s, int* head, unsigned* status, int num_sms,
                         cudaStream_t st, bool eval)

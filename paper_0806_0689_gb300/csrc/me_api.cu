@@ -1047,7 +1047,11 @@ int me_last_call_ms(me_ctx* c, float* ms)
 
 int me_inject_wait_timeout(me_ctx* c, int on)
 {
-    if (!c) return ME_ERR_ARG;
+    if (!c) {
+        // the no-allocation path has no context: a NULL context arms its hook
+        me::noalloc_inject_wait_timeout(on);
+        return ME_OK;
+    }
     c->inject_wait_timeout = on ? 1 : 0;
     return ME_OK;
 }

@@ -148,6 +148,11 @@ cudaError_t launch_dcds(const FrameDev* frames, int nframes, int ntiles, int blo
                         cudaStream_t st, bool eval = false);
 size_t dcds_smem_bytes(int block, int max_range, const Shape& s);
 int dcds_ctas_per_sm(int block, int max_range, bool simplified, const Shape& s);
+// Load (under lazy module loading) the one-stage search-only DCDS kernels
+// for both block sizes and both variants, without launching them.
+cudaError_t dcds_preload();
+// Failure-detection test hook of me_estimate_batch_noalloc (noalloc.cu).
+void noalloc_inject_wait_timeout(int on);
 
 // Warp-specialised DCDS.  counters: kCounterInts ints, zeroed before every
 // launch.  queue: kQueueHeadWords header words (word 0: epoch), then

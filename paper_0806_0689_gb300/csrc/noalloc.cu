@@ -17,19 +17,26 @@
 // array's name as a device address: the first call on each device, with that
 // device current, asks cudaGetSymbolAddress for the address and keeps it.
 // A small set-up kernel copies the descriptors (passed by value) into the
-// array and clears the counter, then the regular DCDS kernel runs on it.
+// array and clears the counters, then the regular DCDS kernel runs on it.
+//
+// Failures the kernel detects on the device (a bounded copy wait that gave
+// up) are ORed into a status word in the same array.  It keeps accumulating
+// over calls until me_noalloc_check_status reads and clears it.
 #include "me.h"
 #include "me_internal.cuh"
 
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <mutex>
 
 namespace {
 
 constexpr int kHeadBytes = 256;
-constexpr int kChunk = 16;   // descriptors per set-up launch (passed by value)
+constexpr int kStatusOffset = 128;  // bytes into the head: the status word, past the counter words
+constexpr int kChunk = 16;          // descriptors per set-up launch (passed by value)
 constexpr int kMaxDevices = 64;
+static_assert(me::kCounterInts * sizeof(int) <= kStatusOffset, "status word overlaps the counters");
 
 static __device__ __align__(256) unsigned char
     g_static_scratch[kHeadBytes + ME_STATIC_MAX_FRAMES * sizeof(me::FrameDev)];
@@ -38,11 +45,14 @@ struct Chunk {
     me::FrameDev f[kChunk];
 };
 
-__global__ void static_setup_kernel(Chunk c, int first, int count, unsigned char* scratch)
+// inject: the failure-detection test hook (me_inject_wait_timeout with a NULL
+// context) -- the kernel then starves its first copy wait, see dcds.cu.
+__global__ void static_setup_kernel(Chunk c, int first, int count, int inject, unsigned char* scratch)
 {
     me::FrameDev* table = reinterpret_cast<me::FrameDev*>(scratch + kHeadBytes);
     // the queue head starts at zero, and so do the kernel's other counter words
-    if (first == 0 && threadIdx.x < me::kCounterInts) reinterpret_cast<int*>(scratch)[threadIdx.x] = 0;
+    if (first == 0 && threadIdx.x < me::kCounterInts)
+        reinterpret_cast<int*>(scratch)[threadIdx.x] = (threadIdx.x == me::kCounterInts - 1) ? inject : 0;
     for (int i = threadIdx.x; i < count; i += blockDim.x) table[first + i] = c.f[i];
 }
 
@@ -53,6 +63,7 @@ struct DeviceState {
 DeviceState g_dev[kMaxDevices];
 std::once_flag g_once[kMaxDevices];
 cudaError_t g_setup_err[kMaxDevices];
+std::atomic<int> g_inject{0};
 
 void setup_device(int dev)
 {
@@ -60,9 +71,19 @@ void setup_device(int dev)
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g_dev[dev].num_sms, cudaDevAttrMultiProcessorCount, dev);
+    // With lazy module loading a kernel is loaded (which may allocate device
+    // memory) on its first launch; load every kernel this path launches now.
+    if (e == cudaSuccess) {
+        cudaFuncAttributes a;
+        e = cudaFuncGetAttributes(&a, static_setup_kernel);
+    }
+    if (e == cudaSuccess) e = me::dcds_preload();
     if (e == cudaSuccess) g_dev[dev].scratch = static_cast<unsigned char*>(p);
     g_setup_err[dev] = e;
 }
+
+// The current device's scratch array, set up on first use.
+int device_scratch(unsigned char** out, int* num_sms, char* err, int err_len);
 
 int set_err(char* err, int len, int code, const char* msg)
 {
@@ -70,7 +91,25 @@ int set_err(char* err, int len, int code, const char* msg)
     return code;
 }
 
+int device_scratch(unsigned char** out, int* num_sms, char* err, int err_len)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return set_err(err, err_len, ME_ERR_CUDA, cudaGetErrorString(e));
+    if (dev < 0 || dev >= kMaxDevices) return set_err(err, err_len, ME_ERR_CUDA, "device index out of range");
+    std::call_once(g_once[dev], setup_device, dev);
+    if (g_setup_err[dev] != cudaSuccess || !g_dev[dev].scratch)
+        return set_err(err, err_len, ME_ERR_CUDA, "set-up of the static scratch failed (symbol address or kernel load)");
+    *out = g_dev[dev].scratch;
+    if (num_sms) *num_sms = g_dev[dev].num_sms;
+    return ME_OK;
+}
+
 }  // namespace
+
+namespace me {
+void noalloc_inject_wait_timeout(int on) { g_inject.store(on ? 1 : 0); }
+}  // namespace me
 
 extern "C" int me_estimate_batch_noalloc(const me_frame_desc* d, int n, int block, int algo, void* stream,
                                          char* err, int err_len)
@@ -123,25 +162,44 @@ extern "C" int me_estimate_batch_noalloc(const me_frame_desc* d, int n, int bloc
     }
     me::set_uniform_tiles(table, n);
 
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return set_err(err, err_len, ME_ERR_CUDA, cudaGetErrorString(e));
-    if (dev < 0 || dev >= kMaxDevices) return set_err(err, err_len, ME_ERR_CUDA, "device index out of range");
-    std::call_once(g_once[dev], setup_device, dev);
-    if (g_setup_err[dev] != cudaSuccess || !g_dev[dev].scratch)
-        return set_err(err, err_len, ME_ERR_CUDA, "cudaGetSymbolAddress of the static scratch failed");
+    unsigned char* scratch = nullptr;
+    int num_sms = 0;
+    const int rc = device_scratch(&scratch, &num_sms, err, err_len);
+    if (rc != ME_OK) return rc;
 
     cudaStream_t st = (cudaStream_t)stream;
-    unsigned char* scratch = g_dev[dev].scratch;
+    const int inject = g_inject.load();
+    cudaError_t e = cudaSuccess;
     for (int first = 0; first < n; first += kChunk) {
         const int cnt = std::min(kChunk, n - first);
         for (int i = 0; i < cnt; ++i) chunk.f[i] = table[first + i];
-        static_setup_kernel<<<1, 32, 0, st>>>(chunk, first, cnt, scratch);
+        static_setup_kernel<<<1, 32, 0, st>>>(chunk, first, cnt, inject, scratch);
         e = cudaGetLastError();
         if (e != cudaSuccess) return set_err(err, err_len, ME_ERR_CUDA, cudaGetErrorString(e));
     }
     e = me::launch_dcds(reinterpret_cast<const me::FrameDev*>(scratch + kHeadBytes), n, tiles, block, max_range,
-                        algo == ME_ALGO_DCDS_S, s, reinterpret_cast<int*>(scratch), nullptr, g_dev[dev].num_sms, st);
+                        algo == ME_ALGO_DCDS_S, s, reinterpret_cast<int*>(scratch),
+                        reinterpret_cast<unsigned*>(scratch + kStatusOffset), num_sms, st);
     if (e != cudaSuccess) return set_err(err, err_len, ME_ERR_CUDA, cudaGetErrorString(e));
+    return ME_OK;
+}
+
+extern "C" int me_noalloc_check_status(void* stream, char* err, int err_len)
+{
+    if (err && err_len > 0) err[0] = '\0';
+    unsigned char* scratch = nullptr;
+    const int rc = device_scratch(&scratch, nullptr, err, err_len);
+    if (rc != ME_OK) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned v = 0;
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&v, scratch + kStatusOffset, sizeof v, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess && v) e = cudaMemsetAsync(scratch + kStatusOffset, 0, sizeof v, st);
+    if (e == cudaSuccess && v) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return set_err(err, err_len, ME_ERR_CUDA, cudaGetErrorString(e));
+    if (v & me::STATUS_TIMEOUT) return set_err(err, err_len, ME_ERR_TIMEOUT, "a bounded device-side wait gave up");
+    if (v & me::STATUS_BOUNDS) return set_err(err, err_len, ME_ERR_CUDA, "a bounds check failed (ME_CHECK build)");
+    if (v) return set_err(err, err_len, ME_ERR_ARG, "a kernel rejected its input");
     return ME_OK;
 }

@@ -29,7 +29,7 @@ EXPORTS = ["me_init", "me_free", "me_last_error", "me_estimate", "me_estimate_ba
            "me_proposal_train_step", "me_proposal_logits", "me_estimate_learned_batch",
            "me_estimate_eval_batch", "me_graph_create_eval", "me_estimate_median_batch", "me_mvp_stats",
            "me_fs_dual_batch", "me_estimate_host_batch", "me_inject_wait_timeout", "me_proposal_save",
-           "me_proposal_load", "me_set_tracing", "me_last_call_ms"]
+           "me_proposal_load", "me_set_tracing", "me_last_call_ms", "me_noalloc_check_status"]
 ME_PROPOSAL_NPARAMS = 37532
 ME_PROPOSAL_NLOGITS = 68
 
@@ -93,6 +93,7 @@ def load(build_if_missing: bool = True):
             L.me_absdiff_peak.argtypes = [P, I, ctypes.POINTER(ctypes.c_double), I, ctypes.POINTER(I), P]
             L.me_check_status.argtypes = [P, P]
             L.me_estimate_batch_noalloc.argtypes = [ctypes.POINTER(FrameDesc), I, I, I, P, ctypes.c_char_p, I]
+            L.me_noalloc_check_status.argtypes = [P, ctypes.c_char_p, I]
             L.me_proposal_create.argtypes = [P, ctypes.POINTER(P)]
             L.me_proposal_free.argtypes = [P]
             L.me_proposal_free.restype = None

@@ -103,6 +103,18 @@ def test_timeout_in_fused_evaluation(ctx):
     assert bool((sums[:, 5] > 0).all())  # the block counts are in
 
 
-def test_hook_needs_a_context():
+def test_null_context_hook_is_the_noalloc_one(ctx):
+    # a NULL context arms the hook of the context-free no-allocation path
+    # only: a context's own launches stay normal
     L = me.load()
-    assert L.me_inject_wait_timeout(None, 1) == 1
+    assert L.me_inject_wait_timeout(None, 1) == me.ME_OK
+    try:
+        pairs = _pairs()[:2]
+        items = _items(pairs, 16)
+        descs = me.Context.frame_descs(items)
+        ctx.me_estimate_batch(descs, 16, "dcds")
+        torch.cuda.synchronize()
+        ctx.me_check_status()
+        assert _matches_oracle(pairs, items, 16, "dcds")
+    finally:
+        assert L.me_inject_wait_timeout(None, 0) == me.ME_OK
