@@ -104,6 +104,11 @@ const char* me_last_error(const me_ctx* ctx);
  *   DCDS^S (Sec. IV-C): step 4 checks only the middle point on the side of
  *   the distant point with the smaller SAD (negative side on a tie; both
  *   middle points when neither distant point is a candidate).
+ *   DCDS from a learned start (not in the paper): runs
+ *   me_estimate_learned_batch with the context's own proposal (loaded by
+ *   me_proposal_load or _set_params with a NULL proposal, or trained by
+ *   me_proposal_train); ME_ERR_ARG when the context has none.  That call
+ *   synchronises `stream`.
  *   mv, sad: required; nsp: may be NULL. */
 int me_estimate(me_ctx* ctx, const uint8_t* cur, const uint8_t* ref, int w, int h,
                 int block, int range, int algo,
@@ -113,7 +118,8 @@ int me_estimate(me_ctx* ctx, const uint8_t* cur, const uint8_t* ref, int w, int 
  * persistent launch that pulls tiles of blocks from a global work queue.
  * `block` and `algo` apply to all descriptors.  Results are identical to
  * calling me_estimate on each pair.  `descs` is HOST memory, read before the
- * call returns. */
+ * call returns.  algo ME_ALGO_DCDS_LEARNED runs me_estimate_learned_batch
+ * with the context's own proposal, as me_estimate does. */
 int me_estimate_batch(me_ctx* ctx, const me_frame_desc* descs, int n, int block, int algo,
                       void* stream);
 
@@ -255,20 +261,29 @@ int me_estimate_host_batch(me_ctx* ctx, const me_frame_desc* descs, const int16_
 /* Learned start proposal.  Not in the paper: libme adds a small CNN that    */
 /* proposes a start point and a horizontal/vertical prior for DCDS, in the    */
 /* spirit of the paper's directional conditional MVP model (Sec. II-C-2,      */
-/* Sec. II-D).  16x16 blocks only.                                            */
-/*   features: the current block centred in a zero 32x32 canvas and the      */
-/*   co-located 32x32 reference patch (clamped), both (p - 128) / 128, plus   */
-/*   the final MVs of the left, top and top-right blocks divided by 16;       */
+/* Sec. II-D).  One proposal per 16x16 region: a 16x16 block, or the four     */
+/* 8x8 blocks of the region, which share it.                                  */
+/*   features: the current region centred in a zero 32x32 canvas and the     */
+/*   co-located 32x32 reference patch (clamped), both (p - 128) / 128; the    */
+/*   final MVs of the left, top and top-right neighbours of the region's      */
+/*   top-left block (in the grid of the search's block size) and their       */
+/*   component-wise median (an absent neighbour counts as (0,0)), divided by */
+/*   16: 8 scalars;                                                           */
 /*   network: 4 conv 3x3 stride 2 (32 channels, ReLU) then a linear head to  */
 /*   68 logits (dx in [-16,16], dy in [-16,16], H/V).  Convolutions run on    */
 /*   the BF16 tensor cores with FP32 accumulation.                            */
 /*   parameters (host float, this order): conv1.w [32][2][3][3], conv1.b      */
 /*   [32], conv2.w [32][32][3][3], conv2.b, conv3.w, conv3.b, conv4.w,        */
-/*   conv4.b, fc.w [68][134], fc.b [68]; fc inputs are the 128 conv-4         */
-/*   outputs in (channel, y, x) order, then the 6 neighbour scalars.          */
+/*   conv4.b, fc.w [68][136], fc.b [68]; fc inputs are the 128 conv-4         */
+/*   outputs in (channel, y, x) order, then the 8 neighbour scalars.          */
+/* Every me_proposal_* call that takes a proposal also accepts NULL: it then */
+/* names the context's own proposal, which me_estimate and me_estimate_batch */
+/* use for ME_ALGO_DCDS_LEARNED.  The calls that give it weights             */
+/* (_set_params, _load, _train_step, _train) create it on first use; the     */
+/* others return ME_ERR_ARG until it exists.  me_free releases it.           */
 /* ---------------------------------------------------------------------- */
 typedef struct me_proposal me_proposal;
-enum { ME_PROPOSAL_NPARAMS = 37532, ME_PROPOSAL_NLOGITS = 68 };
+enum { ME_PROPOSAL_NPARAMS = 37668, ME_PROPOSAL_NLOGITS = 68 };
 
 /* Create (all parameters zero: the proposal is then the origin with a
  * horizontal prior, which makes the learned search equal to DCDS) / free. */
@@ -281,7 +296,7 @@ int me_proposal_get_params(me_ctx* ctx, me_proposal* p, float* params);
 /* Checkpoint and resume of training (not in the paper).  me_proposal_save
  * synchronises the device and writes the parameters, both Adam moment vectors
  * and the Adam step count to `path`: a 32-byte header (magic "MEPROP\0\1",
- * version 1, ME_PROPOSAL_NPARAMS, ME_PROPOSAL_NLOGITS, step, CRC-32 of the
+ * version 2, ME_PROPOSAL_NPARAMS, ME_PROPOSAL_NLOGITS, step, CRC-32 of the
  * payload, a reserved word; little-endian) followed by three float32 arrays of
  * ME_PROPOSAL_NPARAMS values in parameter order.  It writes `path`.tmp and
  * renames it over `path`, so a crash never leaves a half-written checkpoint.
@@ -301,35 +316,60 @@ int me_proposal_load(me_ctx* ctx, me_proposal* p, const char* path);
  * 65536 blocks per step.  Synchronises `stream`. */
 int me_proposal_train_step(me_ctx* ctx, me_proposal* p, const me_frame_desc* descs, int n, float lr,
                            float* loss, float* grad, void* stream);
+
+/* Training of the proposal, the loop in the library (not in the paper).
+ * Each of `steps` steps draws pairs_per_step distinct pairs of descs (the
+ * first places of a Fisher-Yates shuffle driven by SplitMix64 from `seed`, so
+ * a seed repeats its sequence) and runs me_proposal_train_step on them with
+ * learning rate lr.  descs: HOST array of n pairs whose mv fields are the
+ * DEVICE label fields (e.g. full-search fields, 16x16 blocks).  losses: HOST
+ * float [steps] receiving each step's mean loss, nullable.  Synchronises
+ * `stream` at every step. */
+typedef struct me_train_cfg {
+    const me_frame_desc* descs;
+    int32_t n;
+    int32_t steps;
+    int32_t pairs_per_step;  /* 1..n */
+    float lr;                /* > 0 */
+    uint64_t seed;
+    float* losses;
+    void* stream;
+} me_train_cfg;
+int me_proposal_train(me_ctx* ctx, me_proposal* p, const me_train_cfg* cfg);
 /* Logits of every block of one pair (DEVICE float [nb][68]), the neighbour
  * scalars taken from desc->mv (a DEVICE motion field).  Synchronises
  * `stream`. */
 int me_proposal_logits(me_ctx* ctx, me_proposal* p, const me_frame_desc* desc, float* logits, void* stream);
-/* Learned-start DCDS over n pairs: blocks run in wavefront order so that the
- * left, top and top-right blocks are final first; the head turns their MVs
- * and the block's conv features into a start (argmax of the dx and dy heads,
- * ties to the class nearest 0, clamped to window and frame) and a prior (V
- * when its logit is larger).  The origin and the start are evaluated, the
+/* Learned-start DCDS over n pairs, blocks of `block` (8 or 16) pixels, w and
+ * h multiples of 16.  Regions run in wavefront order so that the neighbours
+ * their proposal reads are final first (16x16: t = bx + 2 by; 8x8: regions by
+ * t = rx + ry, the four blocks of a region together).  The head turns those
+ * MVs, their median and the region's conv features into a start (argmax of
+ * the dx and dy heads, ties to the class nearest 0) and a prior (V when its
+ * logit is larger).  For each block of the region the start is clamped to
+ * the block's window and frame; the origin and the start are evaluated, the
  * better one (the origin on a tie) centres the first pattern (HCSP, or its
  * transpose for a V prior), then DCDS steps 2-4 follow.  NSP counts every
  * distinct point.  Outputs go to descs[i].mv / sad / nsp; starts (DEVICE
- * int16 [total blocks][3] = sx, sy, prior; nullable) records the proposals.
- * Waits between blocks are bounded (ME_ERR_TIMEOUT via me_check_status).
- * Synchronises `stream`. */
-int me_estimate_learned_batch(me_ctx* ctx, me_proposal* p, const me_frame_desc* descs, int n,
+ * int16 [total blocks][3] = sx, sy, prior per search block, clamped;
+ * nullable) records the proposals.  p = NULL uses the context's own
+ * proposal.  Waits between blocks are bounded (ME_ERR_TIMEOUT via
+ * me_check_status).  Synchronises `stream`. */
+int me_estimate_learned_batch(me_ctx* ctx, me_proposal* p, const me_frame_desc* descs, int n, int block,
                               int16_t* starts, void* stream);
 
 /* me_estimate_median_batch: the non-learned control for the learned start
  * (not in the paper).  The same wavefront search as me_estimate_learned_batch
- * (16x16 blocks, left, top and top-right blocks final first), with the start
- * at the component-wise median of those three neighbours' final MVs (an
- * absent neighbour counts as (0,0)), clamped to the window and the frame,
- * and a vertical prior (the VCSP first) when the median's |dy| > |dx|.  The
+ * (the same block sizes, regions and neighbours), with the region's start at
+ * the component-wise median of those three neighbours' final MVs (an absent
+ * neighbour counts as (0,0)) and a vertical prior (the VCSP first) when the
+ * median's |dy| > |dx|; each block clamps it to its window and frame.  The
  * origin and the start are evaluated, the better one (the origin on a tie)
  * centres the first pattern, then DCDS steps 2-4.  Arguments, outputs and
  * errors as for me_estimate_learned_batch; no proposal is needed.  The call
  * returns after the search (it waits on `stream`). */
-int me_estimate_median_batch(me_ctx* ctx, const me_frame_desc* descs, int n, int16_t* starts, void* stream);
+int me_estimate_median_batch(me_ctx* ctx, const me_frame_desc* descs, int n, int block, int16_t* starts,
+                             void* stream);
 
 /* ---------------------------------------------------------------------- */
 /* Evaluation: the six measures of Sec. IV (MAD, MSE, NSP, PSNR, distance  */
@@ -450,7 +490,13 @@ int me_last_call_ms(me_ctx* ctx, float* ms);
  * for 16 bytes more than the copy delivers.  The copies land, the barrier
  * never completes, and each CTA's bounded wait (shortened to a few thousand
  * polls) gives up, records the time-out and exits: the launch writes no
- * output and the next me_check_status returns ME_ERR_TIMEOUT.  Nothing faults,
+ * output and the next me_check_status returns ME_ERR_TIMEOUT.  In the
+ * wavefront searches (me_estimate_learned_batch, me_estimate_median_batch)
+ * the blocks of the first region in wavefront order then never publish their
+ * hand-off words:
+ * the blocks that wait for it give up after a shortened wait (taking that
+ * neighbour as absent), record the time-out and go on, so every block is
+ * written and the next me_check_status returns ME_ERR_TIMEOUT.  Nothing faults,
  * traps or hangs, and the context stays usable: with `on` = 0 the next launch
  * is a normal one.  The no-allocation path has no context: ctx = NULL arms
  * the same hook for every later me_estimate_batch_noalloc call in the

@@ -86,7 +86,7 @@ def _load():
             lib.oracle_dcds_from_starts.argtypes = [P, P, I, I, I, I, I, P, P, P, P]
             lib.oracle_cnn_nparams.restype = I
             lib.oracle_cnn_features.restype = None
-            lib.oracle_cnn_features.argtypes = [P, P, I, I, I, I, I, P, P, P]
+            lib.oracle_cnn_features.argtypes = [P, P, I, I, I, I, I, P, I, P, P]
             lib.oracle_cnn_forward.restype = None
             lib.oracle_cnn_forward.argtypes = [P, P, P, P]
             lib.oracle_cnn_loss_grad.restype = ctypes.c_double
@@ -230,14 +230,15 @@ def cnn_nparams():
     return int(_load().oracle_cnn_nparams())
 
 
-def cnn_features(cur, ref, px, py, nbr=None):
-    """(x [2, 32, 32] float64, mvf [6] float64) of the 16x16 block at (px, py)."""
+def cnn_features(cur, ref, px, py, nbr=None, block=16):
+    """(x [2, 32, 32] float64, mvf [8] float64) of the 16x16 region at (px, py);
+    nbr is the motion field in the grid of `block` (8 or 16) pixels."""
     cur, ref = _frames(cur, ref)
     h, w = cur.shape
     x = np.zeros((2, 32, 32), np.float64)
-    mvf = np.zeros(6, np.float64)
+    mvf = np.zeros(8, np.float64)
     nbr = None if nbr is None else np.ascontiguousarray(nbr, dtype=np.int16)
-    _load().oracle_cnn_features(_ptr(cur), _ptr(ref), w, h, w, px, py, _ptr(nbr), _ptr(x), _ptr(mvf))
+    _load().oracle_cnn_features(_ptr(cur), _ptr(ref), w, h, w, px, py, _ptr(nbr), block, _ptr(x), _ptr(mvf))
     return x, mvf
 
 
@@ -263,28 +264,19 @@ def cnn_loss_grad(params, x, mvf, labels, grad=None):
 
 
 def cnn_start(logits, px, py, w, h, rng, block=16):
-    """Start point and direction prior chosen from logits: the argmax of the dx
-    and dy heads (ties go to the class nearest the centre, checked in the order
-    0, -1, +1, -2, +2, ...), clamped to the window and the frame; vertical
-    prior when the V logit is strictly larger."""
-    def centre_out_argmax(z):
-        best, bv = 0, z[16]
-        for a in range(1, 17):
-            for d in (-a, a):
-                if z[d + 16] > bv:
-                    best, bv = d, z[d + 16]
-        return best
-    sx = centre_out_argmax(logits[:33])
-    sy = centre_out_argmax(logits[33:66])
+    """cnn_raw_start clamped to the window and the frame of the block of
+    `block` pixels at (px, py)."""
+    sx, sy, pv = cnn_raw_start(logits)
     sx = max(max(-rng, -px), min(min(rng, w - block - px), sx))
     sy = max(max(-rng, -py), min(min(rng, h - block - py), sy))
-    return sx, sy, int(logits[67] > logits[66])
+    return sx, sy, pv
 
 
 def median_start(mv, k, nbx, px, py, w, h, rng, block=16):
-    """Start of the non-learned control: the component-wise median of the
-    left, top and top-right final MVs (absent neighbours count as (0,0)),
-    clamped to the window and the frame; vertical prior when |dy| > |dx|."""
+    """Start of the non-learned control for block k (of `block` pixels, at
+    (px, py)): the component-wise median of the left, top and top-right final
+    MVs (absent neighbours count as (0,0)), clamped to the window and the
+    frame; vertical prior when the median's |dy| > |dx|."""
     bx, by = k % nbx, k // nbx
     cand = []
     for ax, ay in ((bx - 1, by), (bx, by - 1), (bx + 1, by - 1)):
@@ -300,31 +292,74 @@ def median_start(mv, k, nbx, px, py, w, h, rng, block=16):
     return sx, sy, pv
 
 
-def median_dcds(cur, ref, rng):
-    """DCDS from the neighbour-median start (16x16 blocks, raster order, so the
-    left, top and top-right neighbours are final first).  Returns
-    (mv, sad, nsp, starts)."""
+def _regions(w, h, block):
+    """The 16x16 regions of a frame in raster order, each with the indices
+    and pixel origins of its blocks (one 16x16 block, or four 8x8 blocks in
+    the order top-left, top-right, bottom-left, bottom-right)."""
+    nbx = w // block
+    per = 16 // block
+    for ry in range(h // 16):
+        for rx in range(w // 16):
+            blocks = []
+            for j in range(per):
+                for i in range(per):
+                    bx, by = rx * per + i, ry * per + j
+                    blocks.append((by * nbx + bx, bx * block, by * block))
+            yield rx * 16, ry * 16, blocks
+
+
+def _search_regions(cur, ref, rng, block, propose):
+    """DCDS of every block from a start shared by the blocks of its 16x16
+    region.  Regions run in raster order, so the left, top and top-right
+    neighbours of a region's top-left block are final before it starts.
+    propose(mv, k0, px, py) returns the region's raw start (sx, sy, prior_v),
+    k0 being the index of its top-left block; every block clamps the start
+    to its own window and frame.  Returns (mv, sad, nsp, starts)."""
     cur, ref = _frames(cur, ref)
     h, w = cur.shape
-    nbx, nby = w // 16, h // 16
-    nb = nbx * nby
+    if w % 16 or h % 16 or block not in (8, 16):
+        raise ValueError("shared-start searches need w, h multiples of 16 and 8x8 or 16x16 blocks")
+    nb = (w // block) * (h // block)
     mv = np.zeros((nb, 2), np.int16)
     sd = np.zeros(nb, np.uint32)
     ns = np.zeros(nb, np.uint16)
     starts = np.zeros((nb, 3), np.int16)
     out = (ctypes.c_int64 * 4)()
     L = _load()
-    for k in range(nb):
-        px, py = (k % nbx) * 16, (k // nbx) * 16
-        starts[k] = median_start(mv, k, nbx, px, py, w, h, rng)
-        rc = L.oracle_dcds_block_from(_ptr(cur), _ptr(ref), w, h, w, 16, rng, px, py, int(starts[k][0]),
-                                      int(starts[k][1]), int(starts[k][2]), ctypes.cast(out, ctypes.c_void_p))
-        if rc:
-            raise MemoryError("oracle_dcds_block_from failed")
-        mv[k] = (out[0], out[1])
-        sd[k] = out[2]
-        ns[k] = out[3]
+    for px, py, blocks in _regions(w, h, block):
+        sx, sy, pv = propose(mv, blocks[0][0], px, py)
+        for k, bx, by in blocks:
+            starts[k] = (max(max(-rng, -bx), min(min(rng, w - block - bx), sx)),
+                         max(max(-rng, -by), min(min(rng, h - block - by), sy)), pv)
+            rc = L.oracle_dcds_block_from(_ptr(cur), _ptr(ref), w, h, w, block, rng, bx, by, int(sx), int(sy),
+                                          int(pv), ctypes.cast(out, ctypes.c_void_p))
+            if rc:
+                raise MemoryError("oracle_dcds_block_from failed")
+            mv[k] = (out[0], out[1])
+            sd[k] = out[2]
+            ns[k] = out[3]
     return mv, sd, ns, starts
+
+
+def median_dcds(cur, ref, rng, block=16):
+    """DCDS from the neighbour-median start: 16x16 blocks each take the median
+    of their own left, top and top-right neighbours; 8x8 blocks share the
+    start of their 16x16 region, the median of the neighbours of its
+    top-left block.  Returns (mv, sad, nsp, starts)."""
+    h, w = np.asarray(cur).shape
+    nbx = w // block
+
+    def propose(mv, k0, px, py):
+        cand = []
+        bx, by = k0 % nbx, k0 // nbx
+        for ax, ay in ((bx - 1, by), (bx, by - 1), (bx + 1, by - 1)):
+            ok = 0 <= ax < nbx and ay >= 0
+            cand.append((int(mv[ay * nbx + ax][0]), int(mv[ay * nbx + ax][1])) if ok else (0, 0))
+        sx = sorted(c[0] for c in cand)[1]
+        sy = sorted(c[1] for c in cand)[1]
+        return sx, sy, int(abs(sy) > abs(sx))
+
+    return _search_regions(cur, ref, rng, block, propose)
 
 
 def mvp_counts(frames, R):
@@ -371,34 +406,39 @@ def mvp_counts(frames, R):
     return out
 
 
-def learned_dcds(cur, ref, rng, params):
-    """Learned-start DCDS of a frame, 16x16 blocks, blocks in raster order (the
-    left, top and top-right neighbours are final before a block starts).
-    Returns (mv, sad, nsp, starts, logits)."""
-    cur, ref = _frames(cur, ref)
-    h, w = cur.shape
-    nbx, nby = w // 16, h // 16
-    nb = nbx * nby
-    mv = np.zeros((nb, 2), np.int16)
-    sd = np.zeros(nb, np.uint32)
-    ns = np.zeros(nb, np.uint16)
-    starts = np.zeros((nb, 3), np.int16)
-    logits = np.zeros((nb, 68), np.float64)
-    out = (ctypes.c_int64 * 4)()
-    L = _load()
-    for k in range(nb):
-        px, py = (k % nbx) * 16, (k // nbx) * 16
-        x, mvf = cnn_features(cur, ref, px, py, mv)
+def cnn_raw_start(logits):
+    """(sx, sy, prior_v) from logits before clamping: the argmax of the dx and
+    dy heads (ties go to the class nearest the centre, checked in the order
+    0, -1, +1, -2, +2, ...); vertical prior when the V logit is strictly
+    larger."""
+    def centre_out_argmax(z):
+        best, bv = 0, z[16]
+        for a in range(1, 17):
+            for d in (-a, a):
+                if z[d + 16] > bv:
+                    best, bv = d, z[d + 16]
+        return best
+    return centre_out_argmax(logits[:33]), centre_out_argmax(logits[33:66]), int(logits[67] > logits[66])
+
+
+def learned_dcds(cur, ref, rng, params, block=16):
+    """Learned-start DCDS of a frame: one proposal per 16x16 region (one
+    16x16 block, or four 8x8 blocks that share it), regions in raster order
+    so that the left, top and top-right neighbours of a region's top-left
+    block are final before it starts.  Returns (mv, sad, nsp, starts,
+    logits), logits per region in raster order."""
+    h, w = np.asarray(cur).shape
+    logits = np.zeros(((w // 16) * (h // 16), 68), np.float64)
+    count = [0]
+
+    def propose(mv, k0, px, py):
+        x, mvf = cnn_features(cur, ref, px, py, mv, block)
         lg = cnn_forward(params, x, mvf)
-        logits[k] = lg
-        starts[k] = cnn_start(lg, px, py, w, h, rng)
-        rc = L.oracle_dcds_block_from(_ptr(cur), _ptr(ref), w, h, w, 16, rng, px, py, int(starts[k][0]),
-                                      int(starts[k][1]), int(starts[k][2]), ctypes.cast(out, ctypes.c_void_p))
-        if rc:
-            raise MemoryError("oracle_dcds_block_from failed")
-        mv[k] = (out[0], out[1])
-        sd[k] = out[2]
-        ns[k] = out[3]
+        logits[count[0]] = lg
+        count[0] += 1
+        return cnn_raw_start(lg)
+
+    mv, sd, ns, starts = _search_regions(cur, ref, rng, block, propose)
     return mv, sd, ns, starts, logits
 
 

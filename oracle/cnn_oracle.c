@@ -5,24 +5,29 @@
  * to DCDS (it is not in the paper; the paper motivates it through the
  * directional conditional MVP distribution, Sec. II-C-2 and Sec. II-D):
  *
- *   features of the 16x16 block at pixel (px, py):
- *     channel 0: the current block, zero-padded and centred in 32x32
+ *   features of the 16x16 region at pixel (px, py) (one 16x16 block, or the
+ *   four 8x8 blocks that share one proposal):
+ *     channel 0: the current region, zero-padded and centred in 32x32
  *                (pixel (i, j) = cur(py + i - 8, px + j - 8) for 8 <= i, j < 24);
  *     channel 1: the co-located 32x32 reference patch, same origin, with
  *                coordinates clamped to the frame;
  *     both scaled as (p - 128) / 128;
- *     6 scalars: the final MVs of the left, top and top-right blocks divided
- *                by 16, zero where the neighbour does not exist;
+ *     6 scalars: the final MVs of the left, top and top-right neighbours of
+ *                the region's top-left block (in the grid of the search's
+ *                block size) divided by 16, zero where the neighbour does not
+ *                exist;
+ *     2 scalars: the component-wise median of those three MVs (an absent
+ *                neighbour counts as (0,0)) divided by 16;
  *   network: 4 convolutions 3x3, stride 2, padding 1, 32 output channels, ReLU
  *            (32x32x2 -> 16x16x32 -> 8x8x32 -> 4x4x32 -> 2x2x32), then a linear
  *            layer over the 128 conv features (order c, y, x) followed by the
- *            6 scalars, giving 68 logits: dx in [-16, 16] (33), dy in
+ *            8 scalars, giving 68 logits: dx in [-16, 16] (33), dy in
  *            [-16, 16] (33), and H/V (2);
  *   loss: the sum of three softmax cross-entropies (dx, dy, H/V).
  *
  * Parameter layout (flat): conv1.w [32][2][3][3], conv1.b [32], conv2.w
  * [32][32][3][3], conv2.b [32], conv3.w, conv3.b, conv4.w, conv4.b,
- * fc.w [68][134], fc.b [68]: 37532 values.
+ * fc.w [68][136], fc.b [68]: 37668 values.
  *
  * Parity: "parity unpinned" with respect to the paper (the paper has no
  * network).  The functions are pinned mathematically by the tests: finite
@@ -37,7 +42,8 @@
 enum {
     C = 32,
     NLOGIT = 68,
-    NFEAT = 134,
+    NFEAT = 136,
+    NSCAL = 8,
     P_W1 = 0, P_B1 = P_W1 + C * 2 * 9,
     P_W2 = P_B1 + C, P_B2 = P_W2 + C * C * 9,
     P_W3 = P_B2 + C, P_B3 = P_W3 + C * C * 9,
@@ -48,11 +54,18 @@ enum {
 
 int oracle_cnn_nparams(void) { return P_TOTAL; }
 
-/* Features of the block at pixel (px, py), 16x16 blocks. x: [2][32][32];
- * mvf: [6]; nbr: the motion field of the frame ([nb][2] int16, the final MVs
- * of already decided blocks; NULL = none available). */
+static int med3(int a, int b, int c)
+{
+    int lo = a < b ? a : b, hi = a < b ? b : a;
+    return c < lo ? lo : (c > hi ? hi : c);
+}
+
+/* Features of the 16x16 region at pixel (px, py). x: [2][32][32]; mvf: [8];
+ * nbr: the motion field of the frame in the grid of `block` (8 or 16) pixels
+ * ([nb][2] int16, the final MVs of already decided blocks; NULL = none
+ * available). */
 void oracle_cnn_features(const uint8_t* cur, const uint8_t* ref, int w, int h, int pitch,
-                         int px, int py, const int16_t* nbr, double* x, double* mvf)
+                         int px, int py, const int16_t* nbr, int block, double* x, double* mvf)
 {
     for (int i = 0; i < 32; ++i) {
         for (int j = 0; j < 32; ++j) {
@@ -66,18 +79,21 @@ void oracle_cnn_features(const uint8_t* cur, const uint8_t* ref, int w, int h, i
             x[1024 + i * 32 + j] = (ref[(long)yy * pitch + xx] - 128.0) / 128.0;
         }
     }
-    int nbx = w / 16, bx = px / 16, by = py / 16;
+    int nbx = w / block, bx = px / block, by = py / block;
     const int nb_dx[3] = {-1, 0, 1}, nb_dy[3] = {0, -1, -1};
+    int mx[3], my[3];
     for (int k = 0; k < 3; ++k) {
         int ax = bx + nb_dx[k], ay = by + nb_dy[k];
-        double vx = 0.0, vy = 0.0;
+        mx[k] = my[k] = 0;
         if (nbr && ax >= 0 && ax < nbx && ay >= 0) {
-            vx = nbr[2 * ((long)ay * nbx + ax)] / 16.0;
-            vy = nbr[2 * ((long)ay * nbx + ax) + 1] / 16.0;
+            mx[k] = nbr[2 * ((long)ay * nbx + ax)];
+            my[k] = nbr[2 * ((long)ay * nbx + ax) + 1];
         }
-        mvf[2 * k] = vx;
-        mvf[2 * k + 1] = vy;
+        mvf[2 * k] = mx[k] / 16.0;
+        mvf[2 * k + 1] = my[k] / 16.0;
     }
+    mvf[6] = med3(mx[0], mx[1], mx[2]) / 16.0;
+    mvf[7] = med3(my[0], my[1], my[2]) / 16.0;
 }
 
 /* 3x3 convolution, stride 2, padding 1: in [cin][hin][hin] -> out [C][hin/2][hin/2]. */
@@ -124,7 +140,7 @@ static void forward(const double* p, const double* x, const double* mvf, acts_t*
     conv_fwd(a->a3, C, 4, p + P_W4, p + P_B4, a->z4);
     memcpy(a->a4, a->z4, sizeof a->z4); relu(a->a4, C * 4);
     for (int i = 0; i < 128; ++i) a->f[i] = a->a4[i];
-    for (int i = 0; i < 6; ++i) a->f[128 + i] = mvf[i];
+    for (int i = 0; i < NSCAL; ++i) a->f[128 + i] = mvf[i];
     for (int o = 0; o < NLOGIT; ++o) {
         double s = p[P_FB + o];
         for (int i = 0; i < NFEAT; ++i) s += p[P_FW + o * NFEAT + i] * a->f[i];

@@ -24,7 +24,9 @@ namespace {
 // C[M][N] (fp32) = A[M][K] * B[N][K]^T, A and B bf16 with K contiguous
 // (lda, ldb elements), K a multiple of 32 inside each split.  CTA tile 64x32,
 // 4 warps of 16x32, k-step 32 through shared memory.  gridDim.z splits K;
-// with more than one split the partial sums are added atomically into C.
+// with more than one split, split z stores its partial product at
+// C + z * M * ldc and a second kernel sums the splits in order (no atomics:
+// the result does not depend on scheduling).
 constexpr int GM = 64, GN = 32, GK = 32, GKP = 40;  // GKP: padded smem row (bank spread)
 
 __device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, const uint32_t* b)
@@ -103,8 +105,8 @@ __global__ void __launch_bounds__(128) gemm_kernel(const __nv_bfloat16* __restri
                 const float v = acc[j][2 * h + q];
                 if (mode == GEMM_STORE) {
                     Cm[(size_t)r * ldc + col] = v;
-                } else if (mode == GEMM_ATOMIC) {
-                    atomicAdd(&Cm[(size_t)r * ldc + col], v);
+                } else if (mode == GEMM_PARTIAL) {
+                    Cm[(size_t)blockIdx.z * M * ldc + (size_t)r * ldc + col] = v;
                 } else {  // GEMM_BIAS_RELU: bias + ReLU, stored as bf16
                     const float z = v + bias[col];
                     out_bf16[(size_t)r * ldc + col] = __float2bfloat16_rn(z > 0.f ? z : 0.f);
@@ -541,9 +543,30 @@ __global__ void transpose_kernel(const __nv_bfloat16* __restrict__ in, int rows,
     }
 }
 
-// dz = dA * (A > 0) as bf16 (rows x 32), and the bias gradient (column sums)
+// out[c] = sum over r in order of p[r * ncols + c]: the fixed-order reduction
+// of partial sums (split-K products, per-CTA column sums)
+__global__ void sum_rows_kernel(const float* __restrict__ p, int nrows, int ncols, float* __restrict__ out)
+{
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncols; c += gridDim.x * blockDim.x) {
+        float t = 0.f;
+        for (int r = 0; r < nrows; ++r) t += p[(size_t)r * ncols + c];
+        out[c] = t;
+    }
+}
+
+__global__ void sum_doubles_kernel(const double* __restrict__ p, int n, double* __restrict__ out)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < n; ++i) t += p[i];
+        *out = t;
+    }
+}
+
+// dz = dA * (A > 0) as bf16 (rows x 32), and this CTA's share of the bias
+// gradient (column sums) in part[blockIdx.x][32]
 __global__ void relu_back_kernel(const float* __restrict__ da, const __nv_bfloat16* __restrict__ a, long rows,
-                                 __nv_bfloat16* __restrict__ dz, float* __restrict__ dbias)
+                                 __nv_bfloat16* __restrict__ dz, float* __restrict__ part_out)
 {
     __shared__ float part[32][33];
     const int c = threadIdx.x & 31, rsub = threadIdx.x >> 5;  // blockDim = 256: 8 rows at a time
@@ -558,7 +581,7 @@ __global__ void relu_back_kernel(const float* __restrict__ da, const __nv_bfloat
     if (rsub == 0) {
         float t = 0.f;
         for (int i = 0; i < 8; ++i) t += part[i][c];
-        atomicAdd(&dbias[c], t);
+        part_out[blockIdx.x * 32 + c] = t;
     }
 }
 
@@ -577,7 +600,7 @@ __global__ void head_fwd_kernel(const __nv_bfloat16* __restrict__ a4, const floa
         float acc = fb[o];
         for (int c = 0; c < 32; ++c)
             for (int p = 0; p < 4; ++p) acc += w[c * 4 + p] * __bfloat162float(a4[s * 128 + p * 32 + c]);
-        for (int q = 0; q < 6; ++q) acc += w[128 + q] * mvf[s * 6 + q];
+        for (int q = 0; q < NSCAL; ++q) acc += w[128 + q] * mvf[s * NSCAL + q];
         logits[i] = acc;
     }
 }
@@ -585,7 +608,7 @@ __global__ void head_fwd_kernel(const __nv_bfloat16* __restrict__ a4, const floa
 // per sample: three softmax cross-entropies (dx 0..32, dy 33..65, H/V 66..67)
 // against labels; dlogits = (softmax - onehot) * scale; loss partial sums
 __global__ void loss_kernel(const float* __restrict__ logits, const int* __restrict__ labels, int n,
-                            float scale, float* __restrict__ dlogits, double* __restrict__ loss_sum)
+                            float scale, float* __restrict__ dlogits, double* __restrict__ loss_part)
 {
     double local = 0.0;
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
@@ -603,7 +626,7 @@ __global__ void loss_kernel(const float* __restrict__ logits, const int* __restr
         }
     }
     for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
-    if ((threadIdx.x & 31) == 0) atomicAdd(loss_sum, local);
+    if ((threadIdx.x & 31) == 0) loss_part[(blockIdx.x * blockDim.x + threadIdx.x) >> 5] = local;
 }
 
 // head backward: gfw[o][i] += sum_s dz[s][o] f[s][i]; gfb[o] += sum_s dz[s][o]
@@ -620,7 +643,7 @@ __global__ void head_wgrad_kernel(const float* __restrict__ dlogits, const __nv_
         float f;
         if (i == NFEAT) f = 1.f;
         else if (i < 128) f = __bfloat162float(a4[(size_t)s * 128 + (i & 3) * 32 + (i >> 2)]);
-        else f = mvf[(size_t)s * 6 + (i - 128)];
+        else f = mvf[(size_t)s * NSCAL + (i - 128)];
         acc += d * f;
     }
     if (i == NFEAT) gfb[o] += acc;
@@ -700,9 +723,25 @@ cudaError_t gemm(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ld
     int kps = (K + splits - 1) / splits;
     kps = (kps + GK - 1) / GK * GK;
     splits = (K + kps - 1) / kps;
-    if (splits > 1 && mode != GEMM_ATOMIC) return cudaErrorInvalidValue;
+    if (splits > 1) return cudaErrorInvalidValue;  // split K through gemm_splitk
     dim3 grid((M + GM - 1) / GM, (N + GN - 1) / GN, splits);
     gemm_kernel<<<grid, 128, 0, st>>>(A, lda, B, ldb, C, ldc, M, N, K, kps, bias, out_bf16, mode);
+    return cudaGetLastError();
+}
+
+cudaError_t gemm_splitk(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, float* C, int M, int N,
+                        int K, int splits, float* partial, cudaStream_t st)
+{
+    if (K % GK) return cudaErrorInvalidValue;
+    splits = std::min(std::max(1, splits), kMaxSplits);
+    int kps = (K + splits - 1) / splits;
+    kps = (kps + GK - 1) / GK * GK;
+    splits = (K + kps - 1) / kps;
+    dim3 grid((M + GM - 1) / GM, (N + GN - 1) / GN, splits);
+    gemm_kernel<<<grid, 128, 0, st>>>(A, lda, B, ldb, partial, N, M, N, K, kps, nullptr, nullptr, GEMM_PARTIAL);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    sum_rows_kernel<<<(M * N + 255) / 256, 256, 0, st>>>(partial, splits, M * N, C);
     return cudaGetLastError();
 }
 
@@ -729,9 +768,13 @@ cudaError_t transpose(const __nv_bfloat16* in, int rows, int ncols, int ld_in, _
 }
 
 cudaError_t relu_back(const float* da, const __nv_bfloat16* a, long rows, __nv_bfloat16* dz, float* dbias,
-                      cudaStream_t st)
+                      float* partial, cudaStream_t st)
 {
-    relu_back_kernel<<<blocks_for(rows, 8, 2048), 256, 0, st>>>(da, a, rows, dz, dbias);
+    const int grid = blocks_for(rows, 8, kReluBackCtas);
+    relu_back_kernel<<<grid, 256, 0, st>>>(da, a, rows, dz, partial);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    sum_rows_kernel<<<1, 32, 0, st>>>(partial, grid, 32, dbias);
     return cudaGetLastError();
 }
 
@@ -766,9 +809,13 @@ cudaError_t head_fwd(const __nv_bfloat16* a4, const float* mvf, int n, const flo
 }
 
 cudaError_t loss(const float* logits, const int* labels, int n, float scale, float* dlogits, double* loss_sum,
-                 cudaStream_t st)
+                 double* partial, cudaStream_t st)
 {
-    loss_kernel<<<blocks_for(n, 256, 1024), 256, 0, st>>>(logits, labels, n, scale, dlogits, loss_sum);
+    const int grid = blocks_for(n, 256, kLossCtas);
+    loss_kernel<<<grid, 256, 0, st>>>(logits, labels, n, scale, dlogits, partial);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    sum_doubles_kernel<<<1, 32, 0, st>>>(partial, grid * 8, loss_sum);
     return cudaGetLastError();
 }
 

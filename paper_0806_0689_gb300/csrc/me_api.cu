@@ -223,9 +223,10 @@ int build_table(const me_frame_desc* d, int n, int block, const Shape& s, bool f
             f.tiles_y = f.nby;
             if (!me::encode_fs_maps(f, g.nch, me::fs_rows(block, f.range, s.k), s.tx * block, block)) return -1;
         } else {
+            const int th = s.kernel == 3 ? me::cross_tile_h() : me::kTile;
             f.tiles_x = (f.w + me::kTile - 1) / me::kTile;
-            f.tiles_y = (f.h + me::kTile - 1) / me::kTile;
-            if (!me::encode_frame_maps(f)) return -1;
+            f.tiles_y = (f.h + th - 1) / th;
+            if (!me::encode_frame_maps(f, th)) return -1;
         }
         if (ev && ev->sums) {
             f.sums = reinterpret_cast<unsigned long long*>(ev->sums) + (size_t)ME_NSUMS * i;
@@ -248,8 +249,10 @@ int build_table(const me_frame_desc* d, int n, int block, const Shape& s, bool f
 int validate_batch(me_ctx* c, const me_frame_desc* d, int n, int block, int algo)
 {
     if (!d || n <= 0) return fail(c, ME_ERR_ARG, "descs must not be NULL and n must be positive");
-    if (algo == ME_ALGO_DCDS_LEARNED) return fail(c, ME_ERR_UNSUPPORTED, "learned start: no proposal weights loaded");
-    if (algo != ME_ALGO_FS && algo != ME_ALGO_DCDS && algo != ME_ALGO_DCDS_S) return fail(c, ME_ERR_ARG, "unknown algo");
+    if (algo != ME_ALGO_FS && algo != ME_ALGO_DCDS && algo != ME_ALGO_DCDS_S && algo != ME_ALGO_DCDS_LEARNED)
+        return fail(c, ME_ERR_ARG, "unknown algo");
+    if (algo == ME_ALGO_DCDS_LEARNED && !c->learned)
+        return fail(c, ME_ERR_ARG, "learned start: no proposal weights loaded into the context (me_proposal_load)");
     for (int i = 0; i < n; ++i) {
         int rc = check_frame(c, d[i].cur, d[i].ref, d[i].w, d[i].h, d[i].pitch, block, d[i].range, d[i].mv,
                              d[i].sad, d[i].nsp);
@@ -272,7 +275,7 @@ cudaError_t launch_search(me_ctx* c, void* dev, void* queue, size_t qcap, int n,
     if (e != cudaSuccess) return e;
     // failure-detection test hook: a non-zero last counter word makes the DCDS
     // tile kernel arm its first copies for bytes that never arrive
-    const bool tile_kernel = algo != ME_ALGO_FS && (s.kernel == 0 || (ev && ev->sums));
+    const bool tile_kernel = algo != ME_ALGO_FS && (s.kernel == 0 || s.kernel == 3 || (ev && ev->sums));
     if (c->inject_wait_timeout && tile_kernel) {
         e = cudaMemsetAsync(head + me::kCounterInts - 1, 1, sizeof(int), st);
         if (e != cudaSuccess) return e;
@@ -281,6 +284,9 @@ cudaError_t launch_search(me_ctx* c, void* dev, void* queue, size_t qcap, int n,
         // the fused evaluation runs in the tile-phase kernel; its sums accumulate from zero
         e = cudaMemsetAsync(ev->sums, 0, sizeof(uint64_t) * ME_NSUMS * (size_t)n, st);
         if (e != cudaSuccess) return e;
+        if (s.kernel == 3)
+            return me::launch_dcds_cross(table, n, ntiles, block, max_range, algo == ME_ALGO_DCDS_S, s, head,
+                                         c->status, c->num_sms, st, true);
         Shape t = s;
         if (t.kernel != 0) t = default_shape(c, algo, block, max_range);
         t.kernel = 0;
@@ -297,6 +303,9 @@ cudaError_t launch_search(me_ctx* c, void* dev, void* queue, size_t qcap, int n,
     if (s.kernel == 2)
         return me::launch_dcds_stream(table, n, ntiles, block, max_range, algo == ME_ALGO_DCDS_S, s, head,
                                       c->status, c->num_sms, st);
+    if (s.kernel == 3)
+        return me::launch_dcds_cross(table, n, ntiles, block, max_range, algo == ME_ALGO_DCDS_S, s, head, c->status,
+                                     c->num_sms, st);
     return me::launch_dcds(table, n, ntiles, block, max_range, algo == ME_ALGO_DCDS_S, s, head, c->status,
                            c->num_sms, st);
 }
@@ -393,6 +402,7 @@ void me_free(me_ctx* c)
     }
     if (c->status) cudaFree(c->status);
     if (c->median_ws) me_proposal_free(c->median_ws);
+    if (c->learned) me_proposal_free(c->learned);
     if (c->trace0) cudaEventDestroy(c->trace0);
     if (c->trace1) cudaEventDestroy(c->trace1);
     me::HostPipe& P = c->pipe;
@@ -419,6 +429,7 @@ int me_estimate(me_ctx* c, const uint8_t* cur, const uint8_t* ref, int w, int h,
     me_frame_desc d{cur, ref, w, h, w, range, mv, sad, nsp};
     int rc = validate_batch(c, &d, 1, block, algo);
     if (rc != ME_OK) return rc;
+    if (algo == ME_ALGO_DCDS_LEARNED) return me_estimate_learned_batch(c, nullptr, &d, 1, block, nullptr, stream);
     return run_batch(c, &d, 1, block, algo, pick_shape(c, algo, block, range, w, h), (cudaStream_t)stream);
 }
 
@@ -428,6 +439,7 @@ int me_estimate_batch(me_ctx* c, const me_frame_desc* descs, int n, int block, i
     Trace trace(c, "me_estimate_batch", (cudaStream_t)stream);
     int rc = validate_batch(c, descs, n, block, algo);
     if (rc != ME_OK) return rc;
+    if (algo == ME_ALGO_DCDS_LEARNED) return me_estimate_learned_batch(c, nullptr, descs, n, block, nullptr, stream);
     int mr = 1, mw = 0, mh = 0;
     for (int i = 0; i < n; ++i) { mr = std::max(mr, descs[i].range); mw = std::max(mw, descs[i].w); mh = std::max(mh, descs[i].h); }
     return run_batch(c, descs, n, block, algo, pick_shape(c, algo, block, mr, mw, mh), (cudaStream_t)stream);
@@ -707,6 +719,8 @@ int me_graph_create(me_ctx* c, const me_frame_desc* descs, int n, int block, int
     if (!c || !out) return ME_ERR_ARG;
     *out = nullptr;
     int rc = validate_batch(c, descs, n, block, algo);
+    if (rc == ME_OK && algo == ME_ALGO_DCDS_LEARNED)
+        rc = fail(c, ME_ERR_UNSUPPORTED, "the learned start is not captured in graphs");
     if (rc != ME_OK) return rc;
     return graph_create(c, descs, n, block, algo, nullptr, out);
 }
@@ -898,6 +912,8 @@ int me_tune_batch(me_ctx* c, const me_frame_desc* descs, int n, int block, int a
 {
     if (!c) return ME_ERR_ARG;
     int rc = validate_batch(c, descs, n, block, algo);
+    if (rc == ME_OK && algo == ME_ALGO_DCDS_LEARNED)
+        rc = fail(c, ME_ERR_UNSUPPORTED, "the learned start has no launch shapes to tune");
     if (rc != ME_OK) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     int mr = 1, mw = 0, mh = 0;
@@ -940,6 +956,13 @@ int me_tune_batch(me_ctx* c, const me_frame_desc* descs, int n, int block, int a
                 s.stages = stages;
                 if (me::dcds_smem_bytes(block, mr, s) <= 220 * 1024) cands.push_back(s);
             }
+        }
+        {
+            Shape s = default_shape(c, algo, block, mr);
+            s.kernel = 3;
+            s.threads = 128;
+            s.stages = 2;
+            if (me::dcds_cross_smem_bytes(block, mr, s) <= 220 * 1024) cands.push_back(s);
         }
     }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -1079,6 +1102,8 @@ int me_estimate_host_batch(me_ctx* c, const me_frame_desc* descs, const int16_t*
     if (!c) return ME_ERR_ARG;
     Trace trace(c, "me_estimate_host_batch", (cudaStream_t)stream);
     int rc = validate_batch(c, descs, n, block, algo);
+    if (rc == ME_OK && algo == ME_ALGO_DCDS_LEARNED)
+        rc = fail(c, ME_ERR_UNSUPPORTED, "host batches run FS, DCDS and DCDS^S");
     if (rc == ME_OK && sums) rc = validate_eval(c, descs, mv_fs, n, algo, sums);
     if (rc != ME_OK) return rc;
     if (chunk < 0) return fail(c, ME_ERR_ARG, "chunk must not be negative");

@@ -58,6 +58,7 @@ struct me_ctx {
     unsigned* status = nullptr;  // device word written by kernels
     unsigned* sink = nullptr;    // microbenchmark sink
     struct me_proposal* median_ws = nullptr;  // wavefront buffers of the neighbour-median start (lazy)
+    struct me_proposal* learned = nullptr;    // the context's own proposal (me_proposal_* with a NULL proposal)
     me::HostPipe pipe;                        // me_estimate_host_batch staging (lazy)
     int inject_wait_timeout = 0;              // failure-detection test hook (me_inject_wait_timeout)
     int tracing = 0;                          // me_set_tracing: NVTX ranges and CUDA events per call

@@ -36,8 +36,9 @@ struct __align__(128) FrameDev {
 };
 
 // Encode the two tensor maps of `f` (its pointers, sizes and range must be
-// set).  Host code; returns false if the CUDA driver rejects the description.
-bool encode_frame_maps(FrameDev& f);
+// set) for tiles of kTile x tile_h pixels.  Host code; returns false if the
+// CUDA driver rejects the description.
+bool encode_frame_maps(FrameDev& f, int tile_h = kTile);
 
 // Host code, after a table's tile counts and bases are set: mark the table
 // uniform when every frame has the same number of tiles, so that the kernels
@@ -67,7 +68,8 @@ struct Shape {
     int ctas_per_sm;   // persistent grid = ctas_per_sm * SM count (0 = occupancy)
     int k;             // FS: candidate rows per thread
     int stages;        // DCDS tile-phase kernel: 1 = load each tile when needed, 2 = prefetch
-    int kernel;        // DCDS: 0 = tile-phase (dcds.cu), 1 = warp-specialised (dcds_ws.cu), 2 = streaming (dcds_stream.cu)
+    int kernel;        // DCDS: 0 = tile-phase (dcds.cu), 1 = warp-specialised (dcds_ws.cu), 2 = streaming (dcds_stream.cu),
+                       //       3 = cross-pass (dcds_cross.cu)
     int a_warps;       // DCDS warp-specialised: warps per CTA that stage tiles and run step 1
 };
 
@@ -148,6 +150,16 @@ cudaError_t launch_dcds(const FrameDev* frames, int nframes, int ntiles, int blo
                         cudaStream_t st, bool eval = false);
 size_t dcds_smem_bytes(int block, int max_range, const Shape& s);
 int dcds_ctas_per_sm(int block, int max_range, bool simplified, const Shape& s);
+// Cross-pass DCDS (dcds_cross.cu): the same search as a per-block state
+// machine over 9-point cross passes, two tile stages of kTile x
+// cross_tile_h() pixels per CTA.  head: kCounterInts ints, zeroed before every
+// launch (the tile counter; the last word is the time-out test hook).
+cudaError_t launch_dcds_cross(const FrameDev* frames, int nframes, int ntiles, int block, int max_range,
+                              bool simplified, const Shape& s, int* head, unsigned* status, int num_sms,
+                              cudaStream_t st, bool eval = false);
+size_t dcds_cross_smem_bytes(int block, int max_range, const Shape& s);
+int cross_tile_h();
+cudaError_t dcds_cross_preload();
 // Load (under lazy module loading) the one-stage search-only DCDS kernels
 // for both block sizes and both variants, without launching them.
 cudaError_t dcds_preload();

@@ -41,11 +41,11 @@ bool encode_2d(CUtensorMap* m, const uint8_t* base, int w, int h, int pitch, int
 
 }  // namespace
 
-bool encode_frame_maps(FrameDev& f)
+bool encode_frame_maps(FrameDev& f, int tile_h)
 {
     const int rx = (f.range + 15) & ~15;
-    return encode_2d(&f.tm_ref, f.ref, f.w, f.h, f.pitch, kTile + 2 * rx, kTile + 2 * f.range) &&
-           encode_2d(&f.tm_cur, f.cur, f.w, f.h, f.pitch, kTile, kTile);
+    return encode_2d(&f.tm_ref, f.ref, f.w, f.h, f.pitch, kTile + 2 * rx, tile_h + 2 * f.range) &&
+           encode_2d(&f.tm_cur, f.cur, f.w, f.h, f.pitch, kTile, tile_h);
 }
 
 bool encode_fs_maps(FrameDev& f, int nch, int rows, int cur_w, int block)

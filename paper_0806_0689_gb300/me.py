@@ -29,8 +29,9 @@ EXPORTS = ["me_init", "me_free", "me_last_error", "me_estimate", "me_estimate_ba
            "me_proposal_train_step", "me_proposal_logits", "me_estimate_learned_batch",
            "me_estimate_eval_batch", "me_graph_create_eval", "me_estimate_median_batch", "me_mvp_stats",
            "me_fs_dual_batch", "me_estimate_host_batch", "me_inject_wait_timeout", "me_proposal_save",
-           "me_proposal_load", "me_set_tracing", "me_last_call_ms", "me_noalloc_check_status"]
-ME_PROPOSAL_NPARAMS = 37532
+           "me_proposal_load", "me_set_tracing", "me_last_call_ms", "me_noalloc_check_status",
+           "me_proposal_train"]
+ME_PROPOSAL_NPARAMS = 37668
 ME_PROPOSAL_NLOGITS = 68
 
 
@@ -50,6 +51,12 @@ class EvalDesc(ctypes.Structure):
     _fields_ = [("cur", ctypes.c_void_p), ("ref", ctypes.c_void_p), ("w", ctypes.c_int32),
                 ("h", ctypes.c_int32), ("pitch", ctypes.c_int32), ("mv", ctypes.c_void_p),
                 ("mv_fs", ctypes.c_void_p), ("nsp", ctypes.c_void_p)]
+
+
+class TrainCfg(ctypes.Structure):
+    _fields_ = [("descs", ctypes.c_void_p), ("n", ctypes.c_int32), ("steps", ctypes.c_int32),
+                ("pairs_per_step", ctypes.c_int32), ("lr", ctypes.c_float), ("seed", ctypes.c_uint64),
+                ("losses", ctypes.c_void_p), ("stream", ctypes.c_void_p)]
 
 
 class Stats(ctypes.Structure):
@@ -104,13 +111,14 @@ def load(build_if_missing: bool = True):
             L.me_proposal_train_step.argtypes = [P, P, ctypes.POINTER(FrameDesc), I, ctypes.c_float,
                                                  ctypes.POINTER(ctypes.c_float), P, P]
             L.me_proposal_logits.argtypes = [P, P, ctypes.POINTER(FrameDesc), P, P]
-            L.me_estimate_learned_batch.argtypes = [P, P, ctypes.POINTER(FrameDesc), I, P, P]
+            L.me_estimate_learned_batch.argtypes = [P, P, ctypes.POINTER(FrameDesc), I, I, P, P]
+            L.me_proposal_train.argtypes = [P, P, ctypes.POINTER(TrainCfg)]
             L.me_estimate_host_batch.argtypes = [P, ctypes.POINTER(FrameDesc), P, I, I, I, P, I, P]
             L.me_estimate_eval_batch.argtypes = [P, ctypes.POINTER(FrameDesc), P, I, I, I, P, P]
             L.me_graph_create_eval.argtypes = [P, ctypes.POINTER(FrameDesc), P, I, I, I, P, ctypes.POINTER(P)]
             L.me_fs_dual_batch.argtypes = [P, ctypes.POINTER(FrameDesc), ctypes.POINTER(FrameDesc), I, P]
             L.me_mvp_stats.argtypes = [P, ctypes.POINTER(FrameDesc), I, I, P, P]
-            L.me_estimate_median_batch.argtypes = [P, ctypes.POINTER(FrameDesc), I, P, P]
+            L.me_estimate_median_batch.argtypes = [P, ctypes.POINTER(FrameDesc), I, I, P, P]
             L.me_inject_wait_timeout.argtypes = [P, I]
             L.me_set_tracing.argtypes = [P, I]
             L.me_last_call_ms.argtypes = [P, ctypes.POINTER(ctypes.c_float)]
@@ -307,8 +315,8 @@ class Context:
     def me_proposal_logits(self, prop, desc, logits, stream=None):
         self._check(self.L.me_proposal_logits(self.h, prop, desc, _ptr(logits), _stream(stream)))
 
-    def me_estimate_learned_batch(self, prop, descs, starts=None, stream=None):
-        self._check(self.L.me_estimate_learned_batch(self.h, prop, descs, len(descs), _ptr(starts),
+    def me_estimate_learned_batch(self, prop, descs, starts=None, stream=None, block=16):
+        self._check(self.L.me_estimate_learned_batch(self.h, prop, descs, len(descs), block, _ptr(starts),
                                                      _stream(stream)))
 
     def me_fs_dual_batch(self, d16, d8, stream=None):
@@ -319,8 +327,9 @@ class Context:
         """Counts of the Sec. II-C statistics; out: device int64 [35 * (2*rng+1)**2]."""
         self._check(self.L.me_mvp_stats(self.h, descs, len(descs), rng, _ptr(out), _stream(stream)))
 
-    def me_estimate_median_batch(self, descs, starts=None, stream=None):
-        self._check(self.L.me_estimate_median_batch(self.h, descs, len(descs), _ptr(starts), _stream(stream)))
+    def me_estimate_median_batch(self, descs, starts=None, stream=None, block=16):
+        self._check(self.L.me_estimate_median_batch(self.h, descs, len(descs), block, _ptr(starts),
+                                                    _stream(stream)))
 
     def me_check_status(self, stream=None):
         self._check(self.L.me_check_status(self.h, _stream(stream)))
@@ -347,22 +356,20 @@ def proposal_init_params(seed=0):
     for cin in (2, 32, 32, 32):
         parts.append(rng.normal(0.0, np.sqrt(2.0 / (9 * cin)), 32 * cin * 9))
         parts.append(np.full(32, 0.01))
-    parts.append(rng.normal(0.0, np.sqrt(1.0 / 134), 68 * 134))
+    parts.append(rng.normal(0.0, np.sqrt(1.0 / 136), 68 * 136))
     parts.append(np.zeros(68))
     p = np.concatenate(parts).astype(np.float32)
     assert p.size == ME_PROPOSAL_NPARAMS
     return p
 
 
-def train_proposal(ctx, prop, descs, steps, lr=2e-3, pairs_per_step=2, seed=0):
-    """Host loop over training steps (each step runs entirely in the library's
-    kernels).  descs: FrameDesc array whose mv fields hold the label fields.
-    Returns the list of step losses."""
-    rng = np.random.default_rng(seed)
-    n = len(descs)
-    losses = []
-    for _ in range(steps):
-        pick = rng.choice(n, size=min(pairs_per_step, n), replace=False)
-        sub = (FrameDesc * len(pick))(*[descs[int(i)] for i in pick])
-        losses.append(ctx.me_proposal_train_step(prop, sub, lr))
-    return losses
+def train_proposal(ctx, prop, descs, steps, lr=2e-3, pairs_per_step=2, seed=0, stream=None):
+    """me_proposal_train: `steps` training steps over pairs drawn from descs
+    (a FrameDesc array whose mv fields hold the label fields); the loop runs in
+    the library.  prop None trains the context's own proposal.  Returns the
+    list of step losses."""
+    losses = np.zeros(max(steps, 1), np.float32)
+    cfg = TrainCfg(ctypes.cast(descs, ctypes.c_void_p).value, len(descs), steps, min(pairs_per_step, len(descs)),
+                   lr, seed, losses.ctypes.data, _stream(stream).value)
+    ctx._check(ctx.L.me_proposal_train(ctx.h, prop, ctypes.byref(cfg)))
+    return losses[:steps].tolist()

@@ -118,3 +118,48 @@ def test_null_context_hook_is_the_noalloc_one(ctx):
         assert _matches_oracle(pairs, items, 16, "dcds")
     finally:
         assert L.me_inject_wait_timeout(None, 0) == me.ME_OK
+
+
+@pytest.mark.parametrize("B,kind", [(16, "median"), (8, "median"), (16, "learned"), (8, "learned")])
+def test_wavefront_wait_timeout_reported_then_exact(ctx, B, kind):
+    """The wavefront searches' neighbour waits: with the hook armed the blocks
+    of the first region in wavefront order never publish their hand-off
+    words, the blocks that wait for them give up after the shortened wait and
+    go on; the call
+    ends within its bound, every block is written, me_check_status reports
+    ME_ERR_TIMEOUT once, and the next call is bit-exact with the oracle."""
+    pairs = _pairs()
+    items = _items(pairs, B)
+    descs = me.Context.frame_descs(items)
+    total = sum(it[3].shape[0] for it in items)
+    starts = torch.zeros((total, 3), dtype=torch.int16, device="cuda")
+    prop = None
+    if kind == "learned":
+        prop = ctx.me_proposal_create()
+        ctx.me_proposal_set_params(prop, me.proposal_init_params(12))
+        run = lambda: ctx.me_estimate_learned_batch(prop, descs, starts, block=B)
+    else:
+        run = lambda: ctx.me_estimate_median_batch(descs, starts, block=B)
+    try:
+        _timed_out(ctx, run)
+        for (_, _, _, mv, sad, nsp) in items:
+            assert bool((mv != -999).any(dim=1).all()) and bool((sad != -1).all())
+        run()
+        torch.cuda.synchronize()
+        ctx.me_check_status()
+        st = starts.cpu().numpy()
+        base = 0
+        for (cur, ref, R), (_, _, _, mv, sad, nsp) in zip(pairs, items):
+            nb = mv.shape[0]
+            if kind == "median":
+                want = oracle.median_dcds(cur, ref, R, block=B)
+                assert np.array_equal(st[base:base + nb], want[3])
+            else:
+                want = oracle.dcds_from_starts(cur, ref, B, R, st[base:base + nb])
+            assert np.array_equal(mv.cpu().numpy(), want[0])
+            assert np.array_equal(sad.cpu().numpy().view(np.uint32), want[1])
+            assert np.array_equal(nsp.cpu().numpy().view(np.uint16), want[2])
+            base += nb
+    finally:
+        if prop is not None:
+            ctx.me_proposal_free(prop)

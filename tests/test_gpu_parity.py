@@ -387,7 +387,9 @@ def test_invalid_arguments_rejected(ctx):
         assert L.me_estimate(h, *a, P(mv), P(sad), P(nsp), s) == me.ME_ERR_ARG, a
         assert len(L.me_last_error(h)) > 0
     assert L.me_estimate(h, P(f), P(f), 64, 64, 16, 7, 1, None, P(sad), P(nsp), s) == me.ME_ERR_ARG
-    assert L.me_estimate(h, P(f), P(f), 64, 64, 16, 7, 3, P(mv), P(sad), P(nsp), s) == me.ME_ERR_UNSUPPORTED
+    # the learned start without weights loaded into the context is an argument error
+    assert L.me_estimate(h, P(f), P(f), 64, 64, 16, 7, 3, P(mv), P(sad), P(nsp), s) == me.ME_ERR_ARG
+    assert b"no proposal" in L.me_last_error(h)
     assert L.me_estimate_batch(h, None, 0, 16, 1, s) == me.ME_ERR_ARG
     ctx.me_check_status()
 
@@ -422,6 +424,7 @@ DCDS_SHAPES = {
     "stream512_s3": "8 8 512 0 3 2 4",
     "stream384_s2": "8 8 384 0 2 2 4",
     "stream128_s3": "8 8 128 0 3 2 4",
+    "cross128": "8 8 128 0 2 3 4",
 }
 
 

@@ -7,13 +7,14 @@ import pytest
 import oracle
 from paper_0806_0689_gb300 import synth
 
-P = 37532
+P = 37668
+NF = 136  # head inputs: 128 conv features, 6 neighbour MV scalars, their 2 median scalars
 # offsets of the parameter tensors in the flat layout
 W1, B1 = 0, 576
 W2, B2 = 608, 608 + 9216
 W3, B3 = B2 + 32, B2 + 32 + 9216
 W4, B4 = B3 + 32, B3 + 32 + 9216
-FW, FB = B4 + 32, B4 + 32 + 68 * 134
+FW, FB = B4 + 32, B4 + 32 + 68 * NF
 
 
 def test_layout():
@@ -73,16 +74,40 @@ def test_features_closed_form():
     assert x[0, 8, 8] == (int(cur[16, 16]) - 128) / 128 and x[0, 0, 0] == 0.0 and x[0, 23, 23] != 0.0
     assert x[0, 24, 24] == 0.0
     assert x[1, 0, 0] == (int(ref[8, 8]) - 128) / 128
-    # left (0,1) -> index 4, top (1,0) -> 1, top-right (2,0) -> 2; scaled by 1/16
-    assert list(mvf) == [8 / 16, 9 / 16, 2 / 16, 3 / 16, 4 / 16, 5 / 16]
+    # left (0,1) -> index 4, top (1,0) -> 1, top-right (2,0) -> 2; then the
+    # component-wise medians med(8, 2, 4) = 4 and med(9, 3, 5) = 5; scaled by 1/16
+    assert list(mvf) == [8 / 16, 9 / 16, 2 / 16, 3 / 16, 4 / 16, 5 / 16, 4 / 16, 5 / 16]
     x2, mvf2 = oracle.cnn_features(cur, ref, 0, 0, nbr)
     assert x2[1, 0, 0] == (int(ref[0, 0]) - 128) / 128  # clamped corner
-    assert list(mvf2) == [0.0] * 6  # no neighbours exist at the top-left block
+    assert list(mvf2) == [0.0] * 8  # no neighbours exist at the top-left block
+    # the median counts an absent neighbour as (0,0): the block at (48, 16)
+    # has no top-right neighbour; left (2,1) -> index 6, top (3,0) -> 3
+    _, mvf3 = oracle.cnn_features(cur, ref, 48, 16, nbr)
+    assert list(mvf3) == [12 / 16, 13 / 16, 6 / 16, 7 / 16, 0.0, 0.0, 6 / 16, 7 / 16]
+
+
+def test_region_features_in_the_8x8_grid():
+    """For 8x8 blocks the network sees the 16x16 region, and its neighbour
+    scalars are the left, top and top-right 8x8 neighbours of the region's
+    top-left block: for the region at (16, 16) in a 64x48 frame (8x8 grid of
+    8 x 6 blocks) that is block (2, 2)'s neighbours (1, 2), (2, 1), (3, 1)."""
+    h, w = 48, 64
+    cur = (np.arange(h * w) % 253).astype(np.uint8).reshape(h, w)
+    ref = (cur // 2).astype(np.uint8)
+    nbr8 = np.zeros((48, 2), np.int16)
+    nbr8[2 * 8 + 1] = (-3, 7)   # left
+    nbr8[1 * 8 + 2] = (10, -1)  # top
+    nbr8[1 * 8 + 3] = (4, 2)    # top-right
+    nbr8[2 * 8 + 3] = (99, 99)  # inside the region: not a neighbour
+    x8, mvf = oracle.cnn_features(cur, ref, 16, 16, nbr8, block=8)
+    x16, _ = oracle.cnn_features(cur, ref, 16, 16, None, block=16)
+    assert np.array_equal(x8, x16)  # the same region pixels
+    assert list(mvf) == [-3 / 16, 7 / 16, 10 / 16, -1 / 16, 4 / 16, 2 / 16, 4 / 16, 2 / 16]
 
 
 def test_uniform_loss():
     x = np.zeros((2, 32, 32))
-    loss, g = oracle.cnn_loss_grad(np.zeros(P), x, np.zeros(6), (3, 20, 1))
+    loss, g = oracle.cnn_loss_grad(np.zeros(P), x, np.zeros(8), (3, 20, 1))
     assert abs(loss - (2 * np.log(33) + np.log(2))) < 1e-12
     # d loss / d bias of the head = softmax - onehot
     assert abs(g[FB + 3] - (1 / 33 - 1)) < 1e-12 and abs(g[FB + 4] - 1 / 33) < 1e-12
@@ -103,19 +128,21 @@ def test_conv_impulse_response(tap):
     for w0 in (W2, W3, W4):
         p[w0 + (0 * 32 + 0) * 9 + 1 * 3 + 1] = 1.0
     feat = 0 * 4 + 1 * 2 + 1  # channel 0, y 1, x 1
-    p[FW + 5 * 134 + feat] = 1.0
+    p[FW + 5 * NF + feat] = 1.0
     x = np.zeros((2, 32, 32))
     x[0, 16 + ky - 1, 16 + kx - 1] = 0.75
-    lg = oracle.cnn_forward(p, x, np.zeros(6))
+    lg = oracle.cnn_forward(p, x, np.zeros(8))
     assert lg[5] == 0.75 and np.count_nonzero(lg) == 1
     x2 = np.zeros((2, 32, 32))
     x2[0, 16, 16 + (1 if (ky, kx) != (1, 2) else 2)] = 0.75  # a pixel the tap does not reach
     if (16 + ky - 1, 16 + kx - 1) != (16, 16 + 1):
-        assert oracle.cnn_forward(p, x2, np.zeros(6))[5] == 0.0
-    # the mv scalars enter after the 128 conv features
+        assert oracle.cnn_forward(p, x2, np.zeros(8))[5] == 0.0
+    # the mv scalars enter after the 128 conv features, the medians last
     p2 = np.zeros(P)
-    p2[FW + 7 * 134 + 128 + 3] = 2.0
-    assert oracle.cnn_forward(p2, x, np.array([0, 0, 0, 0.25, 0, 0]))[7] == 0.5
+    p2[FW + 7 * NF + 128 + 3] = 2.0
+    p2[FW + 9 * NF + 128 + 7] = 3.0
+    lg2 = oracle.cnn_forward(p2, x, np.array([0, 0, 0, 0.25, 0, 0, 0, 0.5]))
+    assert lg2[7] == 0.5 and lg2[9] == 1.5
 
 
 def test_gradient_finite_differences():
@@ -124,12 +151,15 @@ def test_gradient_finite_differences():
     for b0 in (B1, B2, B3, B4):
         p[b0:b0 + 32] = np.abs(p[b0:b0 + 32]) + 0.05  # keep units active
     x = rng.uniform(-1, 1, (2, 32, 32))
-    mvf = rng.uniform(-1, 1, 6)
+    mvf = rng.uniform(-1, 1, 8)
     lab = (7, 25, 0)
     loss, g = oracle.cnn_loss_grad(p, x, mvf, lab)
     idx = np.concatenate([rng.choice(np.arange(a, b), 6, replace=False)
                           for a, b in ((W1, B1), (B1, W2), (W2, B2), (B2, W3), (W3, B3), (W4, B4), (FW, FB), (FB, P))])
-    h = 1e-5
+    # a small step keeps the perturbation from crossing a ReLU kink (a bias
+    # moves every pre-activation of its unit); fp64 rounding of the loss
+    # stays near 1e-9 at this step
+    h = 1e-7
     for i in idx:
         pp, pm = p.copy(), p.copy()
         pp[i] += h
@@ -178,3 +208,79 @@ def test_median_dcds_on_a_global_shift():
             k = by * nbx + bx
             assert tuple(starts[k]) == (2, 0, 0)
             assert tuple(mv[k]) == (2, 0) and sad[k] == 0 and nsp[k] == 7
+
+
+# ---------------------------------------------------------------- 8x8 blocks sharing a region's start
+
+def test_zero_network_reduces_to_dcds_8x8():
+    """All logits equal -> every region proposes (0,0) with a horizontal
+    prior, so each of its four 8x8 blocks runs the paper's DCDS."""
+    seq = synth.workload_sequence("cif", 2, seed=17, max_motion=16, scale=(6.0, 3.0))
+    mv, sd, ns, st, lg = oracle.learned_dcds(seq[1], seq[0], 16, np.zeros(P), block=8)
+    m2, s2, n2 = oracle.dcds(seq[1], seq[0], 8, 16)
+    assert (st == 0).all() and lg.shape == (396, 68)
+    assert np.array_equal(mv, m2) and np.array_equal(sd, s2) and np.array_equal(ns, n2)
+
+
+def _median_following_head(alpha=4.0):
+    """Conv weights zero; the dx logit of class c (displacement d = c - 16) is
+    alpha * (16 d * m_x - d^2 / 2) with m_x = median_x / 16 the head's 7th
+    scalar, i.e. -alpha / 2 * (d - median_x)^2 up to a per-sample constant:
+    its argmax is the median itself for |median| <= 16.  Same for dy; the
+    prior logits favour H."""
+    p = np.zeros(P)
+    for c in range(33):
+        d = c - 16
+        p[FW + c * NF + 128 + 6] = alpha * 16 * d
+        p[FB + c] = -alpha * d * d / 2
+        p[FW + (33 + c) * NF + 128 + 7] = alpha * 16 * d
+        p[FB + 33 + c] = -alpha * d * d / 2
+    p[FB + 66] = 1.0
+    return p
+
+
+@pytest.mark.parametrize("block", [16, 8])
+def test_median_following_network_gives_the_median_start(block):
+    """A hand-set head that outputs the neighbours' median (and an H prior)
+    makes the learned search the search from the median start: the median
+    scalars, the argmax and the sharing of a region's start by its blocks
+    are wired as stated."""
+    seq = synth.workload_sequence("cif", 2, seed=23, max_motion=12, scale=(6.0, 3.0))
+    cur, ref = seq[1], seq[0]
+    mv, sd, ns, st, _ = oracle.learned_dcds(cur, ref, 16, _median_following_head(), block=block)
+    nbx = cur.shape[1] // block
+
+    def propose(m, k0, px, py):
+        bx, by = k0 % nbx, k0 // nbx
+        cand = [(int(m[ay * nbx + ax][0]), int(m[ay * nbx + ax][1])) if 0 <= ax < nbx and ay >= 0 else (0, 0)
+                for ax, ay in ((bx - 1, by), (bx, by - 1), (bx + 1, by - 1))]
+        return sorted(c[0] for c in cand)[1], sorted(c[1] for c in cand)[1], 0
+
+    m2, s2, n2, st2 = oracle._search_regions(cur, ref, 16, block, propose)
+    assert np.array_equal(mv, m2) and np.array_equal(sd, s2) and np.array_equal(ns, n2)
+    assert np.array_equal(st, st2)
+    assert (st[:, :2] != 0).any()  # the test exercises non-zero starts
+
+
+def test_median_start_8x8_global_shift_closed_form():
+    """White noise shifted by (2, 0): in the first row of regions the median
+    of the (partly absent) neighbours is the origin and plain DCDS finds the
+    shift; from the second row on the median of the neighbours of every
+    region's top-left block is (2, 0), and each of the region's four 8x8
+    blocks evaluates the origin, the start and the HCSP around the start
+    without the origin (one of its points): 7 points, MV (2, 0), SAD 0 --
+    for every block whose HCSP around (2, 0) lies inside the frame (not the
+    last block row or column)."""
+    rng = np.random.default_rng(5)
+    cur, ref = synth.shifted_pair(rng, 96, 128, 2, 0)
+    mv, sad, nsp, st = oracle.median_dcds(cur, ref, 7, block=8)
+    nbx, nby = 16, 12
+    m0, _, n0 = oracle.dcds(cur, ref, 8, 7)
+    for bx in range(nbx - 1):
+        assert tuple(st[bx]) == (0, 0, 0)  # region row 0, block row 0
+        assert tuple(mv[bx]) == (2, 0) and nsp[bx] == n0[bx]
+    for by in range(2, nby - 1):
+        for bx in range(nbx - 1):
+            k = by * nbx + bx
+            assert tuple(st[k]) == (2, 0, 0), (bx, by)
+            assert tuple(mv[k]) == (2, 0) and sad[k] == 0 and nsp[k] == 7, (bx, by)

@@ -60,7 +60,10 @@ CNN_MUTATIONS = [
      "memcpy(a->a3, a->z3, sizeof a->z3);"),
     ("current block scaled wrongly", "v0 = (cur[(long)(py + i - 8) * pitch + (px + j - 8)] - 128.0) / 128.0;",
      "v0 = (cur[(long)(py + i - 8) * pitch + (px + j - 8)] - 128.0) / 256.0;"),
-    ("neighbour MV scale", "vx = nbr[2 * ((long)ay * nbx + ax)] / 16.0;", "vx = nbr[2 * ((long)ay * nbx + ax)] / 8.0;"),
+    ("neighbour MV scale", "mvf[2 * k] = mx[k] / 16.0;", "mvf[2 * k] = mx[k] / 8.0;"),
+    ("median axes swapped", "mvf[6] = med3(mx[0], mx[1], mx[2]) / 16.0;", "mvf[6] = med3(my[0], my[1], my[2]) / 16.0;"),
+    ("top-right neighbour one block too far", "const int nb_dx[3] = {-1, 0, 1}, nb_dy[3] = {0, -1, -1};",
+     "const int nb_dx[3] = {-1, 0, 2}, nb_dy[3] = {0, -1, -1};"),
 ]
 
 
