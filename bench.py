@@ -182,6 +182,20 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def clocked(torch, fn, seconds=1.2):
+    """Run fn repeatedly for at least `seconds` (synchronising every few
+    calls) while nvidia-smi samples the clocks; returns the clock record."""
+    clk = Clocks(torch.cuda.current_device())
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        for _ in range(8):
+            fn()
+        torch.cuda.synchronize()
+    rec = clk.stop()
+    rec["window_s"] = time.perf_counter() - t0
+    return rec
+
+
 # ---------------------------------------------------------------- learned proposal
 
 def other_workloads(ctx, me, torch, dev, hbm_peak, sad_peak):
@@ -245,52 +259,115 @@ def other_workloads(ctx, me, torch, dev, hbm_peak, sad_peak):
 
 
 def cnn_flop_per_block():
-    """Forward FLOPs of the start proposal per 16x16 block (2 per
+    """Forward FLOPs of the start proposal per 16x16 region (2 per
     multiply-add): four 3x3 stride-2 convolutions (2 -> 32 channels at 16x16
     outputs, then 32 -> 32 at 8x8, 4x4 and 2x2) and the linear head (128
-    conv features + 6 neighbour scalars -> 68 logits)."""
+    conv features + 8 neighbour scalars -> 68 logits)."""
     conv = sum(2 * o * o * 32 * cin * 9 for o, cin in ((16, 2), (8, 32), (4, 32), (2, 32)))
-    return conv + 2 * (128 + 6) * 68
+    return conv + 2 * (128 + 8) * 68
+
+
+def _descs_for(me, torch, dev, pairs, R, B):
+    keep, items = [], []
+    for cur, ref in pairs:
+        h, w = cur.shape
+        nb = (w // B) * (h // B)
+        c, r = torch.from_numpy(cur).to(dev), torch.from_numpy(ref).to(dev)
+        m = torch.zeros((nb, 2), dtype=torch.int16, device=dev)
+        sd_ = torch.zeros(nb, dtype=torch.int32, device=dev)
+        ns = torch.zeros(nb, dtype=torch.int16, device=dev)
+        keep.append((c, r, m, sd_, ns))
+        items.append((c, r, R, m, sd_, ns))
+    return keep, me.Context.frame_descs(items)
+
+
+def _quality(ctx, me, torch, keep, B, mv_fs=None):
+    """Mean NSP, PSNR and FS-equal probability of the fields in `keep` (the
+    Sec. IV measures from this library's evaluation kernel)."""
+    sums = torch.zeros((len(keep), me.ME_NSUMS), dtype=torch.int64, device=keep[0][0].device)
+    ev = me.Context.eval_descs((c, r, m, None if mv_fs is None else mv_fs[i], ns)
+                               for i, (c, r, m, sd_, ns) in enumerate(keep))
+    ctx.me_eval_batch(ev, B, sums)
+    torch.cuda.synchronize()
+    st = [ctx.me_stats_from_sums(x) for x in sums.cpu().numpy().view(np.uint64)]
+    out = {"nsp_per_block": float(np.mean([x["nsp"] for x in st])), "psnr_db": float(np.mean([x["psnr"] for x in st]))}
+    if mv_fs is not None:
+        out["probability_fs"] = float(np.mean([x["probability"] for x in st]))
+    return out
+
+
+def _timed_call(torch, fn, reps=3):
+    fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return float(np.median(ts))
+
+
+def _compare(ctx, me, torch, dev, prop, pairs, R, B, with_fs=False):
+    """Plain DCDS, the neighbour-median control and the learned start on the
+    same pairs: blocks/s of one batched call each, NSP and PSNR."""
+    nblocks = sum((c.shape[0] // B) * (c.shape[1] // B) for c, _ in pairs)
+    out = {"pairs": len(pairs), "blocks": nblocks}
+    mv_fs = None
+    if with_fs:
+        kf, df = _descs_for(me, torch, dev, pairs, R, B)
+        ms = _timed_call(torch, lambda: ctx.me_estimate_batch(df, B, "fs"), reps=1)
+        mv_fs = [k[2] for k in kf]
+        out["fs"] = dict(_quality(ctx, me, torch, kf, B), blocks_per_s=nblocks / (ms * 1e-3), ms=ms)
+    for kind in ("plain", "median", "learned"):
+        keep, d = _descs_for(me, torch, dev, pairs, R, B)
+        if kind == "plain":
+            call = lambda: ctx.me_estimate_batch(d, B, "dcds")
+        elif kind == "median":
+            call = lambda: ctx.me_estimate_median_batch(d, block=B)
+        else:
+            call = lambda: ctx.me_estimate_learned_batch(prop, d, block=B)
+        ms = _timed_call(torch, call)
+        out[kind] = dict(_quality(ctx, me, torch, keep, B, mv_fs), blocks_per_s=nblocks / (ms * 1e-3), ms=ms)
+    out["learned_minus_median"] = {"nsp": out["learned"]["nsp_per_block"] - out["median"]["nsp_per_block"],
+                                   "psnr_db": out["learned"]["psnr_db"] - out["median"]["psnr_db"]}
+    return out
 
 
 def learned_leg(ctx, me, torch, dev, curs, refs, mv_plain, mv_fs, st_plain, nb, npairs,
-                tensor_peak=None, train_seqs=60, steps=3000):
-    """Train the start proposal on full-search fields of synthetic CIF pairs
-    with the benchmark's motion statistics (seeds from 100000, disjoint from
-    the benchmark's), then run the learned-start search on the benchmark
-    batch.  Reports its throughput (one call of the C-ABI entry point, which
-    runs the CNN trunk and the wavefront search), NSP and PSNR beside plain
-    DCDS."""
+                tensor_peak=None, train_seqs=400, steps=6000):
+    """The learned start proposal (not in the paper), per the task's
+    learned-proposal workload: trained on full-search fields this library
+    computes on 2,000 synthetic CIF pairs (seeds from 100000, disjoint from
+    every evaluation seed; half with the motion scales 2/1, half 6/3), then
+    compared with plain DCDS and the neighbour-median control on held-out
+    CIF and 720p pairs, on the benchmark batch, and on the stress workload
+    (3840x2160, 8x8 blocks sharing their 16x16 region's proposal, +-32)."""
     from paper_0806_0689_gb300 import synth
     t0 = time.perf_counter()
-    items, keep = [], []
+    train = []
     for sd in range(train_seqs):
-        s = synth.workload_sequence("cif", 6, seed=100000 + sd, max_motion=R_)
-        for t in range(1, 6):
-            c = torch.from_numpy(s[t]).to(dev)
-            r = torch.from_numpy(s[t - 1]).to(dev)
-            n_cif = (352 // 16) * (288 // 16)
-            m = torch.zeros((n_cif, 2), dtype=torch.int16, device=dev)
-            sd_ = torch.zeros(n_cif, dtype=torch.int32, device=dev)
-            ns = torch.zeros(n_cif, dtype=torch.int16, device=dev)
-            keep.append((c, r, m, sd_, ns))
-            items.append((c, r, R_, m, sd_, ns))
-    descs = me.Context.frame_descs(items)
+        scale = (6.0, 3.0) if sd % 2 else (2.0, 1.0)
+        s = synth.workload_sequence("cif", 6, seed=100000 + sd, max_motion=R_, scale=scale)
+        train += [(s[t], s[t - 1]) for t in range(1, 6)]
+    keep_t, descs = _descs_for(me, torch, dev, train, R_, B_)
     ctx.me_estimate_batch(descs, B_, "fs")  # labels: this library's full search
     torch.cuda.synchronize()
+    t_labels = time.perf_counter() - t0
     prop = ctx.me_proposal_create()
     ctx.me_proposal_set_params(prop, me.proposal_init_params(0))
-    losses = me.train_proposal(ctx, prop, descs, steps=steps, lr=3e-3, pairs_per_step=4)
+    t1 = time.perf_counter()
+    losses = me.train_proposal(ctx, prop, descs, steps=steps, lr=2e-3, pairs_per_step=4, seed=1)
     torch.cuda.synchronize()
-    t_train = time.perf_counter() - t0
-    mv_l = torch.empty_like(mv_plain)
-    sad_l = torch.empty((npairs, nb), dtype=torch.int32, device=dev)
-    nsp_l = torch.empty((npairs, nb), dtype=torch.int16, device=dev)
-    d_l = me.Context.frame_descs((curs[i], refs[i], R_, mv_l[i], sad_l[i], nsp_l[i]) for i in range(npairs))
-    # the CNN forward alone (features, trunk, head) on one pair, timed by the
-    # library's own per-call events, against the sustained bf16 tensor peak
+    t_train = time.perf_counter() - t1
+    del keep_t, descs
+    # the CNN forward alone (features, trunk, head) on one 1080p pair, timed by
+    # the library's own per-call events, against the sustained bf16 tensor peak
     logits = torch.empty((nb, me.ME_PROPOSAL_NLOGITS), dtype=torch.float32, device=dev)
-    d_one = me.Context.frame_descs([(curs[0], refs[0], R_, mv_plain[0], sad_l[0], None)])
+    sad_t = torch.empty((nb,), dtype=torch.int32, device=dev)
+    d_one = me.Context.frame_descs([(curs[0], refs[0], R_, mv_plain[0], sad_t, None)])
     ctx.me_set_tracing(True)
     tf = []
     for rep in range(11):
@@ -305,51 +382,46 @@ def learned_leg(ctx, me, torch, dev, curs, refs, mv_plain, mv_fs, st_plain, nb, 
                    "peak": tensor_peak, "frac": fwd_tflops / tensor_peak if tensor_peak else None,
                    "peak_source": "bf16 sustained of measured" if tensor_peak else None,
                    "call": "me_proposal_logits on one 1080p pair (median of 10, me_last_call_ms)"}
-    ctx.me_estimate_learned_batch(prop, d_l)  # warm-up
-    ts = []
-    for _ in range(3):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        ctx.me_estimate_learned_batch(prop, d_l)
-        e1.record()
-        torch.cuda.synchronize()
-        ts.append(e0.elapsed_time(e1))
-    sums = torch.zeros((npairs, me.ME_NSUMS), dtype=torch.int64, device=dev)
-    e_l = me.Context.eval_descs((curs[i], refs[i], mv_l[i], mv_fs[i], nsp_l[i]) for i in range(npairs))
-    ctx.me_eval_batch(e_l, B_, sums)
-    torch.cuda.synchronize()
-    st = [ctx.me_stats_from_sums(r) for r in sums.cpu().numpy().view(np.uint64)]
-    ctx.me_proposal_free(prop)
+    # the benchmark batch: learned and median against plain DCDS, beside the FS field
+    mv_l = torch.empty_like(mv_plain)
+    sad_l = torch.empty((npairs, nb), dtype=torch.int32, device=dev)
+    nsp_l = torch.empty((npairs, nb), dtype=torch.int16, device=dev)
+    d_l = me.Context.frame_descs((curs[i], refs[i], R_, mv_l[i], sad_l[i], nsp_l[i]) for i in range(npairs))
+    keep_l = [(curs[i], refs[i], mv_l[i], sad_l[i], nsp_l[i]) for i in range(npairs)]
+    fs_list = [mv_fs[i] for i in range(npairs)]
+    ms = _timed_call(torch, lambda: ctx.me_estimate_learned_batch(prop, d_l))
+    q_l = _quality(ctx, me, torch, keep_l, B_, fs_list)
+    ms_m = _timed_call(torch, lambda: ctx.me_estimate_median_batch(d_l))
+    q_m = _quality(ctx, me, torch, keep_l, B_, fs_list)
     mean = lambda rows, k: float(np.mean([r[k] for r in rows]))
-    ms = float(np.median(ts))
-    # the non-learned control: the same wavefront search from the neighbours' median
-    ctx.me_estimate_median_batch(d_l)
-    tm = []
-    for _ in range(3):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        ctx.me_estimate_median_batch(d_l)
-        e1.record()
-        torch.cuda.synchronize()
-        tm.append(e0.elapsed_time(e1))
-    sums_m = torch.zeros_like(sums)
-    ctx.me_eval_batch(e_l, B_, sums_m)
-    torch.cuda.synchronize()
-    st_m = [ctx.me_stats_from_sums(r) for r in sums_m.cpu().numpy().view(np.uint64)]
-    ms_m = float(np.median(tm))
-    median = {"macroblocks_per_s": npairs * nb / (ms_m * 1e-3), "ms_per_batch": ms_m,
-              "nsp_per_mb": mean(st_m, "nsp"), "psnr_db": mean(st_m, "psnr"),
-              "psnr_minus_plain_db": mean(st_m, "psnr") - mean(st_plain, "psnr"),
-              "probability_fs": mean(st_m, "probability")}
-    return {"macroblocks_per_s": npairs * nb / (ms * 1e-3), "ms_per_batch": ms,
-            "nsp_per_mb": mean(st, "nsp"), "psnr_db": mean(st, "psnr"),
-            "plain_nsp_per_mb": mean(st_plain, "nsp"), "plain_psnr_db": mean(st_plain, "psnr"),
-            "psnr_minus_plain_db": mean(st, "psnr") - mean(st_plain, "psnr"),
-            "distance_to_fs": mean(st, "distance"), "probability_fs": mean(st, "probability"),
-            "training": {"pairs": len(items), "steps": steps, "final_loss": float(np.mean(losses[-50:])),
-                         "seconds": t_train, "labels": "full-search fields from this library (CIF, seeds >= 100000)"},
-            "cnn_forward": cnn_forward,
-            "median_start_control": median}
+    bench_batch = {"macroblocks_per_s": npairs * nb / (ms * 1e-3), "ms_per_batch": ms,
+                   "nsp_per_mb": q_l["nsp_per_block"], "psnr_db": q_l["psnr_db"],
+                   "probability_fs": q_l["probability_fs"],
+                   "plain_nsp_per_mb": mean(st_plain, "nsp"), "plain_psnr_db": mean(st_plain, "psnr"),
+                   "psnr_minus_plain_db": q_l["psnr_db"] - mean(st_plain, "psnr"),
+                   "median_start_control": {"macroblocks_per_s": npairs * nb / (ms_m * 1e-3), "ms_per_batch": ms_m,
+                                            "nsp_per_mb": q_m["nsp_per_block"], "psnr_db": q_m["psnr_db"],
+                                            "probability_fs": q_m["probability_fs"]}}
+    # held-out CIF and 720p pairs (the learned-proposal workload's evaluation)
+    held = {}
+    for name, nfr, seeds, scale in (("cif", 4, range(5000, 5010), (6.0, 3.0)), ("cif", 4, range(5000, 5010), (2.0, 1.0)),
+                                    ("720p", 3, range(5100, 5104), (6.0, 3.0)), ("720p", 3, range(5100, 5104), (2.0, 1.0))):
+        pairs = []
+        for sd in seeds:
+            s = synth.workload_sequence(name, nfr, seed=sd, max_motion=R_, scale=scale)
+            pairs += [(s[t], s[t - 1]) for t in range(1, nfr)]
+        held[f"{name}_scales_{scale[0]:g}_{scale[1]:g}"] = _compare(ctx, me, torch, dev, prop, pairs, R_, B_)
+    # the stress workload: 12 pairs of 3840x2160, 8x8 blocks, +-32, scales 6/3
+    s = synth.workload_sequence("2160p", 13, seed=4000, max_motion=32, scale=(6.0, 3.0))
+    stress = _compare(ctx, me, torch, dev, prop, [(s[t + 1], s[t]) for t in range(12)], 32, 8, with_fs=True)
+    ctx.me_proposal_free(prop)
+    return dict(bench_batch,
+                training={"pairs": len(train), "steps": steps, "pairs_per_step": 4, "lr": 2e-3,
+                          "first_loss": float(np.mean(losses[:20])), "final_loss": float(np.mean(losses[-50:])),
+                          "label_seconds": t_labels, "train_seconds": t_train,
+                          "labels": "full-search fields from this library (CIF, seeds >= 100000, scales 2/1 and 6/3)",
+                          "call": "me_proposal_train (the loop in the library)"},
+                cnn_forward=cnn_forward, held_out=held, stress_2160p_8x8_r32_12_pairs=stress)
 
 
 # ---------------------------------------------------------------- reference arm
@@ -490,7 +562,15 @@ def main():
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+    # the clock sampler runs across the timed steps: started a little before
+    # them (the same step runs meanwhile, untimed) and kept on afterwards, so
+    # that its window covers at least 1.2 s of this load
     clk = Clocks(local)
+    w0 = time.perf_counter()
+    while time.perf_counter() - w0 < 0.3:
+        for _ in range(20):
+            ctx.me_graph_launch(g_step)
+        torch.cuda.synchronize()
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
     t_start.record(stream)
@@ -501,7 +581,13 @@ def main():
         e1.record(stream)
     t_end.record(stream)
     torch.cuda.synchronize()
+    while time.perf_counter() - w0 < 1.2:
+        for _ in range(20):
+            ctx.me_graph_launch(g_step)
+        torch.cuda.synchronize()
     clocks = clk.stop()
+    clocks["window_s"] = time.perf_counter() - w0
+    clocks["window"] = "the timed steps plus untimed repeats of the same step before and after them"
     if dist:
         dist.barrier()
     ms_total = t_start.elapsed_time(t_end)
@@ -704,6 +790,8 @@ def main():
     achieved = alg_bytes / (dcds_launch_ms * 1e-3) / 1e9
     rates, used = ctx.me_absdiff_peak(iters=4096)
     sad_peak = max(rates)
+    clk_absdiff = clocked(torch, lambda: ctx.me_absdiff_peak(iters=4096))
+    clk_fs = clocked(torch, lambda: ctx.me_graph_launch(g_fs))
     nsp_mean = mean(st_d, "nsp")
     fs_launch_ms = float(np.median(fs_ms))
     fs_absdiff = float(np.sum(nsp_fs.cpu().numpy().view(np.uint16).astype(np.float64))) * B_ * B_
@@ -751,6 +839,14 @@ def main():
         "e2e_sequence": e2e_seq,
         "gpu_launches": a.steps,
         "clocks": clocks,
+        "clock_normalised": {
+            "note": "time x the median SM clock sampled while that work ran (kilocycles), and rates per cycle",
+            "dcds_step_kcycles": dcds_launch_ms * clocks["sm_mhz"] if clocks.get("sm_mhz") else None,
+            "fs_launch_kcycles": fs_launch_ms * clk_fs["sm_mhz"] if clk_fs.get("sm_mhz") else None,
+            "absdiff_peak_per_cycle_per_sm": (sad_peak / (clk_absdiff["sm_mhz"] * 1e6) /
+                                              torch.cuda.get_device_properties(dev).multi_processor_count
+                                              if clk_absdiff.get("sm_mhz") else None),
+            "clocks_fs": clk_fs, "clocks_absdiff": clk_absdiff},
     }
     if cb is not None:
         line["cpu_baseline"] = cb

@@ -346,10 +346,11 @@ int me_proposal_logits(me_ctx* ctx, me_proposal* p, const me_frame_desc* desc, f
  * t = rx + ry, the four blocks of a region together).  The head turns those
  * MVs, their median and the region's conv features into a start (argmax of
  * the dx and dy heads, ties to the class nearest 0) and a prior (V when its
- * logit is larger).  For each block of the region the start is clamped to
- * the block's window and frame; the origin and the start are evaluated, the
- * better one (the origin on a tie) centres the first pattern (HCSP, or its
- * transpose for a V prior), then DCDS steps 2-4 follow.  NSP counts every
+ * logit is larger).  For each block of the region the median and the start
+ * are clamped to the block's window and frame; the origin, the median and
+ * the start are evaluated in this order, the best one (the earliest on a
+ * tie) centres the first pattern (HCSP, or its transpose for a V prior), then
+ * DCDS steps 2-4 follow.  NSP counts every
  * distinct point.  Outputs go to descs[i].mv / sad / nsp; starts (DEVICE
  * int16 [total blocks][3] = sx, sy, prior per search block, clamped;
  * nullable) records the proposals.  p = NULL uses the context's own

@@ -79,11 +79,11 @@ def _load():
             lib.oracle_hcsp_offsets.restype = None
             lib.oracle_hcsp_offsets.argtypes = [P]
             lib.oracle_search_from.restype = I
-            lib.oracle_search_from.argtypes = [BDM_FN, P, I, I, I, I, I, I, I, I, I, P]
+            lib.oracle_search_from.argtypes = [BDM_FN, P, I, I, I, I, I, I, I, I, I, I, I, P]
             lib.oracle_dcds_block_from.restype = I
-            lib.oracle_dcds_block_from.argtypes = [P, P, I, I, I, I, I, I, I, I, I, I, P]
+            lib.oracle_dcds_block_from.argtypes = [P, P, I, I, I, I, I, I, I, I, I, I, I, I, P]
             lib.oracle_dcds_from_starts.restype = I
-            lib.oracle_dcds_from_starts.argtypes = [P, P, I, I, I, I, I, P, P, P, P]
+            lib.oracle_dcds_from_starts.argtypes = [P, P, I, I, I, I, I, P, P, P, P, P]
             lib.oracle_cnn_nparams.restype = I
             lib.oracle_cnn_features.restype = None
             lib.oracle_cnn_features.argtypes = [P, P, I, I, I, I, I, P, I, P, P]
@@ -194,31 +194,35 @@ def search(bdm, rng, dx_lim=(-10**6, 10**6), dy_lim=(-10**6, 10**6), simplified=
 
 
 def search_from(bdm, rng, start=(0, 0), prior_v=False, dx_lim=(-10**6, 10**6), dy_lim=(-10**6, 10**6),
-                simplified=False):
-    """DCDS from a proposed start: the better of the origin and ``start`` (the
-    origin on a tie) centres the first pattern, the HCSP or (prior_v) its
-    transpose; then DCDS steps 2-4.  Returns (mvx, mvy, bdm_at_mv, nsp)."""
+                simplified=False, cand=(0, 0)):
+    """DCDS from a proposal: the origin, ``cand`` and ``start`` are evaluated in
+    this order and the best (the earliest on a tie) centres the first
+    pattern, the HCSP or (prior_v) its transpose; then DCDS steps 2-4.
+    Returns (mvx, mvy, bdm_at_mv, nsp)."""
     cb = BDM_FN(lambda _u, dx, dy: int(bdm(dx, dy)))
     out = (ctypes.c_int64 * 4)()
-    rc = _load().oracle_search_from(cb, None, rng, dx_lim[0], dx_lim[1], dy_lim[0], dy_lim[1], int(start[0]),
-                                    int(start[1]), int(bool(prior_v)), int(bool(simplified)),
-                                    ctypes.cast(out, ctypes.c_void_p))
+    rc = _load().oracle_search_from(cb, None, rng, dx_lim[0], dx_lim[1], dy_lim[0], dy_lim[1], int(cand[0]),
+                                    int(cand[1]), int(start[0]), int(start[1]), int(bool(prior_v)),
+                                    int(bool(simplified)), ctypes.cast(out, ctypes.c_void_p))
     if rc:
         raise MemoryError("oracle_search_from failed")
     return int(out[0]), int(out[1]), int(out[2]), int(out[3])
 
 
-def dcds_from_starts(cur, ref, block, rng, starts):
-    """DCDS of every block from per-block (sx, sy, prior_v) starts (int16 [nb, 3])."""
+def dcds_from_starts(cur, ref, block, rng, starts, cands=None):
+    """DCDS of every block from per-block (sx, sy, prior_v) starts (int16
+    [nb, 3]), with cands (int16 [nb, 2], None = the origin) evaluated before
+    each start."""
     cur, ref = _frames(cur, ref)
     h, w = cur.shape
     nb = (w // block) * (h // block)
     starts = np.ascontiguousarray(starts, dtype=np.int16).reshape(nb, 3)
+    cands = None if cands is None else np.ascontiguousarray(cands, dtype=np.int16).reshape(nb, 2)
     mv = np.zeros((nb, 2), np.int16)
     sd = np.zeros(nb, np.uint32)
     ns = np.zeros(nb, np.uint16)
-    rc = _load().oracle_dcds_from_starts(_ptr(cur), _ptr(ref), w, h, w, block, rng, _ptr(starts), _ptr(mv),
-                                         _ptr(sd), _ptr(ns))
+    rc = _load().oracle_dcds_from_starts(_ptr(cur), _ptr(ref), w, h, w, block, rng, _ptr(starts), _ptr(cands),
+                                         _ptr(mv), _ptr(sd), _ptr(ns))
     if rc:
         raise ValueError("oracle_dcds_from_starts rejected its arguments")
     return mv, sd, ns
@@ -312,9 +316,10 @@ def _search_regions(cur, ref, rng, block, propose):
     """DCDS of every block from a start shared by the blocks of its 16x16
     region.  Regions run in raster order, so the left, top and top-right
     neighbours of a region's top-left block are final before it starts.
-    propose(mv, k0, px, py) returns the region's raw start (sx, sy, prior_v),
-    k0 being the index of its top-left block; every block clamps the start
-    to its own window and frame.  Returns (mv, sad, nsp, starts)."""
+    propose(mv, k0, px, py) returns the region's raw start (sx, sy, prior_v)
+    and the candidate evaluated before it (ax, ay), k0 being the index of its
+    top-left block; every block clamps both to its own window and frame.
+    Returns (mv, sad, nsp, starts)."""
     cur, ref = _frames(cur, ref)
     h, w = cur.shape
     if w % 16 or h % 16 or block not in (8, 16):
@@ -327,12 +332,12 @@ def _search_regions(cur, ref, rng, block, propose):
     out = (ctypes.c_int64 * 4)()
     L = _load()
     for px, py, blocks in _regions(w, h, block):
-        sx, sy, pv = propose(mv, blocks[0][0], px, py)
+        sx, sy, pv, ax, ay = propose(mv, blocks[0][0], px, py)
         for k, bx, by in blocks:
             starts[k] = (max(max(-rng, -bx), min(min(rng, w - block - bx), sx)),
                          max(max(-rng, -by), min(min(rng, h - block - by), sy)), pv)
-            rc = L.oracle_dcds_block_from(_ptr(cur), _ptr(ref), w, h, w, block, rng, bx, by, int(sx), int(sy),
-                                          int(pv), ctypes.cast(out, ctypes.c_void_p))
+            rc = L.oracle_dcds_block_from(_ptr(cur), _ptr(ref), w, h, w, block, rng, bx, by, int(ax), int(ay),
+                                          int(sx), int(sy), int(pv), ctypes.cast(out, ctypes.c_void_p))
             if rc:
                 raise MemoryError("oracle_dcds_block_from failed")
             mv[k] = (out[0], out[1])
@@ -350,16 +355,32 @@ def median_dcds(cur, ref, rng, block=16):
     nbx = w // block
 
     def propose(mv, k0, px, py):
-        cand = []
-        bx, by = k0 % nbx, k0 // nbx
-        for ax, ay in ((bx - 1, by), (bx, by - 1), (bx + 1, by - 1)):
-            ok = 0 <= ax < nbx and ay >= 0
-            cand.append((int(mv[ay * nbx + ax][0]), int(mv[ay * nbx + ax][1])) if ok else (0, 0))
-        sx = sorted(c[0] for c in cand)[1]
-        sy = sorted(c[1] for c in cand)[1]
-        return sx, sy, int(abs(sy) > abs(sx))
+        sx, sy = neighbour_median(mv, k0, nbx)
+        return sx, sy, int(abs(sy) > abs(sx)), 0, 0
 
     return _search_regions(cur, ref, rng, block, propose)
+
+
+def neighbour_median(mv, k0, nbx):
+    """Component-wise median of the left, top and top-right final MVs of block
+    k0 (an absent neighbour counts as (0,0))."""
+    cand = []
+    bx, by = k0 % nbx, k0 // nbx
+    for ax, ay in ((bx - 1, by), (bx, by - 1), (bx + 1, by - 1)):
+        ok = 0 <= ax < nbx and ay >= 0
+        cand.append((int(mv[ay * nbx + ax][0]), int(mv[ay * nbx + ax][1])) if ok else (0, 0))
+    return sorted(c[0] for c in cand)[1], sorted(c[1] for c in cand)[1]
+
+
+def region_medians(field, w, h, block):
+    """Per block (int16 [nb, 2]): the neighbour median of its 16x16 region's
+    top-left block, taken from a final motion field -- the candidate the
+    learned search evaluates before the network's start."""
+    nbx = w // block
+    out = np.zeros(((w // block) * (h // block), 2), np.int16)
+    for _, _, blocks in _regions(w, h, block):
+        out[[k for k, _, _ in blocks]] = neighbour_median(field, blocks[0][0], nbx)
+    return out
 
 
 def mvp_counts(frames, R):
@@ -425,18 +446,24 @@ def learned_dcds(cur, ref, rng, params, block=16):
     """Learned-start DCDS of a frame: one proposal per 16x16 region (one
     16x16 block, or four 8x8 blocks that share it), regions in raster order
     so that the left, top and top-right neighbours of a region's top-left
-    block are final before it starts.  Returns (mv, sad, nsp, starts,
-    logits), logits per region in raster order."""
+    block are final before it starts.  Each block evaluates the origin, the
+    neighbours' median and the network's start, in this order; the best
+    centres the first pattern (HCSP, or its transpose for a vertical prior).
+    Returns (mv, sad, nsp, starts, logits), logits per region in raster
+    order."""
     h, w = np.asarray(cur).shape
     logits = np.zeros(((w // 16) * (h // 16), 68), np.float64)
     count = [0]
+    nbx = w // block
 
     def propose(mv, k0, px, py):
         x, mvf = cnn_features(cur, ref, px, py, mv, block)
         lg = cnn_forward(params, x, mvf)
         logits[count[0]] = lg
         count[0] += 1
-        return cnn_raw_start(lg)
+        sx, sy, pv = cnn_raw_start(lg)
+        mx, my = neighbour_median(mv, k0, nbx)
+        return sx, sy, pv, mx, my
 
     mv, sd, ns, starts = _search_regions(cur, ref, rng, block, propose)
     return mv, sd, ns, starts, logits

@@ -206,11 +206,13 @@ static const int VCSP_[7][2] = {{0, 0}, {0, -1}, {0, 1}, {-1, 0}, {1, 0}, {0, -2
 
 /*
  * One DCDS search over the window of `range` (Sec. III-B, steps 1-4 and the
- * two switching strategies), started from a proposal: the origin and the
- * start point (sx, sy) are evaluated and the better one (the origin on a
- * tie) becomes the centre of the first pattern, which is the HCSP, or its
- * transpose when prior_v is set.  With start (0,0) and prior_v = 0 this is
- * exactly the paper's DCDS.  `simplified` selects DCDS^S (Sec. IV-C): the
+ * two switching strategies), started from a proposal: the origin, the
+ * candidate (ax, ay) and the start point (sx, sy) are evaluated in this
+ * order and the best one (the earliest on a tie) becomes the centre of the
+ * first pattern, which is the HCSP, or its transpose when prior_v is set; a
+ * candidate that repeats an earlier one is neither evaluated nor counted
+ * again.  With both at the origin and prior_v = 0 this is exactly the
+ * paper's DCDS.  `simplified` selects DCDS^S (Sec. IV-C): the
  * last step checks only the middle point on the side of the better distant
  * point.  Returns the motion vector, its BDM and the NSP in out[0..3]
  * (out[2] is the BDM truncated to 64 bits, out[3] the NSP).
@@ -223,7 +225,7 @@ static const int VCSP_[7][2] = {{0, 0}, {0, -1}, {0, 1}, {-1, 0}, {1, 0}, {0, -2
  */
 int oracle_search_from(oracle_bdm_fn bdm, void* user, int range,
                        int dx_min, int dx_max, int dy_min, int dy_max,
-                       int sx, int sy, int prior_v, int simplified, int64_t* out)
+                       int ax, int ay, int sx, int sy, int prior_v, int simplified, int64_t* out)
 {
     search_t s;
     s.range = range;
@@ -235,12 +237,15 @@ int oracle_search_from(oracle_bdm_fn bdm, void* user, int range,
     s.nsp = 0;
     if (!s.value || !s.seen) { free(s.value); free(s.seen); return 1; }
 
-    /* Centre of the first pattern: the origin, or the proposed start when it
-     * is strictly better. */
+    /* Centre of the first pattern: the origin, or a proposed point when it
+     * is strictly better than the ones before it. */
     int64_t cval, sval;
     eval_point(&s, 0, 0, &cval);            /* the origin is always a candidate */
     int cx = 0, cy = 0, bx, by;
-    if ((sx != 0 || sy != 0) && eval_point(&s, sx, sy, &sval) && sval < cval) {
+    if (eval_point(&s, ax, ay, &sval) && sval < cval) {
+        cx = ax; cy = ay; cval = sval;
+    }
+    if (eval_point(&s, sx, sy, &sval) && sval < cval) {
         cx = sx; cy = sy; cval = sval;
     }
     /* Step 1: HCSP (or VCSP) at that centre. */
@@ -289,7 +294,7 @@ int oracle_search(oracle_bdm_fn bdm, void* user, int range,
                   int dx_min, int dx_max, int dy_min, int dy_max,
                   int simplified, int64_t* out)
 {
-    return oracle_search_from(bdm, user, range, dx_min, dx_max, dy_min, dy_max, 0, 0, 0, simplified, out);
+    return oracle_search_from(bdm, user, range, dx_min, dx_max, dy_min, dy_max, 0, 0, 0, 0, 0, simplified, out);
 }
 
 typedef struct {
@@ -348,25 +353,28 @@ int oracle_dcds_blocks(const uint8_t* cur, const uint8_t* ref, int w, int h, int
     return 0;
 }
 
-/* DCDS of the block at pixel (bx, by) from the start (sx, sy, prior_v),
- * the start clamped to the window and the frame.  out = mv x, mv y, SAD, NSP. */
+static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+/* DCDS of the block at pixel (bx, by) from the candidate (ax, ay) and the
+ * start (sx, sy, prior_v), both clamped to the window and the frame.
+ * out = mv x, mv y, SAD, NSP. */
 int oracle_dcds_block_from(const uint8_t* cur, const uint8_t* ref, int w, int h, int pitch, int block,
-                           int range, int bx, int by, int sx, int sy, int prior_v, int64_t* out)
+                           int range, int bx, int by, int ax, int ay, int sx, int sy, int prior_v, int64_t* out)
 {
     int lo_x = -bx > -range ? -bx : -range, hi_x = w - block - bx < range ? w - block - bx : range;
     int lo_y = -by > -range ? -by : -range, hi_y = h - block - by < range ? h - block - by : range;
-    sx = sx < lo_x ? lo_x : (sx > hi_x ? hi_x : sx);
-    sy = sy < lo_y ? lo_y : (sy > hi_y ? hi_y : sy);
     sad_user_t u = {cur, ref, pitch, bx, by, block};
-    return oracle_search_from(sad_cb, &u, range, -bx, w - block - bx, -by, h - block - by, sx, sy,
-                              prior_v != 0, 0, out);
+    return oracle_search_from(sad_cb, &u, range, -bx, w - block - bx, -by, h - block - by,
+                              clampi(ax, lo_x, hi_x), clampi(ay, lo_y, hi_y), clampi(sx, lo_x, hi_x),
+                              clampi(sy, lo_y, hi_y), prior_v != 0, 0, out);
 }
 
 /* DCDS of every block of a frame from per-block starts: starts[3k..3k+2] =
- * (sx, sy, prior_v) (16x16 or 8x8 blocks; the start is clamped to the
+ * (sx, sy, prior_v), cands[2k..2k+1] (NULL: the origin) the candidate
+ * evaluated before the start (16x16 or 8x8 blocks; both clamped to the
  * window and the frame). */
 int oracle_dcds_from_starts(const uint8_t* cur, const uint8_t* ref, int w, int h, int pitch,
-                            int block, int range, const int16_t* starts,
+                            int block, int range, const int16_t* starts, const int16_t* cands,
                             int16_t* mv, uint32_t* sad, uint16_t* nsp)
 {
     if (block <= 0 || w % block || h % block || range < 0) return 1;
@@ -377,13 +385,13 @@ int oracle_dcds_from_starts(const uint8_t* cur, const uint8_t* ref, int w, int h
             int bx = i * block, by = j * block;
             int lo_x = -bx > -range ? -bx : -range, hi_x = w - block - bx < range ? w - block - bx : range;
             int lo_y = -by > -range ? -by : -range, hi_y = h - block - by < range ? h - block - by : range;
-            int sx = starts[3 * k], sy = starts[3 * k + 1];
-            sx = sx < lo_x ? lo_x : (sx > hi_x ? hi_x : sx);
-            sy = sy < lo_y ? lo_y : (sy > hi_y ? hi_y : sy);
+            int sx = clampi(starts[3 * k], lo_x, hi_x), sy = clampi(starts[3 * k + 1], lo_y, hi_y);
+            int ax = cands ? clampi(cands[2 * k], lo_x, hi_x) : 0;
+            int ay = cands ? clampi(cands[2 * k + 1], lo_y, hi_y) : 0;
             sad_user_t u = {cur, ref, pitch, bx, by, block};
             int64_t out[4];
             if (oracle_search_from(sad_cb, &u, range, -bx, w - block - bx, -by, h - block - by,
-                                   sx, sy, starts[3 * k + 2] != 0, 0, out)) return 1;
+                                   ax, ay, sx, sy, starts[3 * k + 2] != 0, 0, out)) return 1;
             mv[2 * k] = (int16_t)out[0];
             mv[2 * k + 1] = (int16_t)out[1];
             sad[k] = (uint32_t)out[2];

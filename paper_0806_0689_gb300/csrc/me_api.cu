@@ -30,12 +30,6 @@ using me::kHeadBytes;
 #ifndef ME_DCDS_THREADS
 #define ME_DCDS_THREADS 128  // default CTA size of the DCDS kernel
 #endif
-#ifndef ME_DCDS_KERNEL
-#define ME_DCDS_KERNEL 0     // default DCDS kernel: tile-phase (the warp-specialised one is a tuner candidate)
-#endif
-#ifndef ME_DCDS_AWARPS
-#define ME_DCDS_AWARPS 4     // default A warps per CTA of the warp-specialised kernel
-#endif
 
 namespace {
 
@@ -112,8 +106,6 @@ Shape default_shape(me_ctx* c, int algo, int block, int range)
     s.k = 0;
     s.ctas_per_sm = 0;  // from the occupancy of the kernel
     s.stages = ME_DCDS_STAGES;
-    s.kernel = ME_DCDS_KERNEL;
-    s.a_warps = ME_DCDS_AWARPS;
     (void)c;
     return s;
 }
@@ -171,23 +163,6 @@ int take_slot(me_ctx* c, size_t bytes, Slot** out)
     return ME_OK;
 }
 
-// Make a DCDS item queue of at least `entries` items, zeroed at allocation
-// (the warp-specialised kernel never needs it reset).
-int ensure_queue(me_ctx* c, void** q, size_t* qcap, size_t entries)
-{
-    if (*qcap >= entries) return ME_OK;
-    if (*q) cudaFree(*q);
-    *q = nullptr;
-    *qcap = 0;
-    const size_t cap = (std::max<size_t>(entries, 4096) + 63) & ~size_t(63);
-    const size_t bytes = me::dcds_queue_bytes(cap);
-    if (cudaMalloc(q, bytes) != cudaSuccess) return fail(c, ME_ERR_NOMEM, "cudaMalloc of the DCDS queue failed");
-    cudaError_t e = cudaMemset(*q, 0, bytes);
-    if (e != cudaSuccess) return cuda_fail(c, e, "queue initialisation");
-    *qcap = cap;
-    return ME_OK;
-}
-
 // Fused evaluation of a DCDS batch: mv_fs (host array of n device pointers,
 // nullable) and the device sums [n][ME_NSUMS].  d8 (FS only): the 8x8 outputs
 // of the two-size full search.
@@ -223,10 +198,9 @@ int build_table(const me_frame_desc* d, int n, int block, const Shape& s, bool f
             f.tiles_y = f.nby;
             if (!me::encode_fs_maps(f, g.nch, me::fs_rows(block, f.range, s.k), s.tx * block, block)) return -1;
         } else {
-            const int th = s.kernel == 3 ? me::cross_tile_h() : me::kTile;
             f.tiles_x = (f.w + me::kTile - 1) / me::kTile;
-            f.tiles_y = (f.h + th - 1) / th;
-            if (!me::encode_frame_maps(f, th)) return -1;
+            f.tiles_y = (f.h + me::kTile - 1) / me::kTile;
+            if (!me::encode_frame_maps(f)) return -1;
         }
         if (ev && ev->sums) {
             f.sums = reinterpret_cast<unsigned long long*>(ev->sums) + (size_t)ME_NSUMS * i;
@@ -264,19 +238,17 @@ int validate_batch(me_ctx* c, const me_frame_desc* d, int n, int block, int algo
     return ME_OK;
 }
 
-// Launch the search over a table already on the device at `dev` (queue: the
-// DCDS item queue of `qcap` entries, for the warp-specialised kernel).
-cudaError_t launch_search(me_ctx* c, void* dev, void* queue, size_t qcap, int n, int ntiles, int block, int algo,
-                          int max_range, const Shape& s, cudaStream_t st, const EvalArgs* ev = nullptr)
+// Launch the search over a table already on the device at `dev`.
+cudaError_t launch_search(me_ctx* c, void* dev, int n, int ntiles, int block, int algo, int max_range,
+                          const Shape& s, cudaStream_t st, const EvalArgs* ev = nullptr)
 {
     int* head = reinterpret_cast<int*>(dev);
     const FrameDev* table = reinterpret_cast<const FrameDev*>(reinterpret_cast<char*>(dev) + kHeadBytes);
     cudaError_t e = cudaMemsetAsync(head, 0, me::kCounterInts * sizeof(int), st);
     if (e != cudaSuccess) return e;
     // failure-detection test hook: a non-zero last counter word makes the DCDS
-    // tile kernel arm its first copies for bytes that never arrive
-    const bool tile_kernel = algo != ME_ALGO_FS && (s.kernel == 0 || s.kernel == 3 || (ev && ev->sums));
-    if (c->inject_wait_timeout && tile_kernel) {
+    // kernel arm its first copies for bytes that never arrive
+    if (c->inject_wait_timeout && algo != ME_ALGO_FS) {
         e = cudaMemsetAsync(head + me::kCounterInts - 1, 1, sizeof(int), st);
         if (e != cudaSuccess) return e;
     }
@@ -284,12 +256,7 @@ cudaError_t launch_search(me_ctx* c, void* dev, void* queue, size_t qcap, int n,
         // the fused evaluation runs in the tile-phase kernel; its sums accumulate from zero
         e = cudaMemsetAsync(ev->sums, 0, sizeof(uint64_t) * ME_NSUMS * (size_t)n, st);
         if (e != cudaSuccess) return e;
-        if (s.kernel == 3)
-            return me::launch_dcds_cross(table, n, ntiles, block, max_range, algo == ME_ALGO_DCDS_S, s, head,
-                                         c->status, c->num_sms, st, true);
         Shape t = s;
-        if (t.kernel != 0) t = default_shape(c, algo, block, max_range);
-        t.kernel = 0;
         t.threads = 128;  // the fused variant uses more registers: small CTAs keep four per SM
         return me::launch_dcds(table, n, ntiles, block, max_range, algo == ME_ALGO_DCDS_S, t, head, c->status,
                                c->num_sms, st, true);
@@ -297,24 +264,8 @@ cudaError_t launch_search(me_ctx* c, void* dev, void* queue, size_t qcap, int n,
     if (algo == ME_ALGO_FS)
         return me::launch_fs(table, n, ntiles, block, max_range, s, head, c->status, c->num_sms, st,
                              ev && ev->d8);
-    if (s.kernel == 1)
-        return me::launch_dcds_ws(table, n, ntiles, block, max_range, algo == ME_ALGO_DCDS_S, s, head, queue,
-                                  (int)qcap, c->status, c->num_sms, st);
-    if (s.kernel == 2)
-        return me::launch_dcds_stream(table, n, ntiles, block, max_range, algo == ME_ALGO_DCDS_S, s, head,
-                                      c->status, c->num_sms, st);
-    if (s.kernel == 3)
-        return me::launch_dcds_cross(table, n, ntiles, block, max_range, algo == ME_ALGO_DCDS_S, s, head, c->status,
-                                     c->num_sms, st);
     return me::launch_dcds(table, n, ntiles, block, max_range, algo == ME_ALGO_DCDS_S, s, head, c->status,
                            c->num_sms, st);
-}
-
-size_t total_blocks(const me_frame_desc* d, int n, int block)
-{
-    size_t t = 0;
-    for (int i = 0; i < n; ++i) t += (size_t)(d[i].w / block) * (d[i].h / block);
-    return t;
 }
 
 int run_batch(me_ctx* c, const me_frame_desc* d, int n, int block, int algo, const Shape& s, cudaStream_t st,
@@ -330,11 +281,7 @@ int run_batch(me_ctx* c, const me_frame_desc* d, int n, int block, int algo, con
     if (ntiles < 0) return fail(c, ME_ERR_CUDA, "cuTensorMapEncodeTiled rejected a frame description");
     cudaError_t e = cudaMemcpyAsync(slot->dev, slot->host, bytes, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "descriptor upload");
-    if (algo != ME_ALGO_FS && s.kernel == 1) {
-        rc = ensure_queue(c, &slot->queue, &slot->qcap, total_blocks(d, n, block));
-        if (rc != ME_OK) return rc;
-    }
-    e = launch_search(c, slot->dev, slot->queue, slot->qcap, n, ntiles, block, algo, max_range, s, st, ev);
+    e = launch_search(c, slot->dev, n, ntiles, block, algo, max_range, s, st, ev);
     if (e != cudaSuccess) return cuda_fail(c, e, "search launch");
     e = cudaEventRecord(slot->done, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaEventRecord");
@@ -348,14 +295,14 @@ void load_tune_cache(me_ctx* c)
     std::ifstream f(c->tune_path);
     std::string line;
     while (std::getline(f, line)) {
-        // algo block range WxH tx ty threads k stages kernel a_warps
+        // algo block range WxH tx ty threads k stages
         std::istringstream is(line);
-        int algo, block, range, tx, ty, th, k, stages, kernel, aw;
+        int algo, block, range, tx, ty, th, k, stages;
         std::string wh;
-        if (is >> algo >> block >> range >> wh >> tx >> ty >> th >> k >> stages >> kernel >> aw) {
+        if (is >> algo >> block >> range >> wh >> tx >> ty >> th >> k >> stages) {
             int w = 0, h = 0;
             if (sscanf(wh.c_str(), "%dx%d", &w, &h) == 2) {
-                Shape s{tx, ty, th, 0, k, stages, kernel, aw};
+                Shape s{tx, ty, th, 0, k, stages};
                 c->tuned[shape_key(algo, block, range, w, h)] = s;
             }
         }
@@ -398,7 +345,6 @@ void me_free(me_ctx* c)
         if (s.done) cudaEventDestroy(s.done);
         if (s.dev) cudaFree(s.dev);
         if (s.host) cudaFreeHost(s.host);
-        if (s.queue) cudaFree(s.queue);
     }
     if (c->status) cudaFree(c->status);
     if (c->median_ws) me_proposal_free(c->median_ws);
@@ -468,15 +414,10 @@ int graph_create(me_ctx* c, const me_frame_desc* descs, int n, int block, int al
     e = cudaMemcpy(reinterpret_cast<char*>(g->dev) + kHeadBytes, table.data(), sizeof(FrameDev) * n,
                    cudaMemcpyHostToDevice);
     cudaStream_t cs = nullptr;
-    size_t qcap = 0;
-    if (e == cudaSuccess && algo != ME_ALGO_FS && s.kernel == 1) {
-        rc = ensure_queue(c, &g->queue, &qcap, total_blocks(descs, n, block));
-        if (rc != ME_OK) { me_graph_free(g); return rc; }
-    }
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        cudaError_t le = launch_search(c, g->dev, g->queue, qcap, n, ntiles, block, algo, max_range, s, cs, ev);
+        cudaError_t le = launch_search(c, g->dev, n, ntiles, block, algo, max_range, s, cs, ev);
         e = cudaStreamEndCapture(cs, &g->graph);
         if (le != cudaSuccess) e = le;
     }
@@ -652,7 +593,6 @@ int host_batch(me_ctx* c, const me_frame_desc* d, const int16_t* const* mv_fs, i
         fsd[i] = (sums && mv_fs && mv_fs[i]) ? reinterpret_cast<const int16_t*>(base + o_fs[i]) : nullptr;
     }
     std::vector<EvalArgs> eas(nchunks);
-    size_t max_chunk_blocks = 0;
     for (int k = 0; k < nchunks; ++k) {
         const int c0 = k * chunk, m = std::min(n, c0 + chunk) - c0;
         eas[k].mv_fs = fsd.data() + c0;
@@ -661,11 +601,6 @@ int host_batch(me_ctx* c, const me_frame_desc* d, const int16_t* const* mv_fs, i
         ntiles[k] = build_table(dd.data() + c0, m, block, s, algo == ME_ALGO_FS, table, &mrange[k],
                                 sums ? &eas[k] : nullptr);
         if (ntiles[k] < 0) return fail(c, ME_ERR_CUDA, "cuTensorMapEncodeTiled rejected a frame description");
-        max_chunk_blocks = std::max(max_chunk_blocks, total_blocks(dd.data() + c0, m, block));
-    }
-    if (algo != ME_ALGO_FS && s.kernel == 1 && !sums) {
-        rc = ensure_queue(c, &slot->queue, &slot->qcap, max_chunk_blocks);
-        if (rc != ME_OK) return rc;
     }
 
     // uploads start once the caller's stream reaches the call and the last
@@ -685,8 +620,8 @@ int host_batch(me_ctx* c, const me_frame_desc* d, const int16_t* const* mv_fs, i
         if (e == cudaSuccess) e = cudaEventRecord(ev_in, P.in);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev_in, 0);
         if (e != cudaSuccess) return cuda_fail(c, e, "host-batch upload");
-        e = launch_search(c, static_cast<char*>(slot->dev) + per * k, slot->queue, slot->qcap, m, ntiles[k], block,
-                          algo, mrange[k], s, st, sums ? &eas[k] : nullptr);
+        e = launch_search(c, static_cast<char*>(slot->dev) + per * k, m, ntiles[k], block, algo, mrange[k], s, st,
+                          sums ? &eas[k] : nullptr);
         if (e != cudaSuccess) return cuda_fail(c, e, "search launch");
         e = cudaEventRecord(ev_run, st);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(P.out, ev_run, 0);
@@ -793,7 +728,6 @@ void me_graph_free(me_graph* g)
     if (g->exec) cudaGraphExecDestroy(g->exec);
     if (g->graph) cudaGraphDestroy(g->graph);
     if (g->dev) cudaFree(g->dev);
-    if (g->queue) cudaFree(g->queue);
     delete g;
 }
 
@@ -932,37 +866,14 @@ int me_tune_batch(me_ctx* c, const me_frame_desc* descs, int n, int block, int a
             }
         }
     } else {
-        for (int th : {512, 384}) {
-            for (int stages : {3, 2}) {
-                Shape s = default_shape(c, algo, block, mr);
-                s.kernel = 2;
-                s.threads = th;
-                s.stages = stages;
-                if (me::dcds_stream_smem_bytes(block, mr, s) <= 227 * 1024) cands.push_back(s);
-            }
-        }
-        for (int aw : {2, 4, 6}) {
-            Shape s = default_shape(c, algo, block, mr);
-            s.kernel = 1;
-            s.threads = 256;
-            s.a_warps = aw;
-            if (me::dcds_ws_smem_bytes(block, mr, s) <= 220 * 1024) cands.push_back(s);
-        }
+        // DCDS: CTA size and tile staging
         for (int th : {128, 256}) {
             for (int stages : {1, 2}) {
                 Shape s = default_shape(c, algo, block, mr);
-                s.kernel = 0;
                 s.threads = th;
                 s.stages = stages;
                 if (me::dcds_smem_bytes(block, mr, s) <= 220 * 1024) cands.push_back(s);
             }
-        }
-        {
-            Shape s = default_shape(c, algo, block, mr);
-            s.kernel = 3;
-            s.threads = 128;
-            s.stages = 2;
-            if (me::dcds_cross_smem_bytes(block, mr, s) <= 220 * 1024) cands.push_back(s);
         }
     }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -998,7 +909,7 @@ int me_tune_batch(me_ctx* c, const me_frame_desc* descs, int n, int block, int a
         std::ofstream f(c->tune_path, std::ios::app);
         const Shape& s = cands[bi];
         f << shape_key(algo, block, mr, mw, mh) << " " << s.tx << " " << s.ty << " " << s.threads << " " << s.k
-          << " " << s.stages << " " << s.kernel << " " << s.a_warps << "\n";
+          << " " << s.stages << "\n";
     }
     if (chosen) *chosen = bi;
     // leave the outputs computed with the chosen shape

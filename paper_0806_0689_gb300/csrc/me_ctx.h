@@ -21,11 +21,9 @@ struct Slot {
     size_t cap = 0;
     cudaEvent_t done = nullptr;
     bool used = false;
-    void* queue = nullptr;  // DCDS item queue: items (16 B each) then flags (4 B each), flags zeroed
-    size_t qcap = 0;        // entries
 };
 
-constexpr size_t kHeadBytes = 256;  // queue head (int) and padding before the table
+constexpr size_t kHeadBytes = 256;  // the kernels' counter words and padding before the table
 
 // Staging of me_estimate_host_batch: two sets of device buffers for a
 // call's frames, FS fields and outputs (consecutive calls alternate, so one
@@ -101,7 +99,6 @@ struct Trace {
 struct me_graph {
     me_ctx* ctx = nullptr;
     void* dev = nullptr;    // [head | table]
-    void* queue = nullptr;  // DCDS item queue (items, then zeroed flags)
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
 };

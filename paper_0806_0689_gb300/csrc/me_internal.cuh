@@ -67,10 +67,7 @@ struct Shape {
     int threads;       // threads per CTA
     int ctas_per_sm;   // persistent grid = ctas_per_sm * SM count (0 = occupancy)
     int k;             // FS: candidate rows per thread
-    int stages;        // DCDS tile-phase kernel: 1 = load each tile when needed, 2 = prefetch
-    int kernel;        // DCDS: 0 = tile-phase (dcds.cu), 1 = warp-specialised (dcds_ws.cu), 2 = streaming (dcds_stream.cu),
-                       //       3 = cross-pass (dcds_cross.cu)
-    int a_warps;       // DCDS warp-specialised: warps per CTA that stage tiles and run step 1
+    int stages;        // DCDS: 1 = load each tile when needed, 2 = prefetch the next tile
 };
 
 // Status bits a kernel may record (read back by me_check_status).
@@ -150,41 +147,15 @@ cudaError_t launch_dcds(const FrameDev* frames, int nframes, int ntiles, int blo
                         cudaStream_t st, bool eval = false);
 size_t dcds_smem_bytes(int block, int max_range, const Shape& s);
 int dcds_ctas_per_sm(int block, int max_range, bool simplified, const Shape& s);
-// Cross-pass DCDS (dcds_cross.cu): the same search as a per-block state
-// machine over 9-point cross passes, two tile stages of kTile x
-// cross_tile_h() pixels per CTA.  head: kCounterInts ints, zeroed before every
-// launch (the tile counter; the last word is the time-out test hook).
-cudaError_t launch_dcds_cross(const FrameDev* frames, int nframes, int ntiles, int block, int max_range,
-                              bool simplified, const Shape& s, int* head, unsigned* status, int num_sms,
-                              cudaStream_t st, bool eval = false);
-size_t dcds_cross_smem_bytes(int block, int max_range, const Shape& s);
-int cross_tile_h();
-cudaError_t dcds_cross_preload();
 // Load (under lazy module loading) the one-stage search-only DCDS kernels
 // for both block sizes and both variants, without launching them.
 cudaError_t dcds_preload();
 // Failure-detection test hook of me_estimate_batch_noalloc (noalloc.cu).
 void noalloc_inject_wait_timeout(int on);
 
-// Warp-specialised DCDS.  counters: kCounterInts ints, zeroed before every
-// launch.  queue: kQueueHeadWords header words (word 0: epoch), then
-// max_items flags (4 B), then max_items items (16 B); all zero when allocated,
-// never reset afterwards; one launch at a time per queue.  max_items must be a
-// multiple of 4 and at least the number of blocks of the batch.
+// DCDS head: kCounterInts ints, zeroed before every launch (word 0: the tile
+// counter; the last word: the failure-detection test hook).
 constexpr int kCounterInts = 8;
-constexpr int kQueueHeadWords = 64;
-inline size_t dcds_queue_bytes(size_t max_items) { return kQueueHeadWords * 4 + max_items * 20; }
-cudaError_t launch_dcds_ws(const FrameDev* frames, int nframes, int ntiles, int block, int max_range,
-                           bool simplified, const Shape& s, int* counters, void* queue, int max_items,
-                           unsigned* status, int num_sms, cudaStream_t st);
-size_t dcds_ws_smem_bytes(int block, int max_range, const Shape& s);
-
-// Streaming DCDS: one CTA per SM, s.stages (2 or 3) resident tiles, s.threads
-// (128..512) threads.  head: the tile counter, zeroed before every launch.
-cudaError_t launch_dcds_stream(const FrameDev* frames, int nframes, int ntiles, int block, int max_range,
-                               bool simplified, const Shape& s, int* head, unsigned* status, int num_sms,
-                               cudaStream_t st);
-size_t dcds_stream_smem_bytes(int block, int max_range, const Shape& s);
 
 // Full search.  counter: one int zeroed before every launch (the tile counter).
 // Shape: threads 256, tx blocks per tile with tx*block <= 256 (tx even for

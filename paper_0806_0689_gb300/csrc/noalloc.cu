@@ -131,7 +131,6 @@ extern "C" int me_estimate_batch_noalloc(const me_frame_desc* d, int n, int bloc
     s.tx = s.ty = me::kTile / block;
     s.k = 0;
     s.stages = 1;
-    s.kernel = 0;  // the tile-phase kernel: it needs no queue beyond the fixed array
     s.ctas_per_sm = 0;
 
     Chunk chunk;

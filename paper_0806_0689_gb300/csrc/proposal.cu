@@ -19,9 +19,10 @@
 // warp waits for those three (acquire loads, bounded), runs the head on the
 // precomputed conv-4 features and the neighbours' MVs, picks the start (argmax
 // of the dx and dy heads, ties to the class nearest the centre) and the prior
-// (V when its logit is larger), and searches: the origin and the start are
-// evaluated, the better one (the origin on a tie) centres the first pattern
-// (the HCSP, or its transpose for a vertical prior), then DCDS steps 2-4.
+// (V when its logit is larger), and searches: the origin, the neighbours'
+// median (learned start only) and the start are evaluated in this order, the
+// best one (the earliest on a tie) centres the first pattern (the HCSP, or
+// its transpose for a vertical prior), then DCDS steps 2-4.
 #include "me.h"
 #include "me_cnn.cuh"
 #include "me_ctx.h"
@@ -541,8 +542,15 @@ __global__ void __launch_bounds__(256) learned_dcds_kernel(const PropFrame* __re
         sy = min(max(sy, b.dylo), b.dyhi);
         // ---- search ----
         int cx = 0, cy = 0;
+        if (LEARNED) {
+            // the neighbours' median (clamped) is evaluated before the network's start
+            const int qx[1] = {min(max(medx, b.dxlo), b.dxhi)}, qy[1] = {min(max(medy, b.dylo), b.dyhi)};
+            uint32_t v[1];
+            const unsigned f = visit_many<B, 1>(b, bm, wmin, wmax, nsp, qx, qy, v, lane);
+            if ((f & 1u) && v[0] < cval) { cx = qx[0]; cy = qy[0]; cval = v[0]; }
+        }
         {
-            // the proposed start (skipped when it is the origin, visited above)
+            // the proposed start (skipped when visited above)
             const int qx[1] = {sx}, qy[1] = {sy};
             uint32_t v[1];
             const unsigned f = visit_many<B, 1>(b, bm, wmin, wmax, nsp, qx, qy, v, lane);

@@ -27,7 +27,7 @@ for name, n, seed in (("qcif", 3, 7001), ("cif", 3, 7002), ("720p", 2, 7003)):
     s = synth.workload_sequence(name, n, seed=seed, max_motion=16)
     cases += [(s[t + 1], s[t]) for t in range(n - 1)]
 runs = 0
-for shape in ("8 8 128 0 1 0 4", "8 8 256 0 2 0 4"):
+for shape in ("8 8 128 0 1", "8 8 256 0 2"):
     for B in (16, 8):
         for algo in ("dcds", "dcds_s"):
             for R in (1, 7, 16, 32):

@@ -155,7 +155,9 @@ def test_wavefront_wait_timeout_reported_then_exact(ctx, B, kind):
                 want = oracle.median_dcds(cur, ref, R, block=B)
                 assert np.array_equal(st[base:base + nb], want[3])
             else:
-                want = oracle.dcds_from_starts(cur, ref, B, R, st[base:base + nb])
+                h, w = cur.shape
+                want = oracle.dcds_from_starts(cur, ref, B, R, st[base:base + nb],
+                                               oracle.region_medians(mv.cpu().numpy(), w, h, B))
             assert np.array_equal(mv.cpu().numpy(), want[0])
             assert np.array_equal(sad.cpu().numpy().view(np.uint32), want[1])
             assert np.array_equal(nsp.cpu().numpy().view(np.uint16), want[2])

@@ -412,27 +412,20 @@ def test_tune_keeps_parity(ctx, cif):
         assert_same(gpu_search(ctx, cur, ref, 16, 7, algo), oracle_search(cur, ref, 16, 7, algo), algo)
 
 
-# launch shapes as the tune cache stores them: tx ty threads k stages kernel a_warps
+# launch shapes as the tune cache stores them: tx ty threads k stages
 DCDS_SHAPES = {
-    "tile128_s1": "8 8 128 0 1 0 4",
-    "tile128_s2": "8 8 128 0 2 0 4",
-    "tile256_s1": "8 8 256 0 1 0 4",
-    "ws256_a2": "8 8 256 0 1 1 2",
-    "ws256_a6": "8 8 256 0 1 1 6",
-    "ws128_a1": "8 8 128 0 1 1 1",
-    "ws128_a4": "8 8 128 0 1 1 4",
-    "stream512_s3": "8 8 512 0 3 2 4",
-    "stream384_s2": "8 8 384 0 2 2 4",
-    "stream128_s3": "8 8 128 0 3 2 4",
-    "cross128": "8 8 128 0 2 3 4",
+    "tile128_s1": "8 8 128 0 1",
+    "tile128_s2": "8 8 128 0 2",
+    "tile256_s1": "8 8 256 0 1",
+    "tile256_s2": "8 8 256 0 2",
 }
 
 
 @pytest.mark.parametrize("shape", sorted(DCDS_SHAPES))
 def test_every_dcds_kernel_shape(tmp_path, cif, shape):
-    """Both DCDS kernels (tile-phase and warp-specialised) in every staging
-    and warp split the tuner may choose give the oracle's results; a shape is
-    forced through the tune cache file of a fresh context."""
+    """The DCDS kernel in every CTA size and tile staging the tuner may
+    choose gives the oracle's results; a shape is forced through the tune
+    cache file of a fresh context."""
     cur, ref = cif[3], cif[2]
     h, w = cur.shape
     cases = [(16, 7, "dcds"), (8, 15, "dcds"), (16, 32, "dcds_s"), (8, 3, "dcds_s")]
@@ -449,7 +442,7 @@ def test_every_dcds_kernel_shape(tmp_path, cif, shape):
         c2.close()
 
 
-@pytest.mark.parametrize("shape", ["ws256_a2", "tile128_s2", "stream512_s3"])
+@pytest.mark.parametrize("shape", ["tile128_s2", "tile256_s1"])
 def test_dcds_shape_graph_replays(tmp_path, qcif, shape):
     """Graph replays of a forced shape: a mixed-size batch, replayed with
     the outputs cleared in between, matches the oracle every time."""

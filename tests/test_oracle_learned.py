@@ -21,13 +21,32 @@ def test_layout():
     assert oracle.cnn_nparams() == P == FB + 68
 
 
-def test_zero_network_reduces_to_dcds():
-    """All logits equal -> start (0,0), horizontal prior -> the paper's DCDS."""
+def _median_h_search(cur, ref, rng, block):
+    """The search from the neighbours' median with a horizontal prior: what
+    the learned start reduces to when the network proposes the origin."""
+    nbx = cur.shape[1] // block
+
+    def propose(m, k0, px, py):
+        mx, my = oracle.neighbour_median(m, k0, nbx)
+        return 0, 0, 0, mx, my
+
+    return oracle._search_regions(cur, ref, rng, block, propose)
+
+
+def test_zero_network_reduces_to_the_median_candidate():
+    """All logits equal -> the network proposes the origin with a horizontal
+    prior, so each block evaluates the origin and the neighbours' median and
+    runs DCDS from the better one; on a frame whose neighbours all rest (a
+    stationary pair) that is exactly the paper's DCDS."""
     seq = synth.workload_sequence("cif", 2, seed=7, max_motion=16)
     mv, sd, ns, st, _ = oracle.learned_dcds(seq[1], seq[0], 16, np.zeros(P))
-    m2, s2, n2 = oracle.dcds(seq[1], seq[0], 16, 16)
-    assert (st == 0).all()
+    m2, s2, n2, st2 = _median_h_search(seq[1], seq[0], 16, 16)
+    assert (st == 0).all() and np.array_equal(st, st2)
     assert np.array_equal(mv, m2) and np.array_equal(sd, s2) and np.array_equal(ns, n2)
+    f = seq[0]
+    mv, sd, ns, st, _ = oracle.learned_dcds(f, f, 7, np.zeros(P))
+    m3, s3, n3 = oracle.dcds(f, f, 16, 7)
+    assert np.array_equal(mv, m3) and np.array_equal(sd, s3) and np.array_equal(ns, n3)
 
 
 def _ideal(mx, my):
@@ -47,6 +66,15 @@ def test_search_from_closed_forms():
     # with the origin start and horizontal prior, the search is the paper's DCDS
     for mx, my in [(3, -2), (-6, 5), (0, 0), (7, 7)]:
         assert oracle.search_from(_ideal(mx, my), 7) == oracle.search(_ideal(mx, my), 7)
+    # the extra candidate comes before the start: a right candidate and a
+    # wrong start cost one point each, then the HCSP around the candidate
+    assert oracle.search_from(_ideal(5, 3), 7, start=(-3, 0), cand=(5, 3)) == (5, 3, 0, 9)
+    # equal distortions: the candidate (earlier) keeps the tie
+    sym = lambda dx, dy: min((dx - 4) ** 2 + dy ** 2, (dx + 4) ** 2 + dy ** 2)
+    assert oracle.search_from(sym, 7, start=(-4, 0), cand=(4, 0))[:2] == (4, 0)
+    assert oracle.search_from(sym, 7, start=(4, 0), cand=(-4, 0))[:2] == (-4, 0)
+    # a candidate equal to the start is evaluated once
+    assert oracle.search_from(_ideal(5, 3), 7, start=(5, 3), cand=(5, 3)) == (5, 3, 0, 8)
 
 
 def test_start_choice_centre_out():
@@ -212,12 +240,13 @@ def test_median_dcds_on_a_global_shift():
 
 # ---------------------------------------------------------------- 8x8 blocks sharing a region's start
 
-def test_zero_network_reduces_to_dcds_8x8():
+def test_zero_network_reduces_to_the_median_candidate_8x8():
     """All logits equal -> every region proposes (0,0) with a horizontal
-    prior, so each of its four 8x8 blocks runs the paper's DCDS."""
+    prior, so each of its four 8x8 blocks evaluates the origin and the
+    region's neighbour median and runs DCDS from the better one."""
     seq = synth.workload_sequence("cif", 2, seed=17, max_motion=16, scale=(6.0, 3.0))
     mv, sd, ns, st, lg = oracle.learned_dcds(seq[1], seq[0], 16, np.zeros(P), block=8)
-    m2, s2, n2 = oracle.dcds(seq[1], seq[0], 8, 16)
+    m2, s2, n2, st2 = _median_h_search(seq[1], seq[0], 16, 8)
     assert (st == 0).all() and lg.shape == (396, 68)
     assert np.array_equal(mv, m2) and np.array_equal(sd, s2) and np.array_equal(ns, n2)
 
@@ -242,9 +271,9 @@ def _median_following_head(alpha=4.0):
 @pytest.mark.parametrize("block", [16, 8])
 def test_median_following_network_gives_the_median_start(block):
     """A hand-set head that outputs the neighbours' median (and an H prior)
-    makes the learned search the search from the median start: the median
-    scalars, the argmax and the sharing of a region's start by its blocks
-    are wired as stated."""
+    makes the learned search the search from the median start, computed here
+    from the neighbours directly: the median scalars, the argmax and the
+    sharing of a region's start by its blocks are wired as stated."""
     seq = synth.workload_sequence("cif", 2, seed=23, max_motion=12, scale=(6.0, 3.0))
     cur, ref = seq[1], seq[0]
     mv, sd, ns, st, _ = oracle.learned_dcds(cur, ref, 16, _median_following_head(), block=block)
@@ -254,7 +283,8 @@ def test_median_following_network_gives_the_median_start(block):
         bx, by = k0 % nbx, k0 // nbx
         cand = [(int(m[ay * nbx + ax][0]), int(m[ay * nbx + ax][1])) if 0 <= ax < nbx and ay >= 0 else (0, 0)
                 for ax, ay in ((bx - 1, by), (bx, by - 1), (bx + 1, by - 1))]
-        return sorted(c[0] for c in cand)[1], sorted(c[1] for c in cand)[1], 0
+        mx, my = sorted(c[0] for c in cand)[1], sorted(c[1] for c in cand)[1]
+        return mx, my, 0, mx, my
 
     m2, s2, n2, st2 = oracle._search_regions(cur, ref, 16, block, propose)
     assert np.array_equal(mv, m2) and np.array_equal(sd, s2) and np.array_equal(ns, n2)
