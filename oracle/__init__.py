@@ -88,7 +88,7 @@ def _load():
             lib.oracle_cnn_features.restype = None
             lib.oracle_cnn_features.argtypes = [P, P, I, I, I, I, I, P, I, P, P]
             lib.oracle_cnn_forward.restype = None
-            lib.oracle_cnn_forward.argtypes = [P, P, P, I, P]
+            lib.oracle_cnn_forward.argtypes = [P, P, P, P]
             lib.oracle_cnn_loss_grad.restype = ctypes.c_double
             lib.oracle_cnn_loss_grad.argtypes = [P, P, P, I, I, I, P]
             _lib = lib
@@ -246,14 +246,12 @@ def cnn_features(cur, ref, px, py, nbr=None, block=16):
     return x, mvf
 
 
-def cnn_forward(params, x, mvf, act_bf16=False):
-    """Logits of one region; act_bf16 rounds every layer's activations to bf16
-    (through fp32) as the deployed network does, otherwise they stay fp64."""
+def cnn_forward(params, x, mvf):
     params = np.ascontiguousarray(params, dtype=np.float64)
     x = np.ascontiguousarray(x, dtype=np.float64)
     mvf = np.ascontiguousarray(mvf, dtype=np.float64)
     out = np.zeros(68, np.float64)
-    _load().oracle_cnn_forward(_ptr(params), _ptr(x), _ptr(mvf), int(bool(act_bf16)), _ptr(out))
+    _load().oracle_cnn_forward(_ptr(params), _ptr(x), _ptr(mvf), _ptr(out))
     return out
 
 
@@ -444,7 +442,7 @@ def cnn_raw_start(logits):
     return centre_out_argmax(logits[:33]), centre_out_argmax(logits[33:66]), int(logits[67] > logits[66])
 
 
-def learned_dcds(cur, ref, rng, params, block=16, act_bf16=False):
+def learned_dcds(cur, ref, rng, params, block=16):
     """Learned-start DCDS of a frame: one proposal per 16x16 region (one
     16x16 block, or four 8x8 blocks that share it), regions in raster order
     so that the left, top and top-right neighbours of a region's top-left
@@ -452,8 +450,7 @@ def learned_dcds(cur, ref, rng, params, block=16, act_bf16=False):
     neighbours' median and the network's start, in this order; the best
     centres the first pattern (HCSP, or its transpose for a vertical prior).
     Returns (mv, sad, nsp, starts, logits), logits per region in raster
-    order. act_bf16 rounds the network's activations to bf16 as cnn_forward
-    does."""
+    order."""
     h, w = np.asarray(cur).shape
     logits = np.zeros(((w // 16) * (h // 16), 68), np.float64)
     count = [0]
@@ -461,7 +458,7 @@ def learned_dcds(cur, ref, rng, params, block=16, act_bf16=False):
 
     def propose(mv, k0, px, py):
         x, mvf = cnn_features(cur, ref, px, py, mv, block)
-        lg = cnn_forward(params, x, mvf, act_bf16)
+        lg = cnn_forward(params, x, mvf)
         logits[count[0]] = lg
         count[0] += 1
         sx, sy, pv = cnn_raw_start(lg)

@@ -29,13 +29,6 @@
  * [32][32][3][3], conv2.b [32], conv3.w, conv3.b, conv4.w, conv4.b,
  * fc.w [68][136], fc.b [68]: 37668 values.
  *
- * Precision: the deployed network multiplies bf16 operands at every layer
- * (weights, and each layer's input activations, rounded once from their fp32
- * value, round to nearest even) and accumulates in fp32.  oracle_cnn_forward
- * accumulates in fp64; with act_bf16 set it rounds each ReLU output to bf16
- * the same way (through fp32), which is the network as deployed; without it
- * the activations stay fp64.  Weights are rounded by the caller.
- *
  * Parity: "parity unpinned" with respect to the paper (the paper has no
  * network).  The functions are pinned mathematically by the tests: finite
  * differences of the loss, impulse responses of the convolution, closed forms
@@ -127,25 +120,6 @@ static void relu(double* v, int n)
     for (int i = 0; i < n; ++i) v[i] = v[i] > 0.0 ? v[i] : 0.0;
 }
 
-/* v rounded to fp32, then to bf16 (8 significant bits), round to nearest,
- * ties to even: the 16 low bits of the fp32 pattern are dropped after adding
- * half an ulp of the kept part (plus one when that part is odd). */
-static double bf16_round(double v)
-{
-    float f = (float)v;
-    uint32_t u;
-    memcpy(&u, &f, 4);
-    u += 0x7FFFu + ((u >> 16) & 1u);
-    u &= 0xFFFF0000u;
-    memcpy(&f, &u, 4);
-    return (double)f;
-}
-
-static void round_bf16(double* v, int n)
-{
-    for (int i = 0; i < n; ++i) v[i] = bf16_round(v[i]);
-}
-
 typedef struct {
     double z1[C * 256], a1[C * 256];
     double z2[C * 64], a2[C * 64];
@@ -155,20 +129,16 @@ typedef struct {
     double logits[NLOGIT];
 } acts_t;
 
-static void forward(const double* p, const double* x, const double* mvf, acts_t* a, int act_bf16)
+static void forward(const double* p, const double* x, const double* mvf, acts_t* a)
 {
     conv_fwd(x, 2, 32, p + P_W1, p + P_B1, a->z1);
     memcpy(a->a1, a->z1, sizeof a->z1); relu(a->a1, C * 256);
-    if (act_bf16) round_bf16(a->a1, C * 256);
     conv_fwd(a->a1, C, 16, p + P_W2, p + P_B2, a->z2);
     memcpy(a->a2, a->z2, sizeof a->z2); relu(a->a2, C * 64);
-    if (act_bf16) round_bf16(a->a2, C * 64);
     conv_fwd(a->a2, C, 8, p + P_W3, p + P_B3, a->z3);
     memcpy(a->a3, a->z3, sizeof a->z3); relu(a->a3, C * 16);
-    if (act_bf16) round_bf16(a->a3, C * 16);
     conv_fwd(a->a3, C, 4, p + P_W4, p + P_B4, a->z4);
     memcpy(a->a4, a->z4, sizeof a->z4); relu(a->a4, C * 4);
-    if (act_bf16) round_bf16(a->a4, C * 4);
     for (int i = 0; i < 128; ++i) a->f[i] = a->a4[i];
     for (int i = 0; i < NSCAL; ++i) a->f[128 + i] = mvf[i];
     for (int o = 0; o < NLOGIT; ++o) {
@@ -178,11 +148,11 @@ static void forward(const double* p, const double* x, const double* mvf, acts_t*
     }
 }
 
-/* Logits of one region (act_bf16: activations rounded as deployed). */
-void oracle_cnn_forward(const double* params, const double* x, const double* mvf, int act_bf16, double* logits)
+/* Logits of one block. */
+void oracle_cnn_forward(const double* params, const double* x, const double* mvf, double* logits)
 {
     acts_t* a = (acts_t*)malloc(sizeof(acts_t));
-    forward(params, x, mvf, a, act_bf16);
+    forward(params, x, mvf, a);
     memcpy(logits, a->logits, sizeof a->logits);
     free(a);
 }
@@ -227,7 +197,7 @@ double oracle_cnn_loss_grad(const double* p, const double* x, const double* mvf,
                             double* grad)
 {
     acts_t* a = (acts_t*)malloc(sizeof(acts_t));
-    forward(p, x, mvf, a, 0);
+    forward(p, x, mvf, a);
     double dz[NLOGIT];
     double loss = xent(a->logits, 33, tdx, dz) + xent(a->logits + 33, 33, tdy, dz + 33) +
                   xent(a->logits + 66, 2, thv, dz + 66);

@@ -123,8 +123,11 @@ __global__ void __launch_bounds__(128) gemm_kernel(const __nv_bfloat16* __restri
 // PXW words so that the 8 output pixels of a fragment, two input pixels
 // apart, fall on 8 different bank groups), B fragments are read from the
 // GEMM-layout weights (L1-resident), bias + ReLU + bf16 rounding happen in
-// the epilogue.  The arithmetic per output is the im2col path's: bf16
-// operands, fp32 accumulation, one bf16 rounding of each activation.
+// the epilogue.  Operands are bf16 and sums fp32; each activation enters the
+// next layer as two bf16 parts (split_relu), both multiplied by the same
+// weights, so the trunk computes the network with bf16 weights and
+// activations of about fp32 precision.  (The training path, on the im2col
+// GEMMs, rounds each activation once to bf16.)
 constexpr int PXW = 18;   // smem words per pixel of a 32-channel activation (16 + 2 padding)
 
 struct TrunkW {
@@ -132,10 +135,20 @@ struct TrunkW {
     const float* b[LAYERS];
 };
 
-__device__ __forceinline__ uint32_t pack_relu(float v0, float v1)
+__device__ __forceinline__ uint32_t bf2_bits(__nv_bfloat162 h) { return *reinterpret_cast<const uint32_t*>(&h); }
+
+// Two ReLU outputs of the inference trunk as a pair of bf16 words, hi + lo:
+// hi is the activation rounded to bf16, lo the remainder rounded to bf16, so
+// that hi + lo carries 16 significant bits and a layer that multiplies both
+// parts by the same bf16 weights sees the fp32 activation to within 2^-17.
+__device__ __forceinline__ void split_relu(float v0, float v1, uint32_t& hi, uint32_t& lo)
 {
-    const __nv_bfloat162 h = __floats2bfloat162_rn(v0 > 0.f ? v0 : 0.f, v1 > 0.f ? v1 : 0.f);
-    return *reinterpret_cast<const uint32_t*>(&h);
+    v0 = v0 > 0.f ? v0 : 0.f;
+    v1 = v1 > 0.f ? v1 : 0.f;
+    const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+    const float2 f = __bfloat1622float2(h);
+    hi = bf2_bits(h);
+    lo = bf2_bits(__floats2bfloat162_rn(v0 - f.x, v1 - f.y));
 }
 
 // Output pixels of a warp's m-tiles: rows g and g + 8 (h = 0, 1) of m-tile i.
@@ -145,17 +158,11 @@ struct Rows {
 };
 
 // One 3x3 stride-2 layer with 32 input channels (implicit GEMM, K = 9 taps x 32)
-// for NM m-tiles and NN n-tiles (from n-tile n0) per warp.
+// for NM m-tiles and NN n-tiles (from n-tile n0) per warp, added to acc.
 template <int HIN, int NM, int NN>
 __device__ __forceinline__ void conv32(const uint32_t* __restrict__ in, const uint32_t* __restrict__ Wl,
                                        const Rows<NM> rw, int n0, float (&acc)[NM][NN][4], int g, int t)
 {
-#pragma unroll
-    for (int i = 0; i < NM; ++i)
-#pragma unroll
-        for (int j = 0; j < NN; ++j)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
 #pragma unroll 1
     for (int tap = 0; tap < 9; ++tap) {
         const int ky = tap / 3, kx = tap - 3 * ky;
@@ -203,8 +210,12 @@ __device__ __forceinline__ int trunk_frame(const PropFrame* fr, int nframes, lon
 
 // ------------------------------------------------------------------ trunk with tcgen05 (inference)
 // Two samples per iteration: their two feature planes are built from the
-// frames straight into shared memory (the features of feat_kernel), then the
-// four layers run back to back.  Layer 2 (64 % of the trunk's multiply-adds)
+// frames straight into shared memory (the features of feat_kernel; values
+// k/128, exact in bf16), then the four layers run back to back, each layer's
+// input as its hi and lo bf16 parts.  Layer 1 runs twice, the first pass
+// writing the hi parts of its output, the second the lo parts, into the same
+// planes; layer 2 accumulates both passes in TMEM.  Layer 2 (64 % of the
+// trunk's multiply-adds)
 // runs on the 5th-generation tensor cores: one thread issues
 // tcgen05.mma (M = 128 rows = 2 samples x 8 x 8 outputs, N = 32, K = 16 per
 // instruction, bf16 x bf16 -> fp32 in TMEM) for the 9 taps x 2 channel
@@ -221,7 +232,9 @@ __device__ __forceinline__ int trunk_frame(const PropFrame* fr, int nframes, lon
 // further (leading byte offset), the next output row of the tile one
 // interleaved line further (stride byte offset).  Layers 1, 3 and 4 stay on
 // mma.sync (K = 18 for layer 1, and too few rows per sample for M = 128 in
-// layers 3-4).
+// layers 3-4).  The layer-2 and layer-3 outputs (hi and lo arrays) reuse the
+// layer-1 planes, dead once the second layer-2 pass has completed; the cells
+// of those planes that are zero padding are cleared again every iteration.
 constexpr int TC_S = 2;                          // samples per iteration (one M = 128 tile in layer 2)
 constexpr int TC_LINE = 9 * 16;                  // bytes per interleaved plane line (9 pixels)
 constexpr int TC_PLANE = 9 * TC_S * TC_LINE;     // 9 rows x 2 samples
@@ -239,17 +252,22 @@ __device__ __forceinline__ uint64_t tc_desc(uint32_t addr, uint32_t lbo, uint32_
            ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
 }
 
+constexpr int TC_A23 = 2 * TC_S * (64 + 16) * PXW;  // words of A2 and A3, hi and lo
+static_assert(TC_A23 * 4 <= TC_A1, "the layer-2/3 outputs fit in the layer-1 planes");
+
 __global__ void __launch_bounds__(256, 3) trunk_tc_kernel(const PropFrame* __restrict__ fr, int nframes, long sbase,
-                                                          int n, TrunkW tw, __nv_bfloat16* __restrict__ a4,
+                                                          int n, TrunkW tw, float* __restrict__ a4,
                                                           unsigned* __restrict__ status)
 {
     extern __shared__ __align__(1024) uint8_t tcs[];
     uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(tcs) + 1023) & ~uintptr_t(1023));
     uint8_t* A1 = base;                                                 // parity-split layer-1 output
     uint8_t* W2c = A1 + TC_A1;                                          // layer-2 weights, core layout
-    uint32_t* A2 = reinterpret_cast<uint32_t*>(W2c + TC_W2);            // [TC_S][8][8][PXW]
-    uint32_t* A3 = A2 + TC_S * 64 * PXW;                                // [TC_S][4][4][PXW]
-    uint32_t* X = A2;                                                   // [TC_S][32][32] words; dead after layer 1
+    uint32_t* X = reinterpret_cast<uint32_t*>(W2c + TC_W2);             // [TC_S][32][32] feature words
+    uint32_t* A2h = reinterpret_cast<uint32_t*>(A1);                    // [TC_S][8][8][PXW], in A1
+    uint32_t* A2l = A2h + TC_S * 64 * PXW;
+    uint32_t* A3h = A2l + TC_S * 64 * PXW;                              // [TC_S][4][4][PXW]
+    uint32_t* A3l = A3h + TC_S * 16 * PXW;
     __shared__ float sb[LAYERS][CH];
     __shared__ int s_fr[TC_S], s_px[TC_S], s_py[TC_S];
     __shared__ __align__(8) uint64_t s_bar;
@@ -314,6 +332,8 @@ __global__ void __launch_bounds__(256, 3) trunk_tc_kernel(const PropFrame* __res
             s_py[tid] = (k / fr[f].nbx) * 16;
         }
         __syncthreads();
+        // the previous iteration's layer-2/3 outputs overwrote padding cells of the planes
+        for (int i = tid; i < TC_A23 / 4; i += blockDim.x) reinterpret_cast<uint4*>(A1)[i] = make_uint4(0u, 0u, 0u, 0u);
         for (int i = tid; i < TC_S * 1024; i += blockDim.x) {
             const int s = i >> 10, pix = i & 1023, yy = pix >> 5, xx = pix & 31;
             uint32_t v = 0u;
@@ -332,71 +352,76 @@ __global__ void __launch_bounds__(256, 3) trunk_tc_kernel(const PropFrame* __res
         }
         __syncthreads();
 
-        // ---- layer 1 (mma.sync): output rows of 16 pixels, written to the parity-split planes ----
-        for (int mt = warp; mt < TC_S * 16; mt += 8) {
-            const int s = mt >> 4, oy = mt & 15;
-            float acc[4][4];
+        // ---- layers 1 and 2, twice: pass 0 feeds layer 2 the hi parts of the
+        // layer-1 output, pass 1 the lo parts, accumulated in the same TMEM tile ----
+        for (int pass = 0; pass < 2; ++pass) {
+            // layer 1 (mma.sync): output rows of 16 pixels, written to the parity-split planes
+            for (int mt = warp; mt < TC_S * 16; mt += 8) {
+                const int s = mt >> 4, oy = mt & 15;
+                float acc[4][4];
 #pragma unroll
-            for (int j = 0; j < 4; ++j)
+                for (int j = 0; j < 4; ++j)
 #pragma unroll
-                for (int q = 0; q < 4; ++q) acc[j][q] = 0.f;
+                    for (int q = 0; q < 4; ++q) acc[j][q] = 0.f;
 #pragma unroll
-            for (int kt = 0; kt < 2; ++kt) {
-                uint32_t a[4];
+                for (int kt = 0; kt < 2; ++kt) {
+                    uint32_t a[4];
 #pragma unroll
-                for (int qq = 0; qq < 4; ++qq) {
-                    const int tap = kt * 8 + t + ((qq & 2) ? 4 : 0);
-                    const int ox = g + ((qq & 1) ? 8 : 0);
-                    uint32_t v = 0u;
-                    if (tap < 9) {
-                        const int y = 2 * oy + tap / 3 - 1, xx = 2 * ox + tap % 3 - 1;
-                        if (y >= 0 && y < 32 && xx >= 0 && xx < 32) v = X[s * 1024 + y * 32 + xx];
+                    for (int qq = 0; qq < 4; ++qq) {
+                        const int tap = kt * 8 + t + ((qq & 2) ? 4 : 0);
+                        const int ox = g + ((qq & 1) ? 8 : 0);
+                        uint32_t v = 0u;
+                        if (tap < 9) {
+                            const int y = 2 * oy + tap / 3 - 1, xx = 2 * ox + tap % 3 - 1;
+                            if (y >= 0 && y < 32 && xx >= 0 && xx < 32) v = X[s * 1024 + y * 32 + xx];
+                        }
+                        a[qq] = v;
                     }
-                    a[qq] = v;
-                }
 #pragma unroll
-                for (int j = 0; j < 4; ++j) mma_bf16(acc[j], a, b1[j][kt]);
+                    for (int j = 0; j < 4; ++j) mma_bf16(acc[j], a, b1[j][kt]);
+                }
+                const int py = oy & 1, yl = (oy + py) >> 1;
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int ox = g + 8 * h, c = j * 8 + 2 * t;
+                        const int px = ox & 1, xl = (ox + px) >> 1;
+                        uint32_t hi, lo;
+                        split_relu(acc[j][2 * h] + sb[0][c], acc[j][2 * h + 1] + sb[0][c + 1], hi, lo);
+                        *reinterpret_cast<uint32_t*>(A1 + j * TC_CG + (py * 2 + px) * TC_PLANE +
+                                                     (yl * TC_S + s) * TC_LINE + xl * 16 + (c & 7) * 2) =
+                            pass ? lo : hi;
+                    }
             }
-            const int py = oy & 1, yl = (oy + py) >> 1;
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int ox = g + 8 * h, c = j * 8 + 2 * t;
-                    const int px = ox & 1, xl = (ox + px) >> 1;
-                    *reinterpret_cast<uint32_t*>(A1 + j * TC_CG + (py * 2 + px) * TC_PLANE + (yl * TC_S + s) * TC_LINE +
-                                                 xl * 16 + (c & 7) * 2) =
-                        pack_relu(acc[j][2 * h] + sb[0][c], acc[j][2 * h + 1] + sb[0][c + 1]);
-                }
-        }
-        // ---- layer 2 (tcgen05): 18 MMAs from the planes, accumulate in TMEM ----
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor-core reads
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (tid == 0) {
-            const uint32_t a_base = tc_smem(A1), b_base = tc_smem(W2c);
+            // layer 2 (tcgen05): 18 MMAs from the planes, accumulated in TMEM
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor-core reads
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncthreads();
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (tid == 0) {
+                const uint32_t a_base = tc_smem(A1), b_base = tc_smem(W2c);
 #pragma unroll 1
-            for (int tap = 0; tap < 9; ++tap) {
-                const int ky = tap / 3, kx = tap - 3 * ky;
-                const int py = ky == 1 ? 0 : 1, yoff = ky == 2 ? 1 : 0;
-                const int px = kx == 1 ? 0 : 1, xoff = kx == 2 ? 1 : 0;
+                for (int tap = 0; tap < 9; ++tap) {
+                    const int ky = tap / 3, kx = tap - 3 * ky;
+                    const int py = ky == 1 ? 0 : 1, yoff = ky == 2 ? 1 : 0;
+                    const int px = kx == 1 ? 0 : 1, xoff = kx == 2 ? 1 : 0;
 #pragma unroll
-                for (int ks = 0; ks < 2; ++ks) {
-                    const uint32_t aa = a_base + (2 * ks) * TC_CG + (py * 2 + px) * TC_PLANE + yoff * TC_S * TC_LINE +
-                                        xoff * 16;
-                    const uint32_t bb = b_base + tap * 2048 + ks * 1024;
-                    const uint64_t ad = tc_desc(aa, TC_CG, TC_LINE), bd = tc_desc(bb, 512, 128);
-                    const uint32_t accum = (tap | ks) ? 1u : 0u;
-                    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
-                                 ::"r"(tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(accum) : "memory");
+                    for (int ks = 0; ks < 2; ++ks) {
+                        const uint32_t aa = a_base + (2 * ks) * TC_CG + (py * 2 + px) * TC_PLANE +
+                                            yoff * TC_S * TC_LINE + xoff * 16;
+                        const uint32_t bb = b_base + tap * 2048 + ks * 1024;
+                        const uint64_t ad = tc_desc(aa, TC_CG, TC_LINE), bd = tc_desc(bb, 512, 128);
+                        const uint32_t accum = (pass | tap | ks) ? 1u : 0u;
+                        asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                                     "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
+                                     ::"r"(tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(accum) : "memory");
+                    }
                 }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                             ::"r"(tc_smem(&s_bar)) : "memory");
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                         ::"r"(tc_smem(&s_bar)) : "memory");
-        }
-        {
+            // every thread waits for the MMAs (and their reads of the planes) to complete
             uint32_t ok = 0;
             for (uint32_t it = 0; it < TC_WAIT && !ok; ++it) {
                 asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -404,34 +429,37 @@ __global__ void __launch_bounds__(256, 3) trunk_tc_kernel(const PropFrame* __res
                              : "=r"(ok) : "r"(tc_smem(&s_bar)), "r"(phase) : "memory");
             }
             phase ^= 1u;
-            if (!__all_sync(0xffffffffu, ok)) {
-                if (lane == 0) atomicOr(&s_fail, 1);
-            } else if (warp < 4) {
-                // warp w reads TMEM lanes 32w .. 32w + 31: row i = (2 * oy + s) * 8 + ox
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                uint32_t v[32];
-                asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-                             "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                             "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                             : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-                               "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
-                               "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),
-                               "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
-                               "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),
-                               "=r"(v[31])
-                             : "r"(tmem + ((uint32_t)(32 * warp) << 16)) : "memory");
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                const int i = 32 * warp + lane;
-                const int oy = i >> 4, s = (i >> 3) & 1, ox = i & 7;
-                uint32_t* dst = A2 + ((s * 8 + oy) * 8 + ox) * PXW;
+            if (!__all_sync(0xffffffffu, ok) && lane == 0) atomicOr(&s_fail, 1);
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncthreads();
+            if (s_fail) break;
+        }
+        if (s_fail) break;
+        // ---- layer-2 epilogue: warp w reads TMEM lanes 32w .. 32w + 31, row i = (2 * oy + s) * 8 + ox ----
+        if (warp < 4) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            uint32_t v[32];
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                         "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                         "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                         : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                           "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+                           "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),
+                           "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+                           "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),
+                           "=r"(v[31])
+                         : "r"(tmem + ((uint32_t)(32 * warp) << 16)) : "memory");
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            const int i = 32 * warp + lane;
+            const int oy = i >> 4, s = (i >> 3) & 1, ox = i & 7;
+            const int o = ((s * 8 + oy) * 8 + ox) * PXW;
 #pragma unroll
-                for (int c = 0; c < 32; c += 2)
-                    dst[c >> 1] = pack_relu(__uint_as_float(v[c]) + sb[1][c], __uint_as_float(v[c + 1]) + sb[1][c + 1]);
-            }
+            for (int c = 0; c < 32; c += 2)
+                split_relu(__uint_as_float(v[c]) + sb[1][c], __uint_as_float(v[c + 1]) + sb[1][c + 1],
+                           A2h[o + (c >> 1)], A2l[o + (c >> 1)]);
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
-        if (s_fail) break;
 
         // ---- layer 3 (mma.sync): m-tile = one sample; warp = (sample, n-tile) ----
         {
@@ -443,18 +471,19 @@ __global__ void __launch_bounds__(256, 3) trunk_tc_kernel(const PropFrame* __res
                 rw.oy[0][h] = (g >> 2) + 2 * h;
                 rw.ox[0][h] = g & 3;
             }
-            float acc[1][1][4];
-            conv32<8, 1, 1>(A2, W3, rw, nt, acc, g, t);
+            float acc[1][1][4] = {};
+            conv32<8, 1, 1>(A2h, W3, rw, nt, acc, g, t);
+            conv32<8, 1, 1>(A2l, W3, rw, nt, acc, g, t);
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int c = nt * 8 + 2 * t;
-                A3[((s * 4 + rw.oy[0][h]) * 4 + rw.ox[0][h]) * PXW + nt * 4 + t] =
-                    pack_relu(acc[0][0][2 * h] + sb[2][c], acc[0][0][2 * h + 1] + sb[2][c + 1]);
+                const int o = ((s * 4 + rw.oy[0][h]) * 4 + rw.ox[0][h]) * PXW + nt * 4 + t;
+                split_relu(acc[0][0][2 * h] + sb[2][c], acc[0][0][2 * h + 1] + sb[2][c + 1], A3h[o], A3l[o]);
             }
         }
         __syncthreads();
 
-        // ---- layer 4 (mma.sync): rows 4 * sample + pixel (rows 8-15 are padding) ----
+        // ---- layer 4 (mma.sync): rows 4 * sample + pixel (rows 8-15 are padding); fp32 out ----
         if (warp < 4) {
             Rows<1> rw;
 #pragma unroll
@@ -463,14 +492,17 @@ __global__ void __launch_bounds__(256, 3) trunk_tc_kernel(const PropFrame* __res
                 rw.oy[0][h] = (g & 3) >> 1;
                 rw.ox[0][h] = g & 1;
             }
-            float acc[1][1][4];
-            conv32<4, 1, 1>(A3, W4, rw, warp, acc, g, t);
+            float acc[1][1][4] = {};
+            conv32<4, 1, 1>(A3h, W4, rw, warp, acc, g, t);
+            conv32<4, 1, 1>(A3l, W4, rw, warp, acc, g, t);
             const int s = g >> 2, pix = g & 3, c = warp * 8 + 2 * t;
             if (s < ns) {
-                const uint32_t v = pack_relu(acc[0][0][0] + sb[3][c], acc[0][0][1] + sb[3][c + 1]);
-                *reinterpret_cast<uint32_t*>(a4 + ((size_t)(s0 + s) * 4 + pix) * CH + c) = v;
+                const float z0 = acc[0][0][0] + sb[3][c], z1 = acc[0][0][1] + sb[3][c + 1];
+                *reinterpret_cast<float2*>(a4 + ((size_t)(s0 + s) * 4 + pix) * CH + c) =
+                    make_float2(z0 > 0.f ? z0 : 0.f, z1 > 0.f ? z1 : 0.f);
             }
         }
+        // the next iteration clears the planes these layers used only after its first barrier
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -587,8 +619,13 @@ __global__ void relu_back_kernel(const float* __restrict__ da, const __nv_bfloat
 
 // ------------------------------------------------------------------ head
 // f[s][i]: the 128 conv-4 features in (c, y, x) order from NHWC [2][2][32],
-// then the 6 scalars; logits[s][o] = fb[o] + sum_i fw[o][i] f[s][i]
-__global__ void head_fwd_kernel(const __nv_bfloat16* __restrict__ a4, const float* __restrict__ mvf, int n,
+// then the NSCAL scalars; logits[s][o] = fb[o] + sum_i fw[o][i] f[s][i].  The
+// features are bf16 (training forward) or fp32 (inference trunk).
+__device__ __forceinline__ float feat(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float feat(float v) { return v; }
+
+template <typename T>
+__global__ void head_fwd_kernel(const T* __restrict__ a4, const float* __restrict__ mvf, int n,
                                 const float* __restrict__ fw, const float* __restrict__ fb,
                                 float* __restrict__ logits)
 {
@@ -599,7 +636,7 @@ __global__ void head_fwd_kernel(const __nv_bfloat16* __restrict__ a4, const floa
         const float* w = fw + (size_t)o * NFEAT;
         float acc = fb[o];
         for (int c = 0; c < 32; ++c)
-            for (int p = 0; p < 4; ++p) acc += w[c * 4 + p] * __bfloat162float(a4[s * 128 + p * 32 + c]);
+            for (int p = 0; p < 4; ++p) acc += w[c * 4 + p] * feat(a4[s * 128 + p * 32 + c]);
         for (int q = 0; q < NSCAL; ++q) acc += w[128 + q] * mvf[s * NSCAL + q];
         logits[i] = acc;
     }
@@ -780,13 +817,12 @@ cudaError_t relu_back(const float* da, const __nv_bfloat16* a, long rows, __nv_b
 
 size_t trunk_tc_smem_bytes()
 {
-    return 1024 + (size_t)TC_A1 + TC_W2 + sizeof(uint32_t) * (size_t)TC_S * (64 + 16) * PXW;
+    return 1024 + (size_t)TC_A1 + TC_W2 + sizeof(uint32_t) * (size_t)TC_S * 1024;
 }
 
 cudaError_t trunk_tc(const PropFrame* frames, int nframes, long sbase, int n, const __nv_bfloat16* const* w,
-                     const float* params, __nv_bfloat16* a4, unsigned* status, int num_sms, cudaStream_t st)
+                     const float* params, float* a4, unsigned* status, int num_sms, cudaStream_t st)
 {
-    static_assert(TC_S * 1024 <= TC_S * (64 + 16) * PXW, "the feature planes fit in the layer-2/3 buffers");
     TrunkW tw;
     for (int l = 0; l < LAYERS; ++l) {
         tw.w[l] = w[l];
@@ -803,6 +839,13 @@ cudaError_t trunk_tc(const PropFrame* frames, int nframes, long sbase, int n, co
 
 cudaError_t head_fwd(const __nv_bfloat16* a4, const float* mvf, int n, const float* fw, const float* fb,
                      float* logits, cudaStream_t st)
+{
+    head_fwd_kernel<<<blocks_for((long)n * NLOGIT), 256, 0, st>>>(a4, mvf, n, fw, fb, logits);
+    return cudaGetLastError();
+}
+
+cudaError_t head_fwd(const float* a4, const float* mvf, int n, const float* fw, const float* fb, float* logits,
+                     cudaStream_t st)
 {
     head_fwd_kernel<<<blocks_for((long)n * NLOGIT), 256, 0, st>>>(a4, mvf, n, fw, fb, logits);
     return cudaGetLastError();

@@ -51,6 +51,8 @@ cudaError_t relu_back(const float* da, const __nv_bfloat16* a, long rows, __nv_b
                       float* partial, cudaStream_t st);
 cudaError_t head_fwd(const __nv_bfloat16* a4, const float* mvf, int n, const float* fw, const float* fb,
                      float* logits, cudaStream_t st);
+cudaError_t head_fwd(const float* a4, const float* mvf, int n, const float* fw, const float* fb, float* logits,
+                     cudaStream_t st);
 cudaError_t loss(const float* logits, const int* labels, int n, float scale, float* dlogits, double* loss_sum,
                  double* partial, cudaStream_t st);
 cudaError_t head_bwd(const float* dlogits, const __nv_bfloat16* a4, const float* mvf, int n, const float* fw,
@@ -80,12 +82,13 @@ struct PropFrame {
 // Inference trunk for the n blocks sbase .. sbase + n - 1 of the frame table
 // (blocks numbered through the frames' bases): features from the frames, then
 // the four layers (layer 2 on tcgen05 with TMEM accumulators, layers 1, 3 and
-// 4 on mma.sync), writing conv-4 activations a4 ([n][2][2][32] bf16) in one
-// launch (no im2col).  w: the four GEMM-layout weights [32][KP[l]]; params:
+// 4 on mma.sync; bf16 weights, each activation carried as two bf16 parts),
+// writing conv-4 activations a4 ([n][2][2][32] fp32) in one launch (no
+// im2col).  w: the four GEMM-layout weights [32][KP[l]]; params:
 // canonical parameters (biases at PB[l]); status (nullable) receives bit 1 if
 // the bounded wait for the tensor cores gave up.
 cudaError_t trunk_tc(const PropFrame* frames, int nframes, long sbase, int n, const __nv_bfloat16* const* w,
-                     const float* params, __nv_bfloat16* a4, unsigned* status, int num_sms, cudaStream_t st);
+                     const float* params, float* a4, unsigned* status, int num_sms, cudaStream_t st);
 
 }  // namespace cnn
 }  // namespace me

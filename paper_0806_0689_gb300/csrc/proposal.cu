@@ -140,7 +140,7 @@ __global__ void mvf_kernel(const PropFrame* __restrict__ fr, int nframes, long s
     }
 }
 
-// features of samples [s0, s0 + n): x NHWC [n][32][32][2] bf16, mvf [n][6], labels [n][3]
+// features of samples [s0, s0 + n): x NHWC [n][32][32][2] bf16, mvf [n][NSCAL], labels [n][3]
 __global__ void feat_kernel(const PropFrame* __restrict__ fr, int nframes, long s0, int n,
                             __nv_bfloat16* __restrict__ x, float* __restrict__ mvf, int* __restrict__ labels)
 {
@@ -320,7 +320,7 @@ __device__ __forceinline__ unsigned visit_many(const WarpBlock& b, uint32_t* bm,
 // the features of 32 samples per step; thread (o, q) accumulates output o of
 // samples q, q + 4, ..., in the same order as the head kernel.
 constexpr int kZS = 32;  // samples per step
-__global__ void __launch_bounds__(4 * NLOGIT) zpart_kernel(const __nv_bfloat16* __restrict__ a4, long total,
+__global__ void __launch_bounds__(4 * NLOGIT) zpart_kernel(const float* __restrict__ a4, long total,
                                                            const float* __restrict__ fw,
                                                            const float* __restrict__ fb, float* __restrict__ zpart)
 {
@@ -336,7 +336,7 @@ __global__ void __launch_bounds__(4 * NLOGIT) zpart_kernel(const __nv_bfloat16* 
         __syncthreads();  // wT ready; the previous step's reads of af are done
         for (int i = tid; i < kZS * 128; i += blockDim.x) {
             const int ss = i >> 7, f = i & 127;
-            af[ss][f] = (s0 + ss < total) ? __bfloat162float(a4[(size_t)(s0 + ss) * 128 + (f & 3) * 32 + (f >> 2)]) : 0.f;
+            af[ss][f] = (s0 + ss < total) ? a4[(size_t)(s0 + ss) * 128 + (f & 3) * 32 + (f >> 2)] : 0.f;
         }
         __syncthreads();
         float acc[kZS / 4];
@@ -622,7 +622,7 @@ inline int nblk(long n, int per = 256, int cap = 4096)
 // ------------------------------------------------------------------ workspace
 struct Ws {
     __nv_bfloat16 *x, *cols[LAYERS], *a[LAYERS], *dz, *dzT, *colsT, *wT;
-    float *mvf, *logits, *dlogits, *da, *dcols, *gw, *part, *bpart;
+    float *a4f, *mvf, *logits, *dlogits, *da, *dcols, *gw, *part, *bpart;
     int* labels;
     double *loss_sum, *lpart;
 };
@@ -640,11 +640,12 @@ size_t ws_layout(uint8_t* base, int n, bool train, Ws* w)
     w->mvf = (float*)take(N * NSCAL * 4);
     w->labels = (int*)take(N * 3 * 4);
     for (int l = 0; l < LAYERS; ++l) {
-        // inference runs the fused trunk: no im2col buffers, only the conv-4 activations
+        // inference runs the fused trunk: no im2col buffers, only the fp32 conv-4 activations
         const size_t ho = HIN[l] / 2;
         w->cols[l] = train ? (__nv_bfloat16*)take(N * ho * ho * KP[l] * 2) : nullptr;
-        w->a[l] = (train || l == LAYERS - 1) ? (__nv_bfloat16*)take(N * ho * ho * CH * 2) : nullptr;
+        w->a[l] = train ? (__nv_bfloat16*)take(N * ho * ho * CH * 2) : nullptr;
     }
+    w->a4f = train ? nullptr : (float*)take(N * 128 * 4);
     w->logits = (float*)take(N * NLOGIT * 4);
     w->dlogits = (float*)take(N * NLOGIT * 4);
     w->loss_sum = (double*)take(8);
@@ -752,7 +753,7 @@ cudaError_t forward(me_proposal* P, const Ws& w, int n, bool head, cudaStream_t 
 
 // inference: the fused trunk writes the conv-4 activations of blocks
 // [s0, s0 + n) to a4 (then the head, whose neighbour scalars are in w.mvf)
-cudaError_t forward_infer(me_proposal* P, int nframes, long s0, const Ws& w, int n, __nv_bfloat16* a4, bool head,
+cudaError_t forward_infer(me_proposal* P, int nframes, long s0, const Ws& w, int n, float* a4, bool head,
                           cudaStream_t st)
 {
     cudaError_t e = trunk_tc(P->frames, nframes, s0, n, P->w, P->p, a4, P->ctx->status, P->ctx->num_sms, st);
@@ -1036,7 +1037,7 @@ int me_proposal_logits(me_ctx* c, me_proposal* P, const me_frame_desc* d, float*
         if (rc != ME_OK) return rc;
         mvf_kernel<<<nblk(ns), 256, 0, st>>>(P->frames, 1, s0, ns, w.mvf);
         cudaError_t e = cudaGetLastError();
-        if (e == cudaSuccess) e = forward_infer(P, 1, s0, w, ns, w.a[3], true, st);
+        if (e == cudaSuccess) e = forward_infer(P, 1, s0, w, ns, w.a4f, true, st);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(logits + s0 * NLOGIT, w.logits, sizeof(float) * ns * NLOGIT, cudaMemcpyDeviceToDevice, st);
         if (e != cudaSuccess) return cuda_fail(c, e, "me_proposal_logits");
@@ -1069,7 +1070,7 @@ int wavefront_batch(me_ctx* c, me_proposal* P, const me_frame_desc* d, int n, in
     // done flags per search block, the counter
     Ws w;
     const size_t trunk = ws_layout(nullptr, kChunk, false, &w);
-    const size_t need = al(trunk) + al((size_t)regions * 128 * 2) + al((size_t)total * 8) + 256 +
+    const size_t need = al(trunk) + al((size_t)regions * 128 * 4) + al((size_t)total * 8) + 256 +
                         al((size_t)regions * NLOGIT * 4);
     if (P->ws_cap < need) {
         cudaFree(P->ws);
@@ -1079,8 +1080,8 @@ int wavefront_batch(me_ctx* c, me_proposal* P, const me_frame_desc* d, int n, in
         P->ws_cap = need;
     }
     ws_layout(P->ws, kChunk, false, &w);
-    __nv_bfloat16* a4all = reinterpret_cast<__nv_bfloat16*>(P->ws + al(trunk));
-    uint8_t* flags = P->ws + al(trunk) + al((size_t)regions * 128 * 2);
+    float* a4all = reinterpret_cast<float*>(P->ws + al(trunk));
+    uint8_t* flags = P->ws + al(trunk) + al((size_t)regions * 128 * 4);
     unsigned long long* done = reinterpret_cast<unsigned long long*>(flags);  // per block: done bit << 32 | MV
     int* counter = reinterpret_cast<int*>(flags + al((size_t)total * 8));
     float* zpart = reinterpret_cast<float*>(flags + al((size_t)total * 8) + 256);

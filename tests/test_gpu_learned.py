@@ -71,6 +71,7 @@ def test_logits_match_oracle(ctx):
             x, mvf = oracle.cnn_features(cur, ref, (k % nbx) * 16, (k // nbx) * 16, field)
             want = oracle.cnn_forward(pref, x, mvf)
             worst = max(worst, float(np.abs(got[k] - want).max()))
+        print(f"untrained logits: largest difference from the oracle {worst:.2e}")
         assert worst < 1e-2, worst
     finally:
         ctx.me_proposal_free(prop)
@@ -133,7 +134,7 @@ def _learned(ctx, prop, pairs, R, B=16):
     return outs, starts.cpu().numpy()
 
 
-def _check_proposals(cur, ref, B, R, mv, st, pref, act_bf16=False):
+def _check_proposals(cur, ref, B, R, mv, st, pref):
     """The GPU's per-block starts against the oracle network on the GPU's own
     final field: every 16x16 region's start (clamped per block) must match,
     except at near-ties (top-2 logit gap < 1e-2).  Returns (regions checked,
@@ -146,7 +147,7 @@ def _check_proposals(cur, ref, B, R, mv, st, pref, act_bf16=False):
         for rx in range(w // 16):
             k0 = (ry * per) * nbx + rx * per
             x, mvf = oracle.cnn_features(cur, ref, rx * 16, ry * 16, mv, B)
-            lg = oracle.cnn_forward(pref, x, mvf, act_bf16)
+            lg = oracle.cnn_forward(pref, x, mvf)
             checked += 1
             gaps = [np.diff(np.sort(seg)[-2:])[0] for seg in (lg[:33], lg[33:66], lg[66:])]
             if min(gaps) < 1e-2:
@@ -333,13 +334,12 @@ def test_training_gain(ctx):
     """The learned-proposal workload: trained on full-search fields of 2,000
     synthetic CIF pairs (seeds >= 100000; half with the motion scales 2/1,
     half 6/3) by me_proposal_train, the network then
-    (1) gives logits within 1e-2 of the oracle network as deployed (bf16
-        trained weights, activations rounded to bf16 at every layer, fp64
-        sums) for every block of held-out pairs; the distance to the
-        all-fp64 activations is printed, not bounded: trained weights are
-        large enough that bf16 activations move logits by ~0.1,
+    (1) gives logits within 1e-2 of the fp64 oracle on the bf16-rounded
+        trained weights for every block of held-out pairs (the trunk carries
+        each activation as two bf16 parts; rounding activations once to bf16
+        would move these logits by ~0.1),
     (2) proposes the oracle network's starts except at near-ties (top-2 logit
-        gap < 1e-2), which stay rare,
+        gap < 1e-2), which stay under 2 % of the regions,
     (3) lowers the search points per block below both plain DCDS and the
         neighbour-median control at a PSNR within 0.05 dB of the control's
         (held-out CIF pairs with large motion)."""
@@ -365,7 +365,7 @@ def test_training_gain(ctx):
         del keep, items, descs
         pref = bf16_conv(ctx.me_proposal_get_params(prop).astype(np.float64))
         # (1) logits of every block of two held-out pairs, neighbours from their FS fields
-        worst = worst64 = 0.0
+        worst = 0.0
         for sd in (5020, 5021):
             s = synth.workload_sequence("cif", 2, seed=sd, scale=(6.0, 3.0), max_motion=16)
             cur, ref = s[1], s[0]
@@ -379,10 +379,8 @@ def test_training_gain(ctx):
             nbx = cur.shape[1] // 16
             for k in range(nb):
                 x, mvf = oracle.cnn_features(cur, ref, (k % nbx) * 16, (k // nbx) * 16, field)
-                worst = max(worst, float(np.abs(got[k] - oracle.cnn_forward(pref, x, mvf, True)).max()))
-                worst64 = max(worst64, float(np.abs(got[k] - oracle.cnn_forward(pref, x, mvf)).max()))
-        print(f"trained logits: largest difference from the oracle {worst:.2e} "
-              f"(from fp64 activations {worst64:.2e})")
+                worst = max(worst, float(np.abs(got[k] - oracle.cnn_forward(pref, x, mvf)).max()))
+        print(f"trained logits: largest difference from the oracle {worst:.2e}")
         assert worst < 1e-2, worst
         # (2) and (3) on held-out pairs with large motion
         test = []
@@ -400,13 +398,13 @@ def test_training_gain(ctx):
             h, w = cur.shape
             m2, s2, n2 = oracle.dcds_from_starts(cur, ref, 16, 16, st, oracle.region_medians(mv, w, h, 16))
             assert np.array_equal(mv, m2) and np.array_equal(sad, s2) and np.array_equal(nsp, n2)
-            c_, k_ = _check_proposals(cur, ref, 16, 16, mv, st, pref, act_bf16=True)
+            c_, k_ = _check_proposals(cur, ref, 16, 16, mv, st, pref)
             checked += c_
             skipped += k_
             nsp_l.append(nsp.mean())
             ps_l.append(oracle.evaluate(cur, ref, 16, mv)["psnr"])
         print(f"trained proposals: {skipped} of {checked} regions skipped as near-ties")
-        assert skipped <= 0.05 * checked, (skipped, checked)
+        assert skipped <= 0.02 * checked, (skipped, checked)
         nsp_m, ps_m, nsp_d, ps_d = [], [], [], []
         for cur, ref in test:
             m, _, n, _ = oracle.median_dcds(cur, ref, 16)

@@ -173,29 +173,6 @@ def test_conv_impulse_response(tap):
     assert lg2[7] == 0.5 and lg2[9] == 1.5
 
 
-def test_bf16_activation_rounding():
-    """act_bf16 rounds every layer's ReLU output to bf16 (8 significant bits,
-    nearest, ties to even).  With one-hot centre taps the impulse passes the
-    four layers unchanged, so the logit is the pixel value rounded once (the
-    rounding is idempotent): exact bf16 values pass, a value halfway between
-    two bf16 neighbours goes to the one with the even last bit, anything past
-    halfway goes up; without act_bf16 the value passes exactly."""
-    p = np.zeros(P)
-    p[W1 + 4] = 1.0
-    for w0 in (W2, W3, W4):
-        p[w0 + 4] = 1.0
-    p[FW + 5 * NF + 3] = 1.0
-    u = 2.0 ** -8  # half an ulp of bf16 at 1
-    cases = [(0.75, 0.75), (1 + 2 * u, 1 + 2 * u), (1 + u, 1.0), (1 + 3 * u, 1 + 4 * u),
-             (1 + u + 2.0 ** -20, 1 + 2 * u), (1 + u - 2.0 ** -20, 1.0), (0.1, 0.10009765625),
-             (-0.5, 0.0)]
-    for v, want in cases:
-        x = np.zeros((2, 32, 32))
-        x[0, 16, 16] = v
-        assert oracle.cnn_forward(p, x, np.zeros(8), act_bf16=True)[5] == want, v
-        assert oracle.cnn_forward(p, x, np.zeros(8))[5] == max(v, 0.0), v
-
-
 def test_gradient_finite_differences():
     rng = np.random.default_rng(3)
     p = rng.normal(0.0, 0.1, P)
