@@ -97,15 +97,35 @@ __device__ __forceinline__ uint32_t ld_word(const uint8_t* p, const Region& g)
     return *reinterpret_cast<const uint32_t*>(p);
 }
 
-// Sec. IV measures of one finished block into the thread's sums.
-// SADs of NP candidates (slots i0 .. i0 + NP - 1 of qx / qy) of a 4-lane group:
-// lane l4 holds RPL rows of one 4-byte column of the block (cb); the loads of
-// all NP points are issued together, then each sum is completed across the
-// group (every lane of the warp takes part in the shuffles).
-template <int NP, int V, int RPL>
+// Lanes of a phase-B group: a block of B x B pixels (B / 4 words per row) is
+// split over LPB lanes, each holding CPL adjacent word columns of RPL rows
+// (first column col0, first row row0 of the block).
+// Lanes per block in the diamond rounds (phase B).  Measured on the 1080p
+// batch (16x16, +-16) and the 2160p 8x8 +-32 batch: 16x16 with 2 lanes 5 %
+// faster than with 4 for the search alone, the same with the evaluation
+// fused; 8x8 with 2 or 1 lanes 23 % and 35 % slower (the per-group bitmaps
+// cost CTAs per SM).
+__host__ __device__ constexpr int dcds_lanes_per_block(int block) { return block == 16 ? 2 : 4; }
+
+template <int B, int LPB>
+struct GroupMap {
+    static constexpr int WPB = B / 4;
+    static constexpr int CPL = WPB >= LPB ? WPB / LPB : 1;
+    static constexpr int RPL = WPB >= LPB ? B : B * WPB / LPB;
+    __device__ static int col0(int lg) { return WPB >= LPB ? lg * CPL : lg % WPB; }
+    __device__ static int row0(int lg) { return WPB >= LPB ? 0 : (lg / WPB) * RPL; }
+};
+
+// SADs of NP candidates (slots i0 .. i0 + NP - 1 of qx / qy; only those below
+// nvalid are loaded, so groups with fewer candidates add no shared-memory
+// traffic) of an LPB-lane group.  Per row a lane loads the CPL + 1 aligned
+// words that cover its CPL unaligned ones; the loads of all NP points are
+// issued together, then each sum is completed across the group (every lane
+// of the warp takes part in the shuffles).
+template <int NP, int V, int RPL, int CPL, int LPB>
 __device__ __forceinline__ void eval_points(const uint8_t* win, int WP, int wx0, int wy0, const int (&qx)[4],
-                                            const int (&qy)[4], const uint32_t (&cb)[RPL], uint32_t (&sad)[4], int i0,
-                                            const Region& gw)
+                                            const int (&qy)[4], const uint32_t (&cb)[RPL][CPL],
+                                            uint32_t (&sad)[4], int i0, int nvalid, const Region& gw)
 {
     const uint8_t* p[NP];
     unsigned sh[NP];
@@ -121,15 +141,19 @@ __device__ __forceinline__ void eval_points(const uint8_t* win, int WP, int wx0,
     for (int r = 0; r < RPL; ++r) {
 #pragma unroll
         for (int k = 0; k < NP; ++k) {
-            const uint32_t l = ld_word(p[k] + r * WP, gw);
-            const uint32_t h = ld_word(p[k] + r * WP + 4, gw);
-            a[k] = sadacc<V>(__funnelshift_r(l, h, sh[k]), cb[r], a[k]);
+            if (i0 + k < nvalid) {
+                uint32_t w[CPL + 1];
+#pragma unroll
+                for (int j = 0; j <= CPL; ++j) w[j] = ld_word(p[k] + r * WP + 4 * j, gw);
+#pragma unroll
+                for (int j = 0; j < CPL; ++j) a[k] = sadacc<V>(__funnelshift_r(w[j], w[j + 1], sh[k]), cb[r][j], a[k]);
+            }
         }
     }
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
-        a[k] += __shfl_xor_sync(0xffffffffu, a[k], 1);
-        a[k] += __shfl_xor_sync(0xffffffffu, a[k], 2);
+#pragma unroll
+        for (int o = 1; o < LPB; o <<= 1) a[k] += __shfl_xor_sync(0xffffffffu, a[k], o);
         sad[i0 + k] = a[k];
     }
 }
@@ -158,11 +182,16 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
                                                    unsigned* __restrict__ status)
 {
     constexpr int V = kSadVariant;
+    constexpr int TH = kDcdsTileH;        // tile height in pixels (width kTile)
     constexpr int TXB = kTile / B;        // blocks per tile row
-    constexpr int NMB = TXB * TXB;        // blocks per tile
+    constexpr int TYB = TH / B;           // block rows per tile
+    constexpr int NMB = TXB * TYB;        // blocks per tile
     constexpr int GA = B / 4;             // phase-A lanes per block
     constexpr int WPB = B / 4;            // 4-byte words per block row
-    constexpr int RPL = B * WPB / 4;      // phase-B rows per lane (4 lanes per block)
+    constexpr int RPL = B * WPB / 4;      // phase-C rows per lane (4 lanes per block)
+    constexpr int LPB = dcds_lanes_per_block(B);  // phase-B lanes per block
+    using GM = GroupMap<B, LPB>;
+    constexpr int RPLB = GM::RPL, CPL = GM::CPL;
     constexpr unsigned FULL = 0xffffffffu;
 
     extern __shared__ uint8_t smem_raw[];
@@ -171,17 +200,17 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
     __shared__ int s_ring_n, s_ring_next;
 
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-    const int cur_off = win_bytes_max(max_range);
-    const int stage_bytes = cur_off + kTile * kTile;
+    const int cur_off = win_bytes_max(max_range, TH);
+    const int stage_bytes = cur_off + kTile * TH;
     uint2* ring = reinterpret_cast<uint2*>(smem + NST * stage_bytes);
     const int side_max = 2 * max_range + 1;
     const int nwb = (side_max * side_max + 31) / 32;
     uint32_t* bm_all = reinterpret_cast<uint32_t*>(ring + NMB);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
-    const int ngroups = blockDim.x >> 2;
+    const int ngroups = blockDim.x >> 2;  // phase-C groups (4 lanes per block)
 
-    for (int i = tid; i < ngroups * nwb; i += blockDim.x) bm_all[i] = 0u;
+    for (int i = tid; i < (int)(blockDim.x / LPB) * nwb; i += blockDim.x) bm_all[i] = 0u;
     // failure-detection test hook (last counter word, zero unless the host set it):
     // the first copy is armed for 16 bytes it never receives and the waits are shortened
     const bool starve = head[kCounterInts - 1] != 0;
@@ -191,7 +220,7 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
     if (tid == 0) {
         for (int s = 0; s < NST; ++s) mbar_init(&s_bar[s], 1);
         fence_mbar_init();
-        issue_tile(atomicAdd(head, 1), frames, nframes, ntiles, smem, cur_off, &s_bar[0], &s_tile[0], &s_frame[0],
+        issue_tile(atomicAdd(head, 1), frames, nframes, ntiles, smem, cur_off, TH, &s_bar[0], &s_tile[0], &s_frame[0],
                    starve ? 16u : 0u);
     }
     __syncthreads();
@@ -213,7 +242,7 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
         if (NST == 2 && tid == 0) {
             // stage st^1 was last read in the previous tile, which ended with a barrier
             fence_proxy_async();
-            issue_tile(atomicAdd(head, 1), frames, nframes, ntiles, smem + (st ^ 1) * stage_bytes, cur_off,
+            issue_tile(atomicAdd(head, 1), frames, nframes, ntiles, smem + (st ^ 1) * stage_bytes, cur_off, TH,
                        &s_bar[st ^ 1], &s_tile[st ^ 1], &s_frame[st ^ 1]);
         }
         // descriptor fields in registers: the output stores below cannot alias them
@@ -226,13 +255,13 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
         const int lt = t - Fp->tile_base;
         const int txs = Fp->tiles_x;
         const int tile_y = lt / txs, tile_x = lt - tile_y * txs;
-        const int bx0 = tile_x * TXB, by0 = tile_y * TXB;
+        const int bx0 = tile_x * TXB, by0 = tile_y * TYB;
         const int rx = (R + 15) & ~15;
         const int WP = kTile + 2 * rx;  // window row pitch
         const uint8_t* win = stage;
         const uint8_t* curS = stage + cur_off;
-        const Region gw = region(win, (size_t)WP * (kTile + 2 * R), status);  // this tile's window rows
-        const Region gc = region(curS, (size_t)kTile * kTile, status);       // its current blocks
+        const Region gw = region(win, (size_t)WP * (TH + 2 * R), status);  // this tile's window rows
+        const Region gc = region(curS, (size_t)kTile * TH, status);       // its current blocks
 
         // ------------------------------------------------ phase A: HCSP
         // A warp takes NR tile rows of blocks per pass (the search alone: two
@@ -345,26 +374,31 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
             // two rows per pass measured faster for the search alone, slower with
             // the evaluation fused (its registers are at the four-CTA limit)
             if constexpr (!EVAL)
-                for (; row + nwarps < TXB; row += 2 * nwarps)
+                for (; row + nwarps < TYB; row += 2 * nwarps)
                     hcsp_rows(row, nwarps, std::integral_constant<int, 2>{});
-            for (; row < TXB; row += nwarps) hcsp_rows(row, 0, std::integral_constant<int, 1>{});
+            for (; row < TYB; row += nwarps) hcsp_rows(row, 0, std::integral_constant<int, 1>{});
         }
         __syncthreads();
 
         // ------------------------------------------------ phase B: diamond rounds
         // Every iteration runs one round for every group of the warp, in
         // converged code: (1) groups without a block take the next ring entries
-        // (one atomic per warp), (2) each group builds its round's list, lane k
-        // checking point k, (3) the new points' SADs are evaluated together,
-        // (4) the switching strategies pick the next list.
+        // (one atomic per warp), (2) each group builds its round's list, lane lg
+        // checking points lg, lg + LPB, ..., (3) the new points' SADs are
+        // evaluated together, (4) the switching strategies pick the next list.
+        // A group is LPB lanes: 2 for 16x16 blocks (a warp serves 16 blocks per
+        // round, so a round's control costs half of what 4-lane groups pay per
+        // block), 4 for 8x8 blocks (whose +-32 bitmaps would otherwise halve
+        // the CTAs per SM).
         {
-            const int gq = tid >> 2, l4 = lane & 3, lead = lane & ~3;
-            const int wb = l4 % WPB, rb = l4 / WPB;
+            constexpr unsigned GMASK = (1u << LPB) - 1u;
+            const int gq = tid / LPB, lg = lane % LPB, lead = lane & ~(LPB - 1);
+            const int col0 = GM::col0(lg), row0 = GM::row0(lg);
             uint32_t* bm = bm_all + gq * nwb;
             const int side = 2 * R + 1;
             const int nring = s_ring_n;
 
-            // group state, identical in the 4 lanes
+            // group state, identical in the group's lanes
             int act = 0;  // 0: needs a block, 1: searching, 2: done
             int phase = PH_DDSP, pat = PAT_H, nsp = 0, pick = -1;
             int cx = 0, cy = 0, bxp = 0, byp = 0;
@@ -374,13 +408,15 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
             int ridx = 0, rmb = 0;                    // EVAL: the block's ring entry and tile position
             uint32_t ds0 = kUnknown, ds1 = kUnknown;  // distant-point SADs of this round (DCDS^S)
             int wmin = INT_MAX, wmax = -1;            // bitmap words this lane has set
-            uint32_t cb[RPL];
+            uint32_t cb[RPLB][CPL];
 #pragma unroll
-            for (int r = 0; r < RPL; ++r) cb[r] = 0u;
+            for (int r = 0; r < RPLB; ++r)
+#pragma unroll
+                for (int j = 0; j < CPL; ++j) cb[r][j] = 0u;
 
             for (int iter = 0;; ++iter) {
                 // ---- (1) fetch: one atomic for all groups of the warp that need a block ----
-                const unsigned need = __ballot_sync(FULL, act == 0 && l4 == 0);
+                const unsigned need = __ballot_sync(FULL, act == 0 && lg == 0);
                 if (need) {
                     const int first = __ffs(need) - 1;
                     int base = 0;
@@ -402,13 +438,15 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
                             rmb = mb;
                             dxlo = max(-R, -px); dxhi = min(R, W - B - px);
                             dylo = max(-R, -py); dyhi = min(R, H - B - py);
-                            wx0 = rx + bxl * B + 4 * wb;
-                            wy0 = R + byl * B + rb * RPL;
+                            wx0 = rx + bxl * B + 4 * col0;
+                            wy0 = R + byl * B + row0;
                             const uint32_t* cp = reinterpret_cast<const uint32_t*>(
-                                curS + (byl * B + rb * RPL) * kTile + bxl * B + 4 * wb);
+                                curS + (byl * B + row0) * kTile + bxl * B + 4 * col0);
 #pragma unroll
-                            for (int r = 0; r < RPL; ++r)
-                                cb[r] = ld_word(reinterpret_cast<const uint8_t*>(cp + r * (kTile / 4)), gc);
+                            for (int r = 0; r < RPLB; ++r)
+#pragma unroll
+                                for (int j = 0; j < CPL; ++j)
+                                    cb[r][j] = ld_word(reinterpret_cast<const uint8_t*>(cp + r * (kTile / 4) + j), gc);
                             decode(kHcsp, hb, cx, cy);
                             bxp = cx; byp = cy; bsad = e.y;
                             nsp = (int)((e.x >> 11) & 7u);
@@ -416,8 +454,8 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
                             phase = PH_DDSP;
                             pick = -1;
                             act = 1;
-                            // every valid HCSP point is visited (lanes take points l4 and l4 + 4)
-                            for (int k = l4; k < 7; k += 4) {
+                            // every valid HCSP point is visited (lane lg takes points lg, lg + LPB, ...)
+                            for (int k = lg; k < 7; k += LPB) {
                                 int ox, oy;
                                 decode(kHcsp, k, ox, oy);
                                 if (ox >= dxlo && ox <= dxhi && oy >= dylo && oy <= dyhi) {
@@ -433,7 +471,7 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
                 }
                 if (!__any_sync(FULL, act != 2)) break;
 
-                // ---- (2) this round's list: lane k checks point k ----
+                // ---- (2) this round's list: lane lg checks points lg, lg + LPB, ... ----
                 uint64_t code;
                 int npts;
                 if (phase == PH_DDSP) { code = pat ? kDdspV : kDdspH; npts = 4; }
@@ -444,28 +482,39 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
                     if (SIMPL && pick >= 0) { code >>= 6 * pick; npts = 1; }
                 }
                 const bool counted = !(SIMPL && phase == PH_SIDE);
-                bool valid = false, fresh = false, fin = false;
-                int bit = 0;
-                if (act == 1 && l4 < npts) {
-                    int ox, oy;
-                    decode(code, l4, ox, oy);
-                    const int x = cx + ox, y = cy + oy;
-                    valid = x >= dxlo && x <= dxhi && y >= dylo && y <= dyhi;
-                    if (valid) {
-                        if (counted) {
-                            bit = (y + R) * side + (x + R);
-                            fresh = index_ok(bit >> 5, nwb, status) && ((bm[bit >> 5] >> (bit & 31)) & 1u) == 0u;
-                        } else {
-                            fresh = (l4 == 0 ? ds0 : ds1) == kUnknown;
+                unsigned vb = 0u, nb = 0u;  // valid / new points of the list, bit k = point k
+#pragma unroll
+                for (int i = 0; i < 4 / LPB; ++i) {
+                    const int k = i * LPB + lg;
+                    bool valid = false, fresh = false;
+                    int bit = 0;
+                    if (act == 1 && k < npts) {
+                        int ox, oy;
+                        decode(code, k, ox, oy);
+                        const int x = cx + ox, y = cy + oy;
+                        valid = x >= dxlo && x <= dxhi && y >= dylo && y <= dyhi;
+                        if (valid) {
+                            if (counted) {
+                                bit = (y + R) * side + (x + R);
+                                fresh = index_ok(bit >> 5, nwb, status) && ((bm[bit >> 5] >> (bit & 31)) & 1u) == 0u;
+                            } else {
+                                fresh = (k == 0 ? ds0 : ds1) == kUnknown;
+                            }
                         }
                     }
-                }
-                const unsigned vb = (__ballot_sync(FULL, valid) >> lead) & 15u;
-                const unsigned nb = (__ballot_sync(FULL, fresh) >> lead) & 15u;
-                if (counted && fresh) {
-                    if (index_ok(bit >> 5, nwb, status)) atomicOr(&bm[bit >> 5], 1u << (bit & 31));
-                    wmin = min(wmin, bit >> 5);
-                    wmax = max(wmax, bit >> 5);
+                    if constexpr (LPB == 1) {
+                        vb |= (unsigned)valid << i;
+                        nb |= (unsigned)fresh << i;
+                    } else {
+                        vb |= ((__ballot_sync(FULL, valid) >> lead) & GMASK) << (i * LPB);
+                        nb |= ((__ballot_sync(FULL, fresh) >> lead) & GMASK) << (i * LPB);
+                    }
+                    // the list's points are distinct: marking one leaves the others' checks unchanged
+                    if (counted && fresh) {
+                        if (index_ok(bit >> 5, nwb, status)) atomicOr(&bm[bit >> 5], 1u << (bit & 31));
+                        wmin = min(wmin, bit >> 5);
+                        wmax = max(wmax, bit >> 5);
+                    }
                 }
                 if (SIMPL && phase == PH_DDSP) {
                     ds0 = (vb & 4u) ? kUnknown : kInvalid;
@@ -493,10 +542,11 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
                 // geometry rules out after the HCSP, would take one more pass)
                 const bool three = __any_sync(FULL, ncand > 2);
                 if (three) {
-                    eval_points<3, V, RPL>(win, WP, wx0, wy0, qx, qy, cb, sad, 0, gw);
-                    if (__any_sync(FULL, ncand > 3)) eval_points<1, V, RPL>(win, WP, wx0, wy0, qx, qy, cb, sad, 3, gw);
+                    eval_points<3, V, RPLB, CPL, LPB>(win, WP, wx0, wy0, qx, qy, cb, sad, 0, ncand, gw);
+                    if (__any_sync(FULL, ncand > 3))
+                        eval_points<1, V, RPLB, CPL, LPB>(win, WP, wx0, wy0, qx, qy, cb, sad, 3, ncand, gw);
                 } else {
-                    eval_points<2, V, RPL>(win, WP, wx0, wy0, qx, qy, cb, sad, 0, gw);
+                    eval_points<2, V, RPLB, CPL, LPB>(win, WP, wx0, wy0, qx, qy, cb, sad, 0, ncand, gw);
                 }
 
                 // ---- (4) best point of the list, then switching strategies (Sec. III-B) ----
@@ -525,7 +575,7 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
                         pick = (ds0 == kInvalid && ds1 == kInvalid) ? -1
                              : (ds0 == kInvalid) ? 1 : (ds1 == kInvalid) ? 0 : (ds1 < ds0 ? 1 : 0);
                     } else {  // step 4 evaluated: the block is done
-                        if (l4 == 0) {
+                        if (lg == 0) {
                             out_mv[blk] = (uint32_t)(uint16_t)bxp | ((uint32_t)(uint16_t)byp << 16);
                             out_sad[blk] = bsad;
                             if (out_nsp) out_nsp[blk] = (uint16_t)nsp;
@@ -535,7 +585,7 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
                         wmin = INT_MAX; wmax = -1;
                         act = 0;
                         // the ring entry now holds the final result for the evaluation pass
-                        if (EVAL && l4 == 0 && index_ok(ridx, NMB, status))
+                        if (EVAL && lg == 0 && index_ok(ridx, NMB, status))
                             ring[ridx] = make_uint2((uint32_t)rmb | ((uint32_t)(bxp + 32) << 8) |
                                                         ((uint32_t)(byp + 32) << 16),
                                                     bsad | ((uint32_t)nsp << 16));
@@ -608,7 +658,8 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
         __syncthreads();  // every read of this stage is done
         if (NST == 1 && tid == 0) {
             fence_proxy_async();
-            issue_tile(atomicAdd(head, 1), frames, nframes, ntiles, smem, cur_off, &s_bar[0], &s_tile[0], &s_frame[0]);
+            issue_tile(atomicAdd(head, 1), frames, nframes, ntiles, smem, cur_off, TH, &s_bar[0], &s_tile[0],
+                       &s_frame[0]);
         }
     }
 }
@@ -666,11 +717,11 @@ int occupancy_t(int max_range, const Shape& s)
 size_t dcds_smem_bytes(int block, int max_range, const Shape& s)
 {
     const int nst = s.stages == 2 ? 2 : 1;
-    const int stage = win_bytes_max(max_range) + kTile * kTile;
-    const int nmb = (kTile / block) * (kTile / block);
+    const int stage = win_bytes_max(max_range, kDcdsTileH) + kTile * kDcdsTileH;
+    const int nmb = (kTile / block) * (kDcdsTileH / block);
     const int side = 2 * max_range + 1;
     const int nwb = (side * side + 31) / 32;
-    return 128 + (size_t)nst * stage + (size_t)nmb * 8 + (size_t)(s.threads / 4) * nwb * 4;
+    return 128 + (size_t)nst * stage + (size_t)nmb * 8 + (size_t)(s.threads / dcds_lanes_per_block(block)) * nwb * 4;
 }
 
 int dcds_ctas_per_sm(int block, int max_range, bool simplified, const Shape& s)
@@ -697,7 +748,7 @@ cudaError_t launch_dcds(const FrameDev* frames, int nframes, int ntiles, int blo
                         bool simplified, const Shape& s, int* head, unsigned* status, int num_sms,
                         cudaStream_t st, bool eval)
 {
-    if (s.threads != 128 && s.threads != 256) return cudaErrorInvalidValue;
+    if (s.threads != 64 && s.threads != 128 && s.threads != 256) return cudaErrorInvalidValue;
     if (block == 16)
         return simplified ? launch_b<16, true>(frames, nframes, ntiles, max_range, s, head, status, num_sms, eval, st)
                           : launch_b<16, false>(frames, nframes, ntiles, max_range, s, head, status, num_sms, eval, st);

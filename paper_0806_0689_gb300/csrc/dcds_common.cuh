@@ -112,10 +112,10 @@ __device__ __forceinline__ int find_frame(const FrameDev* frames, int nframes, i
 
 __host__ __device__ inline int round128(int v) { return (v + 127) & ~127; }
 
-__host__ __device__ inline int win_bytes_max(int max_range)
+__host__ __device__ inline int win_bytes_max(int max_range, int tile_h)
 {
     const int rxm = (max_range + 15) & ~15;
-    return round128((kTile + 2 * rxm) * (kTile + 2 * max_range));
+    return round128((kTile + 2 * rxm) * (tile_h + 2 * max_range));
 }
 
 // Thread 0: take tile t into stage `st`: publish its index and frame, then arm
@@ -124,7 +124,7 @@ __host__ __device__ inline int win_bytes_max(int max_range)
 // extra_tx > 0 arms the barrier for more bytes than the copies deliver (the
 // failure-detection test hook: the wait on this stage then runs out).
 __device__ inline void issue_tile(int t, const FrameDev* frames, int nframes, int ntiles, uint8_t* stage,
-                           int cur_off, uint64_t* bar, int* s_tile, int* s_frame, uint32_t extra_tx = 0)
+                           int cur_off, int tile_h, uint64_t* bar, int* s_tile, int* s_frame, uint32_t extra_tx = 0)
 {
     *s_tile = t;
     if (t >= ntiles) {
@@ -137,10 +137,10 @@ __device__ inline void issue_tile(int t, const FrameDev* frames, int nframes, in
     const int lt = t - F.tile_base;
     const int ty = lt / F.tiles_x, tx = lt - ty * F.tiles_x;
     const int rx = (F.range + 15) & ~15;
-    const uint32_t bytes = (uint32_t)((kTile + 2 * rx) * (kTile + 2 * F.range) + kTile * kTile) + extra_tx;
+    const uint32_t bytes = (uint32_t)((kTile + 2 * rx) * (tile_h + 2 * F.range) + kTile * tile_h) + extra_tx;
     mbar_arrive_expect_tx(bar, bytes);
-    tma_load_2d(stage, &F.tm_ref, tx * kTile - rx, ty * kTile - F.range, bar);
-    tma_load_2d(stage + cur_off, &F.tm_cur, tx * kTile, ty * kTile, bar);
+    tma_load_2d(stage, &F.tm_ref, tx * kTile - rx, ty * tile_h - F.range, bar);
+    tma_load_2d(stage + cur_off, &F.tm_cur, tx * kTile, ty * tile_h, bar);
 }
 
 

@@ -102,7 +102,8 @@ Shape default_shape(me_ctx* c, int algo, int block, int range)
         return s;
     }
     s.threads = ME_DCDS_THREADS;
-    s.tx = s.ty = me::kTile / block;
+    s.tx = me::kTile / block;
+    s.ty = me::kDcdsTileH / block;
     s.k = 0;
     s.ctas_per_sm = 0;  // from the occupancy of the kernel
     s.stages = ME_DCDS_STAGES;
@@ -199,8 +200,8 @@ int build_table(const me_frame_desc* d, int n, int block, const Shape& s, bool f
             if (!me::encode_fs_maps(f, g.nch, me::fs_rows(block, f.range, s.k), s.tx * block, block)) return -1;
         } else {
             f.tiles_x = (f.w + me::kTile - 1) / me::kTile;
-            f.tiles_y = (f.h + me::kTile - 1) / me::kTile;
-            if (!me::encode_frame_maps(f)) return -1;
+            f.tiles_y = (f.h + me::kDcdsTileH - 1) / me::kDcdsTileH;
+            if (!me::encode_frame_maps(f, me::kDcdsTileH)) return -1;
         }
         if (ev && ev->sums) {
             f.sums = reinterpret_cast<unsigned long long*>(ev->sums) + (size_t)ME_NSUMS * i;

@@ -128,7 +128,8 @@ extern "C" int me_estimate_batch_noalloc(const me_frame_desc* d, int n, int bloc
 
     me::Shape s{};
     s.threads = 128;
-    s.tx = s.ty = me::kTile / block;
+    s.tx = me::kTile / block;
+    s.ty = me::kDcdsTileH / block;
     s.k = 0;
     s.stages = 1;
     s.ctas_per_sm = 0;
@@ -151,8 +152,8 @@ extern "C" int me_estimate_batch_noalloc(const me_frame_desc* d, int n, int bloc
         f.w = x.w; f.h = x.h; f.pitch = x.pitch; f.range = x.range;
         f.nbx = x.w / block; f.nby = x.h / block;
         f.tiles_x = (x.w + me::kTile - 1) / me::kTile;
-        f.tiles_y = (x.h + me::kTile - 1) / me::kTile;
-        if (!me::encode_frame_maps(f))
+        f.tiles_y = (x.h + me::kDcdsTileH - 1) / me::kDcdsTileH;
+        if (!me::encode_frame_maps(f, me::kDcdsTileH))
             return set_err(err, err_len, ME_ERR_CUDA, "cuTensorMapEncodeTiled rejected a frame description");
         f.tile_base = tiles;
         tiles += f.tiles_x * f.tiles_y;

@@ -10,8 +10,9 @@ workload, 4000 with motion scales 6/3 for 2160p as in the stress workload,
 2000 otherwise).  --algo: fs, dcds, dcds_s, eval (DCDS with the Sec. IV
 measures fused, against the FS field), median or learned (an untrained
 network: the cost of the learned start does not depend on its weights).
-Every call runs --reps times on one stream, then the process synchronises
-and prints one line.
+Every call runs --reps times on the current stream; the line printed at the
+end gives the median time of one call (CUDA events around it, host work
+included).
 """
 from __future__ import annotations
 
@@ -62,13 +63,19 @@ def main(argv=None):
         run = lambda: ctx.me_estimate_learned_batch(prop, d, block=a.block)
     else:
         run = lambda: ctx.me_estimate_batch(d, a.block, a.algo)
+    ms = []
     for _ in range(a.reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
         run()
-    torch.cuda.synchronize()
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
     ctx.me_check_status()
     blocks = sum(x[2].shape[0] for x in keep)
+    ms.sort()
     print(f"{a.workload} block {a.block} range {a.range} {a.algo}: {a.pairs} pairs, {blocks} blocks, "
-          f"{a.reps} calls")
+          f"{a.reps} calls, median {ms[len(ms) // 2]:.3f} ms per call")
 
 
 if __name__ == "__main__":
