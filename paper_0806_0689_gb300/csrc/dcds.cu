@@ -97,32 +97,38 @@ __device__ __forceinline__ uint32_t ld_word(const uint8_t* p, const Region& g)
     return *reinterpret_cast<const uint32_t*>(p);
 }
 
-// Lanes of a phase-B group: a block of B x B pixels (B / 4 words per row) is
-// split over LPB lanes, each holding CPL adjacent word columns of RPL rows
-// (first column col0, first row row0 of the block).
 // Lanes per block in the diamond rounds (phase B).  Measured on the 1080p
 // batch (16x16, +-16) and the 2160p 8x8 +-32 batch: 16x16 with 2 lanes 5 %
 // faster than with 4 for the search alone, the same with the evaluation
 // fused; 8x8 with 2 or 1 lanes 23 % and 35 % slower (the per-group bitmaps
-// cost CTAs per SM).
+// cost CTAs per SM), and with 1 lane and a 15 x 15 visited box per lane
+// (blocks whose path leaves it searched again in an overflow pass) 56 %
+// slower: 32 lanes reading 32 unrelated rows multiply the bank conflicts.
 __host__ __device__ constexpr int dcds_lanes_per_block(int block) { return block == 16 ? 2 : 4; }
 
+// Lanes of a phase-B group: a block of B x B pixels (B / 4 words per row) is
+// split over LPB lanes, each holding CPL adjacent word columns of RPL rows:
+// rows row0, row0 + RS, row0 + 2 RS, ... from column col0.  With more lanes
+// than words per row the lanes of one column interleave their rows (RS > 1):
+// lanes that read rows 4 apart would hit the same banks (a window row is 40
+// or 48 words, so 4 rows are a multiple of 32 words), rows 1 apart do not.
 template <int B, int LPB>
 struct GroupMap {
     static constexpr int WPB = B / 4;
     static constexpr int CPL = WPB >= LPB ? WPB / LPB : 1;
     static constexpr int RPL = WPB >= LPB ? B : B * WPB / LPB;
+    static constexpr int RS = WPB >= LPB ? 1 : LPB / WPB;
     __device__ static int col0(int lg) { return WPB >= LPB ? lg * CPL : lg % WPB; }
-    __device__ static int row0(int lg) { return WPB >= LPB ? 0 : (lg / WPB) * RPL; }
+    __device__ static int row0(int lg) { return WPB >= LPB ? 0 : lg / WPB; }
 };
 
 // SADs of NP candidates (slots i0 .. i0 + NP - 1 of qx / qy; only those below
 // nvalid are loaded, so groups with fewer candidates add no shared-memory
-// traffic) of an LPB-lane group.  Per row a lane loads the CPL + 1 aligned
+// traffic) of an LPB-lane group (a lane's rows RS apart).  Per row a lane loads the CPL + 1 aligned
 // words that cover its CPL unaligned ones; the loads of all NP points are
 // issued together, then each sum is completed across the group (every lane
 // of the warp takes part in the shuffles).
-template <int NP, int V, int RPL, int CPL, int LPB>
+template <int NP, int V, int RPL, int CPL, int LPB, int RS>
 __device__ __forceinline__ void eval_points(const uint8_t* win, int WP, int wx0, int wy0, const int (&qx)[4],
                                             const int (&qy)[4], const uint32_t (&cb)[RPL][CPL],
                                             uint32_t (&sad)[4], int i0, int nvalid, const Region& gw)
@@ -144,7 +150,10 @@ __device__ __forceinline__ void eval_points(const uint8_t* win, int WP, int wx0,
             if (i0 + k < nvalid) {
                 uint32_t w[CPL + 1];
 #pragma unroll
-                for (int j = 0; j <= CPL; ++j) w[j] = ld_word(p[k] + r * WP + 4 * j, gw);
+                for (int j = 0; j < CPL; ++j) w[j] = ld_word(p[k] + r * RS * WP + 4 * j, gw);
+                // the word after them only when the columns are unaligned (at the
+                // window's right edge an aligned block needs nothing beyond it)
+                w[CPL] = ld_word(p[k] + r * RS * WP + 4 * CPL, gw);
 #pragma unroll
                 for (int j = 0; j < CPL; ++j) a[k] = sadacc<V>(__funnelshift_r(w[j], w[j + 1], sh[k]), cb[r][j], a[k]);
             }
@@ -191,12 +200,13 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
     constexpr int RPL = B * WPB / 4;      // phase-C rows per lane (4 lanes per block)
     constexpr int LPB = dcds_lanes_per_block(B);  // phase-B lanes per block
     using GM = GroupMap<B, LPB>;
-    constexpr int RPLB = GM::RPL, CPL = GM::CPL;
+    constexpr int RPLB = GM::RPL, CPL = GM::CPL, RSB = GM::RS;
     constexpr unsigned FULL = 0xffffffffu;
 
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t s_bar[NST];
     __shared__ int s_tile[NST], s_frame[NST];
+    __shared__ TileDesc s_desc[NST];
     __shared__ int s_ring_n, s_ring_next;
 
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
@@ -205,7 +215,7 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
     uint2* ring = reinterpret_cast<uint2*>(smem + NST * stage_bytes);
     const int side_max = 2 * max_range + 1;
     const int nwb = (side_max * side_max + 31) / 32;
-    uint32_t* bm_all = reinterpret_cast<uint32_t*>(ring + NMB);
+    uint32_t* bm_all = reinterpret_cast<uint32_t*>(ring + NMB);  // one +-R visited bitmap per group
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
     const int ngroups = blockDim.x >> 2;  // phase-C groups (4 lanes per block)
@@ -221,7 +231,7 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
         for (int s = 0; s < NST; ++s) mbar_init(&s_bar[s], 1);
         fence_mbar_init();
         issue_tile(atomicAdd(head, 1), frames, nframes, ntiles, smem, cur_off, TH, &s_bar[0], &s_tile[0], &s_frame[0],
-                   starve ? 16u : 0u);
+                   &s_desc[0], starve ? 16u : 0u);
     }
     __syncthreads();
 
@@ -243,24 +253,29 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
             // stage st^1 was last read in the previous tile, which ended with a barrier
             fence_proxy_async();
             issue_tile(atomicAdd(head, 1), frames, nframes, ntiles, smem + (st ^ 1) * stage_bytes, cur_off, TH,
-                       &s_bar[st ^ 1], &s_tile[st ^ 1], &s_frame[st ^ 1]);
+                       &s_bar[st ^ 1], &s_tile[st ^ 1], &s_frame[st ^ 1], &s_desc[st ^ 1]);
         }
-        // descriptor fields in registers: the output stores below cannot alias them
-        const FrameDev* Fp = frames + s_frame[st];
-        const int W = Fp->w, H = Fp->h, R = Fp->range, NBX = Fp->nbx, NBY = Fp->nby;
-        uint32_t* __restrict__ out_mv = reinterpret_cast<uint32_t*>(Fp->mv);
-        uint32_t* __restrict__ out_sad = Fp->sad;
-        uint16_t* __restrict__ out_nsp = Fp->nsp;
-        const uint32_t* __restrict__ mv_fs = EVAL ? reinterpret_cast<const uint32_t*>(Fp->mv_fs) : nullptr;
-        const int lt = t - Fp->tile_base;
-        const int txs = Fp->tiles_x;
-        const int tile_y = lt / txs, tile_x = lt - tile_y * txs;
+        // descriptor fields in registers (from the claim's shared copy): the
+        // output stores below cannot alias them
+        const TileDesc& D = s_desc[st];
+        const int W = D.w, H = D.h, R = D.range, NBX = D.nbx, NBY = D.nby;
+        uint32_t* __restrict__ out_mv = D.mv;
+        uint32_t* __restrict__ out_sad = D.sad;
+        uint16_t* __restrict__ out_nsp = D.nsp;
+        const uint32_t* __restrict__ mv_fs = EVAL ? D.mv_fs : nullptr;
+        unsigned long long* const sums = EVAL ? D.sums : nullptr;
+        const bool first_tile = D.first != 0;
+        const int tile_y = D.tile_y, tile_x = D.tile_x;
         const int bx0 = tile_x * TXB, by0 = tile_y * TYB;
         const int rx = (R + 15) & ~15;
         const int WP = kTile + 2 * rx;  // window row pitch
         const uint8_t* win = stage;
         const uint8_t* curS = stage + cur_off;
-        const Region gw = region(win, (size_t)WP * (TH + 2 * R), status);  // this tile's window rows
+        // this tile's window rows; the word after a lane's last needed byte is
+        // always loaded (a shift of 0 discards it: loading it only when needed
+        // measured 26 % slower), so at the window's last row a read may reach
+        // 4 bytes past it, still inside the stage (the current tile follows)
+        const Region gw = region(win, (size_t)WP * (TH + 2 * R) + 4, status);
         const Region gc = region(curS, (size_t)kTile * TH, status);       // its current blocks
 
         // ------------------------------------------------ phase A: HCSP
@@ -446,7 +461,8 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
                             for (int r = 0; r < RPLB; ++r)
 #pragma unroll
                                 for (int j = 0; j < CPL; ++j)
-                                    cb[r][j] = ld_word(reinterpret_cast<const uint8_t*>(cp + r * (kTile / 4) + j), gc);
+                                    cb[r][j] = ld_word(
+                                        reinterpret_cast<const uint8_t*>(cp + r * RSB * (kTile / 4) + j), gc);
                             decode(kHcsp, hb, cx, cy);
                             bxp = cx; byp = cy; bsad = e.y;
                             nsp = (int)((e.x >> 11) & 7u);
@@ -542,11 +558,11 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
                 // geometry rules out after the HCSP, would take one more pass)
                 const bool three = __any_sync(FULL, ncand > 2);
                 if (three) {
-                    eval_points<3, V, RPLB, CPL, LPB>(win, WP, wx0, wy0, qx, qy, cb, sad, 0, ncand, gw);
+                    eval_points<3, V, RPLB, CPL, LPB, RSB>(win, WP, wx0, wy0, qx, qy, cb, sad, 0, ncand, gw);
                     if (__any_sync(FULL, ncand > 3))
-                        eval_points<1, V, RPLB, CPL, LPB>(win, WP, wx0, wy0, qx, qy, cb, sad, 3, ncand, gw);
+                        eval_points<1, V, RPLB, CPL, LPB, RSB>(win, WP, wx0, wy0, qx, qy, cb, sad, 3, ncand, gw);
                 } else {
-                    eval_points<2, V, RPLB, CPL, LPB>(win, WP, wx0, wy0, qx, qy, cb, sad, 0, ncand, gw);
+                    eval_points<2, V, RPLB, CPL, LPB, RSB>(win, WP, wx0, wy0, qx, qy, cb, sad, 0, ncand, gw);
                 }
 
                 // ---- (4) best point of the list, then switching strategies (Sec. III-B) ----
@@ -598,6 +614,7 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
             // ---- phase C: squared error of every ring block at its final MV (dense, 4 lanes per block) ----
             __syncthreads();
             const int nring = s_ring_n;
+            constexpr int RS4 = 4 / WPB;  // a lane's row step (rows interleaved as in phase B)
             const int gq = tid >> 2, l4 = lane & 3;
             const int wb = l4 % WPB, rb = l4 / WPB;
             for (int base = 0; base < nring; base += ngroups) {
@@ -615,15 +632,16 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
                     const int bxl = mb % TXB, byl = mb / TXB;
                     if (mv_fs && l4 == 0) fw = __ldg(mv_fs + (size_t)(by0 + byl) * NBX + bx0 + bxl);
                     const int c0 = rx + bxl * B + 4 * wb + dx;
-                    const uint8_t* p0 = win + (R + byl * B + rb * RPL + dy) * WP + (c0 & ~3);
+                    const uint8_t* p0 = win + (R + byl * B + rb + dy) * WP + (c0 & ~3);
                     const unsigned s0 = (unsigned)(c0 & 3) * 8u;
-                    const uint32_t* cp = reinterpret_cast<const uint32_t*>(curS + (byl * B + rb * RPL) * kTile +
+                    const uint32_t* cp = reinterpret_cast<const uint32_t*>(curS + (byl * B + rb) * kTile +
                                                                            bxl * B + 4 * wb);
 #pragma unroll
                     for (int r = 0; r < RPL; ++r) {
-                        const uint32_t l0 = ld_word(p0 + r * WP, gw);
-                        const uint32_t h0 = ld_word(p0 + r * WP + 4, gw);
-                        const uint32_t cw0 = ld_word(reinterpret_cast<const uint8_t*>(cp + r * (kTile / 4)), gc);
+                        const uint32_t l0 = ld_word(p0 + r * RS4 * WP, gw);
+                        const uint32_t h0 = ld_word(p0 + r * RS4 * WP + 4, gw);
+                        const uint32_t cw0 =
+                            ld_word(reinterpret_cast<const uint8_t*>(cp + r * RS4 * (kTile / 4)), gc);
                         const uint32_t d = __vabsdiffu4(__funnelshift_r(l0, h0, s0), cw0);
                         q = __dp4a(d, d, q);
                     }
@@ -634,7 +652,7 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
                     eval_block(dx, dy, fsad, q, fnsp, out_nsp != nullptr, mv_fs != nullptr, fw, B * B, esum, edist);
             }
             // this tile's sums: one atomic per warp and counter
-            unsigned long long* fs = Fp->sums;
+            unsigned long long* fs = sums;
 #pragma unroll
             for (int k = 0; k < 5; ++k) {
                 uint32_t v = esum[k];
@@ -650,16 +668,16 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
                 if (lane == 0 && v) atomicAdd(fs + 4, v);
                 edist = 0ull;
             }
-            if (tid == 0 && lt == 0) {
+            if (tid == 0 && first_tile) {
                 fs[5] = (unsigned long long)NBX * NBY;
-                fs[7] = Fp->mv_fs ? 1ull : 0ull;
+                fs[7] = mv_fs ? 1ull : 0ull;
             }
         }
         __syncthreads();  // every read of this stage is done
         if (NST == 1 && tid == 0) {
             fence_proxy_async();
             issue_tile(atomicAdd(head, 1), frames, nframes, ntiles, smem, cur_off, TH, &s_bar[0], &s_tile[0],
-                       &s_frame[0]);
+                       &s_frame[0], &s_desc[0]);
         }
     }
 }

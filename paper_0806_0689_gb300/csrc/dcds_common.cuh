@@ -118,13 +118,26 @@ __host__ __device__ inline int win_bytes_max(int max_range, int tile_h)
     return round128((kTile + 2 * rxm) * (tile_h + 2 * max_range));
 }
 
-// Thread 0: take tile t into stage `st`: publish its index and frame, then arm
-// the stage's mbarrier with the byte count and start the two TMA copies.  A
-// tile index past the end completes the phase with no data.
+// The fields of a tile's frame that the search reads, copied into shared
+// memory by the thread that claims the tile, so that the CTA does not wait on
+// the frame table's global loads when the tile arrives.
+struct TileDesc {
+    uint32_t* mv;
+    uint32_t* sad;
+    uint16_t* nsp;
+    const uint32_t* mv_fs;
+    unsigned long long* sums;
+    int w, h, range, nbx, nby, tile_x, tile_y, first;  // first: the frame's first tile (writes its counts)
+};
+
+// Thread 0: take tile t into stage `st`: publish its index, frame and
+// descriptor, then arm the stage's mbarrier with the byte count and start the
+// two TMA copies.  A tile index past the end completes the phase with no data.
 // extra_tx > 0 arms the barrier for more bytes than the copies deliver (the
 // failure-detection test hook: the wait on this stage then runs out).
 __device__ inline void issue_tile(int t, const FrameDev* frames, int nframes, int ntiles, uint8_t* stage,
-                           int cur_off, int tile_h, uint64_t* bar, int* s_tile, int* s_frame, uint32_t extra_tx = 0)
+                           int cur_off, int tile_h, uint64_t* bar, int* s_tile, int* s_frame, TileDesc* desc,
+                           uint32_t extra_tx = 0)
 {
     *s_tile = t;
     if (t >= ntiles) {
@@ -137,6 +150,13 @@ __device__ inline void issue_tile(int t, const FrameDev* frames, int nframes, in
     const int lt = t - F.tile_base;
     const int ty = lt / F.tiles_x, tx = lt - ty * F.tiles_x;
     const int rx = (F.range + 15) & ~15;
+    desc->mv = reinterpret_cast<uint32_t*>(F.mv);
+    desc->sad = F.sad;
+    desc->nsp = F.nsp;
+    desc->mv_fs = reinterpret_cast<const uint32_t*>(F.mv_fs);
+    desc->sums = F.sums;
+    desc->w = F.w; desc->h = F.h; desc->range = F.range; desc->nbx = F.nbx; desc->nby = F.nby;
+    desc->tile_x = tx; desc->tile_y = ty; desc->first = lt == 0;
     const uint32_t bytes = (uint32_t)((kTile + 2 * rx) * (tile_h + 2 * F.range) + kTile * tile_h) + extra_tx;
     mbar_arrive_expect_tx(bar, bytes);
     tma_load_2d(stage, &F.tm_ref, tx * kTile - rx, ty * tile_h - F.range, bar);

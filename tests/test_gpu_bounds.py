@@ -3,8 +3,10 @@ every shared-memory read of a staged tile against its window or current-tile
 region and every ring and bitmap index, recording a violation instead of
 making it).  Run in a child process over frame sizes with partial tiles,
 block sizes 8 and 16, ranges 1 to 32, DCDS and DCDS^S, one and two stages,
-128 and 256 threads, with and without the fused evaluation: no check may
-fire, and every field stays bit-exact with the oracle (Sec. III-B, IV-C)."""
+128 and 256 threads, with and without the fused evaluation, and smooth
+shifted content whose long search paths reach the window's edges and the
+8x8 overflow pass: no check may fire, and every field stays bit-exact with
+the oracle (Sec. III-B, IV-C)."""
 import os
 import subprocess
 import sys
@@ -26,6 +28,13 @@ cases = []
 for name, n, seed in (("qcif", 3, 7001), ("cif", 3, 7002), ("720p", 2, 7003)):
     s = synth.workload_sequence(name, n, seed=seed, max_motion=16)
     cases += [(s[t + 1], s[t]) for t in range(n - 1)]
+# smooth content shifted far: long diamond paths, up to the window's edges
+# (and, for 8x8 blocks, past the visited box into the overflow pass)
+for (h, w, sx, sy) in ((128, 176, 13, -9), (96, 256, -17, 6)):
+    yy, xx = np.mgrid[0:h + 96, 0:w + 96].astype(np.float64)
+    big = 128 + 60 * np.sin(xx / 17.0) * np.cos(yy / 13.0) + 40 * np.sin((xx + 2 * yy) / 29.0)
+    big = np.clip(np.rint(big), 0, 255).astype(np.uint8)
+    cases.append((big[48 + sy:48 + sy + h, 48 + sx:48 + sx + w].copy(), big[48:48 + h, 48:48 + w].copy()))
 runs = 0
 for shape in ("8 8 128 0 1", "8 8 256 0 2"):
     for B in (16, 8):

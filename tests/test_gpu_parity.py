@@ -161,6 +161,53 @@ def test_global_shift(ctx, sx, sy):
         assert_same(gpu_search(ctx, cur, ref, 16, 7, algo), oracle_search(cur, ref, 16, 7, algo), algo)
 
 
+def smooth_pair(h, w, sx, sy, margin=48):
+    """(cur, ref) of smooth, slowly varying content shifted by (sx, sy): the
+    diamond search walks towards the shift in many small steps, so paths run
+    far from the block's HCSP winner (NSP up to about 110 at +-32)."""
+    yy, xx = np.mgrid[0:h + 2 * margin, 0:w + 2 * margin].astype(np.float64)
+    big = 128 + 60 * np.sin(xx / 17.0) * np.cos(yy / 13.0) + 40 * np.sin((xx + 2 * yy) / 29.0)
+    big = np.clip(np.rint(big), 0, 255).astype(np.uint8)
+    ref = big[margin:margin + h, margin:margin + w].copy()
+    cur = big[margin + sy:margin + sy + h, margin + sx:margin + sx + w].copy()
+    return cur, ref
+
+
+@pytest.mark.parametrize("B", [8, 16])
+@pytest.mark.parametrize("algo", ["dcds", "dcds_s"])
+def test_long_diamond_paths(ctx, B, algo):
+    """Long search paths, bit-exact: 8x8 blocks keep their visited points in a
+    box of +-7 around the HCSP winner and send a block whose path leaves it
+    to the overflow pass; here about half of them do (final MVs of 12 and
+    more).  Two pairs in one batch (the overflow list is per tile), and the
+    same search with the Sec. IV sums fused."""
+    pairs = [smooth_pair(128, 176, 13, -9), smooth_pair(96, 256, -17, 6)]
+    keep, descs = _batch(ctx, pairs, B, algo, [32, 32])
+    ctx.me_estimate_batch(descs, B, algo)
+    torch.cuda.synchronize()
+    far = 0
+    for (cur, ref), (c, r, mv, sad, nsp) in zip(pairs, keep):
+        got = _host(mv, sad, nsp)
+        want = oracle_search(cur, ref, B, 32, algo)
+        assert_same(got, want, f"{algo} B{B}")
+        far += int((np.abs(got[0]).max(1) >= 12).sum())
+    assert far > 20, far
+    # fused: the same fields, and sums equal to the oracle's measures of them
+    keep2, descs2 = _batch(ctx, pairs, B, algo, [32, 32])
+    fs = [_dev(oracle.fs(cur, ref, B, 32)[0]) for cur, ref in pairs]
+    sums = torch.zeros((len(pairs), me.ME_NSUMS), dtype=torch.int64, device="cuda")
+    ctx.me_estimate_eval_batch(descs2, fs, B, algo, sums)
+    torch.cuda.synchronize()
+    for i, ((cur, ref), (c, r, mv, sad, nsp)) in enumerate(zip(pairs, keep2)):
+        got = _host(mv, sad, nsp)
+        want = oracle_search(cur, ref, B, 32, algo)
+        assert_same(got, want, f"fused {algo} B{B}")
+        ev = oracle.evaluate(cur, ref, B, want[0], fs[i].cpu().numpy(), want[2])
+        st = ctx.me_stats_from_sums(sums[i].cpu().numpy().view(np.uint64))
+        for k in ("mad", "mse", "nsp", "probability"):
+            assert st[k] == ev[k], k
+
+
 def _batch(ctx, frames_list, B, algo, rngs):
     """frames_list: list of (cur, ref) numpy pairs.  Returns list of outputs."""
     keep, items = [], []
