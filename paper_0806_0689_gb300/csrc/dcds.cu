@@ -207,6 +207,7 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
     __shared__ __align__(8) uint64_t s_bar[NST];
     __shared__ int s_tile[NST], s_frame[NST];
     __shared__ TileDesc s_desc[NST];
+    __shared__ unsigned long long s_part[EVAL ? 8 : 1][6];  // EVAL: the warps' tile sums
     __shared__ int s_ring_n, s_ring_next;
 
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
@@ -652,20 +653,24 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
                     eval_block(dx, dy, fsad, q, fnsp, out_nsp != nullptr, mv_fs != nullptr, fw, B * B, esum, edist);
             }
             // this tile's sums: one atomic per warp and counter
+            // (warp sums by redux.sync: one instruction each instead of a
+            // five-step shuffle tree; the 64-bit distance in two 32-bit parts,
+            // its low 16 bits and the rest, neither of which can overflow: a
+            // lane adds at most four blocks' distances per tile, each below
+            // 2^41).  The warps' sums meet in shared memory and one warp adds
+            // the tile's total to the frame's counters after the barrier: a
+            // quarter of the atomics, which all land on the frame's eight words.
             unsigned long long* fs = sums;
 #pragma unroll
             for (int k = 0; k < 5; ++k) {
-                uint32_t v = esum[k];
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
-                if (lane == 0 && v) atomicAdd(fs + (k < 4 ? k : 6), (unsigned long long)v);
+                const uint32_t v = __reduce_add_sync(FULL, esum[k]);
+                if (lane == 0) s_part[warp][k] = v;
                 esum[k] = 0u;
             }
             {
-                unsigned long long v = edist;
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
-                if (lane == 0 && v) atomicAdd(fs + 4, v);
+                const uint32_t lo = __reduce_add_sync(FULL, (uint32_t)(edist & 0xffffu));
+                const uint32_t hi = __reduce_add_sync(FULL, (uint32_t)(edist >> 16));
+                if (lane == 0) s_part[warp][5] = ((unsigned long long)hi << 16) + lo;
                 edist = 0ull;
             }
             if (tid == 0 && first_tile) {
@@ -674,6 +679,14 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
             }
         }
         __syncthreads();  // every read of this stage is done
+        if constexpr (EVAL) {
+            if (warp == nwarps - 1 && lane < 6) {
+                unsigned long long v = 0ull;
+                for (int w = 0; w < nwarps; ++w) v += s_part[w][lane];
+                // sums order: ABS SQ NSP EQUAL, then DIST (slot 4) and PIXELS (slot 6)
+                if (v) atomicAdd(sums + (lane < 4 ? lane : lane == 4 ? 6 : 4), v);
+            }
+        }
         if (NST == 1 && tid == 0) {
             fence_proxy_async();
             issue_tile(atomicAdd(head, 1), frames, nframes, ntiles, smem, cur_off, TH, &s_bar[0], &s_tile[0],
