@@ -231,7 +231,10 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
     if (tid == 0) {
         for (int s = 0; s < NST; ++s) mbar_init(&s_bar[s], 1);
         fence_mbar_init();
-        issue_tile(atomicAdd(head, 1), frames, nframes, ntiles, smem, cur_off, TH, &s_bar[0], &s_tile[0], &s_frame[0],
+        // a CTA's first tile is its own index (the grid never exceeds the tile
+        // count), later ones come from the counter: the launch does not open with
+        // every CTA queueing on the counter's one word
+        issue_tile((int)blockIdx.x, frames, nframes, ntiles, smem, cur_off, TH, &s_bar[0], &s_tile[0], &s_frame[0],
                    &s_desc[0], starve ? 16u : 0u);
     }
     __syncthreads();
@@ -253,8 +256,8 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
         if (NST == 2 && tid == 0) {
             // stage st^1 was last read in the previous tile, which ended with a barrier
             fence_proxy_async();
-            issue_tile(atomicAdd(head, 1), frames, nframes, ntiles, smem + (st ^ 1) * stage_bytes, cur_off, TH,
-                       &s_bar[st ^ 1], &s_tile[st ^ 1], &s_frame[st ^ 1], &s_desc[st ^ 1]);
+            issue_tile((int)gridDim.x + atomicAdd(head, 1), frames, nframes, ntiles, smem + (st ^ 1) * stage_bytes,
+                       cur_off, TH, &s_bar[st ^ 1], &s_tile[st ^ 1], &s_frame[st ^ 1], &s_desc[st ^ 1]);
         }
         // descriptor fields in registers (from the claim's shared copy): the
         // output stores below cannot alias them
@@ -689,8 +692,8 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
         }
         if (NST == 1 && tid == 0) {
             fence_proxy_async();
-            issue_tile(atomicAdd(head, 1), frames, nframes, ntiles, smem, cur_off, TH, &s_bar[0], &s_tile[0],
-                       &s_frame[0], &s_desc[0]);
+            issue_tile((int)gridDim.x + atomicAdd(head, 1), frames, nframes, ntiles, smem, cur_off, TH, &s_bar[0],
+                       &s_tile[0], &s_frame[0], &s_desc[0]);
         }
     }
 }
