@@ -198,6 +198,47 @@ __device__ __forceinline__ void conv32(const uint32_t* __restrict__ in, const ui
     }
 }
 
+// conv32 over an activation held as hi and lo bf16 parts (the same layout
+// twice): each weight fragment is loaded once for both parts, and the taps
+// are unrolled so that the weight loads of later taps issue early.
+template <int HIN, int NM>
+__device__ __forceinline__ void conv32_hl(const uint32_t* __restrict__ hi, const uint32_t* __restrict__ lo,
+                                          const uint32_t* __restrict__ Wl, const Rows<NM> rw, int n0,
+                                          float (&acc)[NM][1][4], int g, int t)
+{
+#pragma unroll 3
+    for (int tap = 0; tap < 9; ++tap) {
+        const int ky = tap / 3, kx = tap - 3 * ky;
+        int pix[NM][2];  // word offset of the input pixel, -1 outside (zero padding)
+#pragma unroll
+        for (int i = 0; i < NM; ++i)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int y = 2 * rw.oy[i][h] + ky - 1, x = 2 * rw.ox[i][h] + kx - 1;
+                pix[i][h] = (y >= 0 && y < HIN && x >= 0 && x < HIN) ? ((rw.s[i][h] * HIN + y) * HIN + x) * PXW : -1;
+            }
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            const int w0 = half * 8 + t;  // channel pair 2*w0 (and +8 channels)
+            const uint32_t* wr = Wl + (size_t)(n0 * 8 + g) * 144 + tap * 16 + half * 8 + t;
+            const uint32_t bf[2] = {__ldg(wr), __ldg(wr + 4)};
+#pragma unroll
+            for (int i = 0; i < NM; ++i) {
+#pragma unroll
+                for (int part = 0; part < 2; ++part) {
+                    const uint32_t* in = part ? lo : hi;
+                    uint32_t a[4];
+                    a[0] = pix[i][0] >= 0 ? in[pix[i][0] + w0] : 0u;
+                    a[1] = pix[i][1] >= 0 ? in[pix[i][1] + w0] : 0u;
+                    a[2] = pix[i][0] >= 0 ? in[pix[i][0] + w0 + 4] : 0u;
+                    a[3] = pix[i][1] >= 0 ? in[pix[i][1] + w0 + 4] : 0u;
+                    mma_bf16(acc[i][0], a, bf);
+                }
+            }
+        }
+    }
+}
+
 __device__ __forceinline__ int trunk_frame(const PropFrame* fr, int nframes, long gid)
 {
     int lo = 0, hi = nframes - 1;
@@ -270,6 +311,9 @@ __global__ void __launch_bounds__(256, 3) trunk_tc_kernel(const PropFrame* __res
     uint32_t* A3l = A3h + TC_S * 16 * PXW;
     __shared__ float sb[LAYERS][CH];
     __shared__ int s_fr[TC_S], s_px[TC_S], s_py[TC_S];
+    __shared__ const uint8_t* s_cur[TC_S];
+    __shared__ const uint8_t* s_ref[TC_S];
+    __shared__ int s_pitch[TC_S], s_w[TC_S], s_h[TC_S];
     __shared__ __align__(8) uint64_t s_bar;
     __shared__ uint32_t s_tmem;
     __shared__ int s_fail;
@@ -330,25 +374,61 @@ __global__ void __launch_bounds__(256, 3) trunk_tc_kernel(const PropFrame* __res
             s_fr[tid] = f;
             s_px[tid] = (k % fr[f].nbx) * 16;
             s_py[tid] = (k / fr[f].nbx) * 16;
+            s_cur[tid] = fr[f].cur;
+            s_ref[tid] = fr[f].ref;
+            s_pitch[tid] = fr[f].pitch;
+            s_w[tid] = fr[f].w;
+            s_h[tid] = fr[f].h;
         }
         __syncthreads();
         // the previous iteration's layer-2/3 outputs overwrote padding cells of the planes
         for (int i = tid; i < TC_A23 / 4; i += blockDim.x) reinterpret_cast<uint4*>(A1)[i] = make_uint4(0u, 0u, 0u, 0u);
-        for (int i = tid; i < TC_S * 1024; i += blockDim.x) {
-            const int s = i >> 10, pix = i & 1023, yy = pix >> 5, xx = pix & 31;
-            uint32_t v = 0u;
+        // a thread builds 8 consecutive pixels of one of the 32 rows of its
+        // sample's planes: one 8-byte load of the reference row (and of the
+        // current row inside the central 16x16), or per-byte clamped loads
+        // when the 32x32 patch crosses the frame's edge
+        static_assert(TC_S * 32 * 4 == 256, "one 8-pixel chunk per thread");
+        {
+            const int s = tid >> 7, q = tid & 127, yy = q >> 2, c = q & 3;
+            uint32_t o[8];
             if (s < ns) {
-                const PropFrame& F = fr[s_fr[s]];
+                const uint8_t* cur = s_cur[s];
+                const uint8_t* ref = s_ref[s];
+                const int pitch = s_pitch[s], fw = s_w[s], fh = s_h[s];
                 const int px = s_px[s], py = s_py[s];
-                float v0 = 0.f;
-                if (yy >= 8 && yy < 24 && xx >= 8 && xx < 24)
-                    v0 = ((float)F.cur[(size_t)(py + yy - 8) * F.pitch + (px + xx - 8)] - 128.f) * (1.f / 128.f);
-                const int ry = min(max(py + yy - 8, 0), F.h - 1), rxx = min(max(px + xx - 8, 0), F.w - 1);
-                const float v1 = ((float)F.ref[(size_t)ry * F.pitch + rxx] - 128.f) * (1.f / 128.f);
-                const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
-                v = *reinterpret_cast<const uint32_t*>(&h);
+                const int ry = py + yy - 8, rx0 = px - 8 + 8 * c;
+                const bool in_cur = yy >= 8 && yy < 24 && (c == 1 || c == 2);
+                uint32_t rw[2], cw[2] = {0u, 0u};
+                if (px >= 8 && px + 24 <= fw && py >= 8 && py + 24 <= fh) {
+                    const uint2 r = *reinterpret_cast<const uint2*>(ref + (size_t)ry * pitch + rx0);
+                    rw[0] = r.x; rw[1] = r.y;
+                    if (in_cur) {
+                        const uint2 u = *reinterpret_cast<const uint2*>(cur + (size_t)ry * pitch + rx0);
+                        cw[0] = u.x; cw[1] = u.y;
+                    }
+                } else {
+                    const int ryc = min(max(ry, 0), fh - 1);
+                    rw[0] = rw[1] = 0u;
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        const int rxc = min(max(rx0 + k, 0), fw - 1);
+                        rw[k >> 2] |= (uint32_t)ref[(size_t)ryc * pitch + rxc] << (8 * (k & 3));
+                        if (in_cur) cw[k >> 2] |= (uint32_t)cur[(size_t)ry * pitch + rx0 + k] << (8 * (k & 3));
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const float v0 = in_cur ? ((float)((cw[k >> 2] >> (8 * (k & 3))) & 255u) - 128.f) * (1.f / 128.f) : 0.f;
+                    const float v1 = ((float)((rw[k >> 2] >> (8 * (k & 3))) & 255u) - 128.f) * (1.f / 128.f);
+                    o[k] = bf2_bits(__floats2bfloat162_rn(v0, v1));
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < 8; ++k) o[k] = 0u;
             }
-            X[i] = v;
+            uint4* dst = reinterpret_cast<uint4*>(X + s * 1024 + yy * 32 + 8 * c);
+            dst[0] = make_uint4(o[0], o[1], o[2], o[3]);
+            dst[1] = make_uint4(o[4], o[5], o[6], o[7]);
         }
         __syncthreads();
 
@@ -472,8 +552,7 @@ __global__ void __launch_bounds__(256, 3) trunk_tc_kernel(const PropFrame* __res
                 rw.ox[0][h] = g & 3;
             }
             float acc[1][1][4] = {};
-            conv32<8, 1, 1>(A2h, W3, rw, nt, acc, g, t);
-            conv32<8, 1, 1>(A2l, W3, rw, nt, acc, g, t);
+            conv32_hl<8, 1>(A2h, A2l, W3, rw, nt, acc, g, t);
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int c = nt * 8 + 2 * t;
@@ -493,8 +572,7 @@ __global__ void __launch_bounds__(256, 3) trunk_tc_kernel(const PropFrame* __res
                 rw.ox[0][h] = g & 1;
             }
             float acc[1][1][4] = {};
-            conv32<4, 1, 1>(A3h, W4, rw, warp, acc, g, t);
-            conv32<4, 1, 1>(A3l, W4, rw, warp, acc, g, t);
+            conv32_hl<4, 1>(A3h, A3l, W4, rw, warp, acc, g, t);
             const int s = g >> 2, pix = g & 3, c = warp * 8 + 2 * t;
             if (s < ns) {
                 const float z0 = acc[0][0][0] + sb[3][c], z1 = acc[0][0][1] + sb[3][c + 1];
