@@ -197,7 +197,6 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
     constexpr int NMB = TXB * TYB;        // blocks per tile
     constexpr int GA = B / 4;             // phase-A lanes per block
     constexpr int WPB = B / 4;            // 4-byte words per block row
-    constexpr int RPL = B * WPB / 4;      // phase-C rows per lane (4 lanes per block)
     constexpr int LPB = dcds_lanes_per_block(B);  // phase-B lanes per block
     using GM = GroupMap<B, LPB>;
     constexpr int RPLB = GM::RPL, CPL = GM::CPL, RSB = GM::RS;
@@ -219,7 +218,6 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
     uint32_t* bm_all = reinterpret_cast<uint32_t*>(ring + NMB);  // one +-R visited bitmap per group
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
-    const int ngroups = blockDim.x >> 2;  // phase-C groups (4 lanes per block)
 
     for (int i = tid; i < (int)(blockDim.x / LPB) * nwb; i += blockDim.x) bm_all[i] = 0u;
     // failure-detection test hook (last counter word, zero unless the host set it):
@@ -615,13 +613,14 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
             }
         }
         if constexpr (EVAL) {
-            // ---- phase C: squared error of every ring block at its final MV (dense, 4 lanes per block) ----
+            // ---- phase C: squared error of every ring block at its final MV (dense; lanes per
+            // block and their words as in phase B) ----
             __syncthreads();
             const int nring = s_ring_n;
-            constexpr int RS4 = 4 / WPB;  // a lane's row step (rows interleaved as in phase B)
-            const int gq = tid >> 2, l4 = lane & 3;
-            const int wb = l4 % WPB, rb = l4 / WPB;
-            for (int base = 0; base < nring; base += ngroups) {
+            const int gq = tid / LPB, lg = lane % LPB;
+            const int col0 = GM::col0(lg), row0 = GM::row0(lg);
+            const int ngroups_c = blockDim.x / LPB;
+            for (int base = 0; base < nring; base += ngroups_c) {
                 const int i = base + gq;
                 const bool ok = i < nring;
                 uint32_t q = 0u, fw = 0u, fsad = 0u;
@@ -634,25 +633,29 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
                     fsad = e.y & 0xffffu;
                     fnsp = (int)(e.y >> 16);
                     const int bxl = mb % TXB, byl = mb / TXB;
-                    if (mv_fs && l4 == 0) fw = __ldg(mv_fs + (size_t)(by0 + byl) * NBX + bx0 + bxl);
-                    const int c0 = rx + bxl * B + 4 * wb + dx;
-                    const uint8_t* p0 = win + (R + byl * B + rb + dy) * WP + (c0 & ~3);
+                    if (mv_fs && lg == 0) fw = __ldg(mv_fs + (size_t)(by0 + byl) * NBX + bx0 + bxl);
+                    const int c0 = rx + bxl * B + 4 * col0 + dx;
+                    const uint8_t* p0 = win + (R + byl * B + row0 + dy) * WP + (c0 & ~3);
                     const unsigned s0 = (unsigned)(c0 & 3) * 8u;
-                    const uint32_t* cp = reinterpret_cast<const uint32_t*>(curS + (byl * B + rb) * kTile +
-                                                                           bxl * B + 4 * wb);
+                    const uint32_t* cp = reinterpret_cast<const uint32_t*>(curS + (byl * B + row0) * kTile +
+                                                                           bxl * B + 4 * col0);
 #pragma unroll
-                    for (int r = 0; r < RPL; ++r) {
-                        const uint32_t l0 = ld_word(p0 + r * RS4 * WP, gw);
-                        const uint32_t h0 = ld_word(p0 + r * RS4 * WP + 4, gw);
-                        const uint32_t cw0 =
-                            ld_word(reinterpret_cast<const uint8_t*>(cp + r * RS4 * (kTile / 4)), gc);
-                        const uint32_t d = __vabsdiffu4(__funnelshift_r(l0, h0, s0), cw0);
-                        q = __dp4a(d, d, q);
+                    for (int r = 0; r < RPLB; ++r) {
+                        uint32_t w[CPL + 1];
+#pragma unroll
+                        for (int j = 0; j <= CPL; ++j) w[j] = ld_word(p0 + r * RSB * WP + 4 * j, gw);
+#pragma unroll
+                        for (int j = 0; j < CPL; ++j) {
+                            const uint32_t cw0 =
+                                ld_word(reinterpret_cast<const uint8_t*>(cp + r * RSB * (kTile / 4) + j), gc);
+                            const uint32_t d = __vabsdiffu4(__funnelshift_r(w[j], w[j + 1], s0), cw0);
+                            q = __dp4a(d, d, q);
+                        }
                     }
                 }
-                q += __shfl_xor_sync(FULL, q, 1);
-                q += __shfl_xor_sync(FULL, q, 2);
-                if (ok && l4 == 0)
+#pragma unroll
+                for (int o = 1; o < LPB; o <<= 1) q += __shfl_xor_sync(FULL, q, o);
+                if (ok && lg == 0)
                     eval_block(dx, dy, fsad, q, fnsp, out_nsp != nullptr, mv_fs != nullptr, fw, B * B, esum, edist);
             }
             // this tile's sums: one atomic per warp and counter
