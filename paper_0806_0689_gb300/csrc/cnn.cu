@@ -201,7 +201,7 @@ __device__ __forceinline__ void conv32(const uint32_t* __restrict__ in, const ui
 // conv32 over an activation held as hi and lo bf16 parts (the same layout
 // twice): each weight fragment is loaded once for both parts, and the taps
 // are unrolled so that the weight loads of later taps issue early.
-template <int HIN, int NM>
+template <int HIN, int NM, int ROWP>
 __device__ __forceinline__ void conv32_hl(const uint32_t* __restrict__ hi, const uint32_t* __restrict__ lo,
                                           const uint32_t* __restrict__ Wl, const Rows<NM> rw, int n0,
                                           float (&acc)[NM][1][4], int g, int t)
@@ -215,7 +215,7 @@ __device__ __forceinline__ void conv32_hl(const uint32_t* __restrict__ hi, const
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int y = 2 * rw.oy[i][h] + ky - 1, x = 2 * rw.ox[i][h] + kx - 1;
-                pix[i][h] = (y >= 0 && y < HIN && x >= 0 && x < HIN) ? ((rw.s[i][h] * HIN + y) * HIN + x) * PXW : -1;
+                pix[i][h] = (y >= 0 && y < HIN && x >= 0 && x < HIN) ? (rw.s[i][h] * HIN + y) * ROWP + x * PXW : -1;
             }
 #pragma unroll
         for (int half = 0; half < 2; ++half) {
@@ -293,7 +293,13 @@ __device__ __forceinline__ uint64_t tc_desc(uint32_t addr, uint32_t lbo, uint32_
            ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
 }
 
-constexpr int TC_A23 = 2 * TC_S * (64 + 16) * PXW;  // words of A2 and A3, hi and lo
+// row pitches (words) of the layer-2 and layer-3 outputs: a fragment's 8
+// pixels then sit on 8 different groups of 4 banks (layer 3 reads rows 2
+// apart: 2 * TC_R8 = 16 mod 32; layer 4 rows 2 and samples 4 rows apart:
+// 2 * TC_R4 = 8 and 4 * TC_R4 = 16 mod 32, pixels 2 apart 4)
+constexpr int TC_R8 = 8 * PXW + 8;
+constexpr int TC_R4 = 4 * PXW + 12;
+constexpr int TC_A23 = 2 * TC_S * (8 * TC_R8 + 4 * TC_R4);  // words of A2 and A3, hi and lo
 static_assert(TC_A23 * 4 <= TC_A1, "the layer-2/3 outputs fit in the layer-1 planes");
 
 __global__ void __launch_bounds__(256, 3) trunk_tc_kernel(const PropFrame* __restrict__ fr, int nframes, long sbase,
@@ -305,10 +311,10 @@ __global__ void __launch_bounds__(256, 3) trunk_tc_kernel(const PropFrame* __res
     uint8_t* A1 = base;                                                 // parity-split layer-1 output
     uint8_t* W2c = A1 + TC_A1;                                          // layer-2 weights, core layout
     uint32_t* X = reinterpret_cast<uint32_t*>(W2c + TC_W2);             // [TC_S][32][32] feature words
-    uint32_t* A2h = reinterpret_cast<uint32_t*>(A1);                    // [TC_S][8][8][PXW], in A1
-    uint32_t* A2l = A2h + TC_S * 64 * PXW;
-    uint32_t* A3h = A2l + TC_S * 64 * PXW;                              // [TC_S][4][4][PXW]
-    uint32_t* A3l = A3h + TC_S * 16 * PXW;
+    uint32_t* A2h = reinterpret_cast<uint32_t*>(A1);                    // [TC_S][8] rows of TC_R8 words, in A1
+    uint32_t* A2l = A2h + TC_S * 8 * TC_R8;
+    uint32_t* A3h = A2l + TC_S * 8 * TC_R8;                             // [TC_S][4] rows of TC_R4 words
+    uint32_t* A3l = A3h + TC_S * 4 * TC_R4;
     __shared__ float sb[LAYERS][CH];
     __shared__ int s_fr[TC_S], s_px[TC_S], s_py[TC_S];
     __shared__ const uint8_t* s_cur[TC_S];
@@ -532,7 +538,7 @@ __global__ void __launch_bounds__(256, 3) trunk_tc_kernel(const PropFrame* __res
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
             const int i = 32 * warp + lane;
             const int oy = i >> 4, s = (i >> 3) & 1, ox = i & 7;
-            const int o = ((s * 8 + oy) * 8 + ox) * PXW;
+            const int o = (s * 8 + oy) * TC_R8 + ox * PXW;
 #pragma unroll
             for (int c = 0; c < 32; c += 2)
                 split_relu(__uint_as_float(v[c]) + sb[1][c], __uint_as_float(v[c + 1]) + sb[1][c + 1],
@@ -552,11 +558,11 @@ __global__ void __launch_bounds__(256, 3) trunk_tc_kernel(const PropFrame* __res
                 rw.ox[0][h] = g & 3;
             }
             float acc[1][1][4] = {};
-            conv32_hl<8, 1>(A2h, A2l, W3, rw, nt, acc, g, t);
+            conv32_hl<8, 1, TC_R8>(A2h, A2l, W3, rw, nt, acc, g, t);
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int c = nt * 8 + 2 * t;
-                const int o = ((s * 4 + rw.oy[0][h]) * 4 + rw.ox[0][h]) * PXW + nt * 4 + t;
+                const int o = (s * 4 + rw.oy[0][h]) * TC_R4 + rw.ox[0][h] * PXW + nt * 4 + t;
                 split_relu(acc[0][0][2 * h] + sb[2][c], acc[0][0][2 * h + 1] + sb[2][c + 1], A3h[o], A3l[o]);
             }
         }
@@ -572,7 +578,7 @@ __global__ void __launch_bounds__(256, 3) trunk_tc_kernel(const PropFrame* __res
                 rw.ox[0][h] = g & 1;
             }
             float acc[1][1][4] = {};
-            conv32_hl<4, 1>(A3h, A3l, W4, rw, warp, acc, g, t);
+            conv32_hl<4, 1, TC_R4>(A3h, A3l, W4, rw, warp, acc, g, t);
             const int s = g >> 2, pix = g & 3, c = warp * 8 + 2 * t;
             if (s < ns) {
                 const float z0 = acc[0][0][0] + sb[3][c], z1 = acc[0][0][1] + sb[3][c + 1];
