@@ -6,7 +6,8 @@
 //
 // GPU mapping
 //   * Persistent CTAs pull 128x128-pixel tiles from a global counter (the work
-//     queue over every frame pair of the launch).  For each tile the TMA unit
+//     queue over every frame pair of the launch; a CTA's first tile is its
+//     own index).  For each tile the TMA unit
 //     copies the reference window (the tile grown by R rows and by R rounded
 //     up to 16 columns, zero-filled outside the frame) and the current tile
 //     into shared memory (cp.async.bulk.tensor.2d, completion on an
@@ -14,13 +15,14 @@
 //     searched.
 //   * Phase A (step 1 for every block, warp-uniform): a warp takes one tile
 //     row of blocks per pass (two rows for the search alone), B/4 lanes per
-//     block, lane w holding 4-pixel column w of the block.  The five horizontal HCSP points share each reference row
-//     (three aligned words and four funnel shifts), the two vertical points
+//     block, lane w holding 4-pixel column w of the block.  The five
+//     horizontal HCSP points share each reference row (three aligned words
+//     and four funnel shifts), the two vertical points
 //     reuse the neighbouring rows, so the 7 SADs cost 18 rows of reads.
 //     Blocks whose centre wins are finished (the half-way stop, Sec. III-C);
 //     the others go to a per-tile ring in shared memory.
-//   * Phase B (steps 2-4): groups of 4 lanes pull blocks from the ring and
-//     run the diamond rounds.  A round evaluates every new point of the
+//   * Phase B (steps 2-4): groups of LPB lanes per block (2 for 16x16, 4
+//     for 8x8) pull blocks from the ring and run the diamond rounds.  A round evaluates every new point of the
 //     current pattern (at most 4) at once, then applies the switching
 //     strategies.  A per-group bitmap of visited points (one bit per
 //     displacement of the +-R window) keeps points from being evaluated or
@@ -34,9 +36,10 @@
 //     takes one pass over the block at that MV (during the HCSP for blocks
 //     whose centre wins; for the others in a dense pass over the ring after
 //     the rounds, where phase B left each block's final MV, SAD and count),
-//     the MV is compared with the full-search MV, and each warp adds its
-//     tile sums to the frame's eight counters with integer atomics -- the
-//     same sums the evaluation kernel computes.
+//     the MV is compared with the full-search MV, and the tile's sums (the
+//     warps' totals met in shared memory) go to the frame's eight counters
+//     with one set of integer atomics per tile -- the same sums the
+//     evaluation kernel computes.
 #include "dcds_common.cuh"
 
 #include <algorithm>
