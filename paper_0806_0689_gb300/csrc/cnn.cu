@@ -1,17 +1,20 @@
 // cnn.cu -- kernels of the learned start proposal (not in the paper; the
 // task adds it): a 4-layer 3x3 stride-2 convolutional trunk over a block's
 // 32x32 neighbourhood, and a linear head producing 33 dx, 33 dy and 2 H/V
-// logits.  Convolutions run as im2col + a BF16 tensor-core GEMM with FP32
-// accumulation (mma.sync m16n8k16); the small head, the loss and the
-// optimiser run on the CUDA cores in FP32.
+// logits.  Training runs the convolutions as im2col + a BF16 tensor-core GEMM
+// with FP32 accumulation (mma.sync m16n8k16); the small head, the loss and
+// the optimiser run on the CUDA cores in FP32, every reduction in a fixed
+// order.  Inference runs the fused trunk (trunk_tc_kernel, layer 2 on
+// tcgen05) with each activation carried as two bf16 parts.
 //
 // Layouts: activations are NHWC ([sample][y][x][channel]); an im2col row is
 // one output pixel, its column k = (ky * 3 + kx) * Cin + c, zero-padded to
 // Kp = a multiple of 32.  GEMM weights are [32][Kp] in the same column order.
 // The canonical parameter vector (the order the host sees) is
 // conv1.w [32][2][3][3], conv1.b, conv2.w [32][32][3][3], conv2.b, conv3.*,
-// conv4.*, fc.w [68][134], fc.b; the head's 134 inputs are the 128 conv-4
-// outputs in (c, y, x) order followed by 6 neighbour-MV scalars.
+// conv4.*, fc.w [68][NFEAT], fc.b; the head's NFEAT = 136 inputs are the 128
+// conv-4 outputs in (c, y, x) order followed by the NSCAL = 8 neighbour
+// scalars (left, top and top-right MVs, then their component-wise median).
 #include "me_cnn.cuh"
 
 #include <algorithm>

@@ -2,17 +2,20 @@
 // task adds it): features, training step, inference and the learned-start
 // search.
 //
-// Features of a 16x16 block at (px, py): the current block centred in a zero
-// 32x32 canvas, the 32x32 reference patch at the same origin (coordinates
-// clamped to the frame), both as (p - 128) / 128; and the final MVs of the
-// left, top and top-right blocks divided by 16 (zero where absent).
+// Features of a 16x16 region at (px, py): the current region centred in a
+// zero 32x32 canvas, the 32x32 reference patch at the same origin
+// (coordinates clamped to the frame), both as (p - 128) / 128; and the final
+// MVs of the left, top and top-right blocks of the region's top-left block,
+// then their component-wise median, divided by 16 (zero where absent).  With
+// 8x8 blocks one proposal serves the region's four blocks.
 //
 // Training labels come from a motion field (the full-search field computed
 // by this library): dx, dy clamped to +-16 (classes 0..32) and H/V = 0 when
 // |mvx| >= |mvy|, else 1.  The neighbour scalars use the same field.
 //
-// Learned-start search: blocks are processed in wavefront order (t = bx + 2 by)
-// so that the left, top and top-right blocks are final first.  The same kernel
+// Learned-start search: blocks are processed in wavefront order (16x16:
+// t = bx + 2 by; 8x8: regions by t = rx + ry, a region's four blocks
+// together) so that the left, top and top-right neighbours are final first.  The same kernel
 // runs the non-learned control: the start is the component-wise median of the
 // three neighbours' MVs (an absent neighbour counts as (0,0)) and the prior is
 // vertical when its |dy| > |dx|.  Per block, one
