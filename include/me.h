@@ -271,7 +271,10 @@ int me_estimate_host_batch(me_ctx* ctx, const me_frame_desc* descs, const int16_
 /*   16: 8 scalars;                                                           */
 /*   network: 4 conv 3x3 stride 2 (32 channels, ReLU) then a linear head to  */
 /*   68 logits (dx in [-16,16], dy in [-16,16], H/V).  Convolutions run on    */
-/*   the BF16 tensor cores with FP32 accumulation.                            */
+/*   the BF16 tensor cores with FP32 accumulation, weights rounded to bf16;  */
+/*   inference carries each activation as two bf16 parts (hi + lo), so the   */
+/*   logits follow the network with exact activations (to about 2e-4 for    */
+/*   trained weights); training rounds each activation once to bf16.         */
 /*   parameters (host float, this order): conv1.w [32][2][3][3], conv1.b      */
 /*   [32], conv2.w [32][32][3][3], conv2.b, conv3.w, conv3.b, conv4.w,        */
 /*   conv4.b, fc.w [68][136], fc.b [68]; fc inputs are the 128 conv-4         */
@@ -285,8 +288,9 @@ int me_estimate_host_batch(me_ctx* ctx, const me_frame_desc* descs, const int16_
 typedef struct me_proposal me_proposal;
 enum { ME_PROPOSAL_NPARAMS = 37668, ME_PROPOSAL_NLOGITS = 68 };
 
-/* Create (all parameters zero: the proposal is then the origin with a
- * horizontal prior, which makes the learned search equal to DCDS) / free. */
+/* Create (all parameters zero: the network then proposes the origin with a
+ * horizontal prior, so the learned search starts from the better of the
+ * origin and the neighbours' median) / free. */
 int me_proposal_create(me_ctx* ctx, me_proposal** out);
 void me_proposal_free(me_proposal* p);
 /* Copy ME_PROPOSAL_NPARAMS floats in / out (HOST arrays).  Setting the
