@@ -160,50 +160,11 @@ struct Rows {
     int s[NM][2], oy[NM][2], ox[NM][2];
 };
 
-// One 3x3 stride-2 layer with 32 input channels (implicit GEMM, K = 9 taps x 32)
-// for NM m-tiles and NN n-tiles (from n-tile n0) per warp, added to acc.
-template <int HIN, int NM, int NN>
-__device__ __forceinline__ void conv32(const uint32_t* __restrict__ in, const uint32_t* __restrict__ Wl,
-                                       const Rows<NM> rw, int n0, float (&acc)[NM][NN][4], int g, int t)
-{
-#pragma unroll 1
-    for (int tap = 0; tap < 9; ++tap) {
-        const int ky = tap / 3, kx = tap - 3 * ky;
-        int pix[NM][2];  // word offset of the input pixel, -1 outside (zero padding)
-#pragma unroll
-        for (int i = 0; i < NM; ++i)
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int y = 2 * rw.oy[i][h] + ky - 1, x = 2 * rw.ox[i][h] + kx - 1;
-                pix[i][h] = (y >= 0 && y < HIN && x >= 0 && x < HIN) ? ((rw.s[i][h] * HIN + y) * HIN + x) * PXW : -1;
-            }
-#pragma unroll
-        for (int half = 0; half < 2; ++half) {
-            const int w0 = half * 8 + t;  // channel pair 2*w0 (and +8 channels)
-            uint32_t bf[NN][2];
-#pragma unroll
-            for (int j = 0; j < NN; ++j) {
-                const uint32_t* wr = Wl + (size_t)((n0 + j) * 8 + g) * 144 + tap * 16 + half * 8 + t;
-                bf[j][0] = __ldg(wr);
-                bf[j][1] = __ldg(wr + 4);
-            }
-#pragma unroll
-            for (int i = 0; i < NM; ++i) {
-                uint32_t a[4];
-                a[0] = pix[i][0] >= 0 ? in[pix[i][0] + w0] : 0u;
-                a[1] = pix[i][1] >= 0 ? in[pix[i][1] + w0] : 0u;
-                a[2] = pix[i][0] >= 0 ? in[pix[i][0] + w0 + 4] : 0u;
-                a[3] = pix[i][1] >= 0 ? in[pix[i][1] + w0 + 4] : 0u;
-#pragma unroll
-                for (int j = 0; j < NN; ++j) mma_bf16(acc[i][j], a, bf[j]);
-            }
-        }
-    }
-}
-
-// conv32 over an activation held as hi and lo bf16 parts (the same layout
-// twice): each weight fragment is loaded once for both parts, and the taps
-// are unrolled so that the weight loads of later taps issue early.
+// One 3x3 stride-2 layer with 32 input channels (implicit GEMM, K = 9 taps x
+// 32) over an activation held as hi and lo bf16 parts (the same layout twice,
+// rows ROWP words apart), for NM m-tiles of n-tile n0 per warp, added to acc:
+// each weight fragment is loaded once for both parts, and the taps are
+// unrolled so that the weight loads of later taps issue early.
 template <int HIN, int NM, int ROWP>
 __device__ __forceinline__ void conv32_hl(const uint32_t* __restrict__ hi, const uint32_t* __restrict__ lo,
                                           const uint32_t* __restrict__ Wl, const Rows<NM> rw, int n0,
