@@ -349,8 +349,9 @@ int me_proposal_logits(me_ctx* ctx, me_proposal* p, const me_frame_desc* desc, f
  * their proposal reads are final first (16x16: t = bx + 2 by; 8x8: regions by
  * t = rx + ry, the four blocks of a region together).  The head turns those
  * MVs, their median and the region's conv features into a start (argmax of
- * the dx and dy heads, ties to the class nearest 0) and a prior (V when its
- * logit is larger).  For each block of the region the median and the start
+ * the dx and dy heads, ties to the class nearest 0; the origin instead when
+ * the network is not confident: the product of the two heads' softmax
+ * maxima below 0.6) and a prior (V when its logit is larger).  For each block of the region the median and the start
  * are clamped to the block's window and frame; the origin, the median and
  * the start are evaluated in this order, the best one (the earliest on a
  * tie) centres the first pattern (HCSP, or its transpose for a V prior), then

@@ -427,11 +427,24 @@ def mvp_counts(frames, R):
     return out
 
 
+START_GATE = 0.6
+
+
+def start_confidence(logits):
+    """Product of the softmax maxima of the dx and dy heads (fp64)."""
+    z = np.asarray(logits, np.float64)
+    p = 1.0
+    for seg in (z[:33], z[33:66]):
+        p /= float(np.sum(np.exp(seg - seg.max())))
+    return p
+
+
 def cnn_raw_start(logits):
     """(sx, sy, prior_v) from logits before clamping: the argmax of the dx and
     dy heads (ties go to the class nearest the centre, checked in the order
-    0, -1, +1, -2, +2, ...); vertical prior when the V logit is strictly
-    larger."""
+    0, -1, +1, -2, +2, ...), replaced by the origin when the network is not
+    confident (start_confidence below START_GATE); vertical prior when the V
+    logit is strictly larger."""
     def centre_out_argmax(z):
         best, bv = 0, z[16]
         for a in range(1, 17):
@@ -439,7 +452,10 @@ def cnn_raw_start(logits):
                 if z[d + 16] > bv:
                     best, bv = d, z[d + 16]
         return best
-    return centre_out_argmax(logits[:33]), centre_out_argmax(logits[33:66]), int(logits[67] > logits[66])
+    sx, sy = centre_out_argmax(logits[:33]), centre_out_argmax(logits[33:66])
+    if start_confidence(logits) < START_GATE:
+        sx, sy = 0, 0
+    return sx, sy, int(logits[67] > logits[66])
 
 
 def learned_dcds(cur, ref, rng, params, block=16):

@@ -21,7 +21,8 @@
 // vertical when its |dy| > |dx|.  Per block, one
 // warp waits for those three (acquire loads, bounded), runs the head on the
 // precomputed conv-4 features and the neighbours' MVs, picks the start (argmax
-// of the dx and dy heads, ties to the class nearest the centre) and the prior
+// of the dx and dy heads, ties to the class nearest the centre; the origin
+// unless the product of the two heads' softmax maxima is at least 0.6) and the prior
 // (V when its logit is larger), and searches: the origin, the neighbours'
 // median (learned start only) and the start are evaluated in this order, the
 // best one (the earliest on a tie) centres the first pattern (the HCSP, or
@@ -196,6 +197,10 @@ __device__ __forceinline__ void st_relaxed64(unsigned long long* p, unsigned lon
 
 constexpr uint32_t kSpinLimit = 1u << 22;
 constexpr uint32_t kShortSpin = 1u << 12;  // the limit under the failure-detection test hook
+// Confidence the learned start needs (product of the dx and dy heads' softmax
+// maxima); below it the network proposes the origin.  Chosen among 0.2, 0.4
+// and 0.6 on the held-out comparisons with the neighbour-median control.
+constexpr float kStartGate = 0.6f;
 
 struct WarpBlock {
     const uint32_t* win;  // the block's reference window, staged in this warp's shared memory
@@ -534,6 +539,19 @@ __global__ void __launch_bounds__(256) learned_dcds_kernel(const PropFrame* __re
             sy = cy_ - 16;
             const float zh = __shfl_sync(0xffffffffu, z[2], 2), zv = __shfl_sync(0xffffffffu, z[2], 3);
             pv = zv > zh ? 1 : 0;
+            {
+                // the network's start only when it is confident: the softmax maxima of
+                // the dx and dy heads (1 / sum of exp(z - max)) multiply to kStartGate
+                // or more; otherwise the start is the origin (the prior stays)
+                float ex = expf(z[0] - vx) + (lane == 0 ? expf(z[1] - vx) : 0.f);
+                float ey = (lane >= 1 ? expf(z[1] - vy) : 0.f) + (lane <= 1 ? expf(z[2] - vy) : 0.f);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    ex += __shfl_xor_sync(0xffffffffu, ex, o);
+                    ey += __shfl_xor_sync(0xffffffffu, ey, o);
+                }
+                if (1.f < kStartGate * ex * ey) { sx = 0; sy = 0; }
+            }
         } else {
             // neighbour-median start (absent neighbours count as (0,0))
             sx = medx;

@@ -78,19 +78,48 @@ def test_search_from_closed_forms():
 
 
 def test_start_choice_centre_out():
+    # confident heads (one class 30 above the rest): the start is the argmax,
+    # clamped to the block's window and frame
     z = np.zeros(68)
     assert oracle.cnn_start(z, 160, 160, 352, 288, 16) == (0, 0, 0)
-    z[16 + 3] = 1.0
-    z[33 + 16 - 5] = 2.0
+    z[16 + 3] = 30.0
+    z[33 + 16 - 5] = 30.0
     z[67] = 0.5
     assert oracle.cnn_start(z, 160, 160, 352, 288, 16) == (3, -5, 1)
-    z2 = np.zeros(68)
-    z2[16 - 2] = z2[16 + 2] = 1.0  # tie between -2 and +2 -> -2 (checked first)
-    assert oracle.cnn_start(z2, 160, 160, 352, 288, 16)[0] == -2
     z3 = np.zeros(68)
-    z3[0] = 1.0  # dx = -16 clamped by the frame at the left border
+    z3[0] = 30.0  # dx = -16 clamped by the frame at the left border
+    z3[33 + 16] = 30.0
     assert oracle.cnn_start(z3, 16, 160, 352, 288, 16)[0] == -16
     assert oracle.cnn_start(z3, 0, 160, 352, 288, 16)[0] == 0
+
+
+def test_start_gate_closed_form():
+    """The network's start is kept only when the product of the dx and dy heads'
+    softmax maxima reaches 0.6.  One class at logit L and 32 at 0 give a
+    maximum of e^L / (e^L + 32); both heads at L = ln 128 give 0.8^2 = 0.64,
+    at L = ln 96 0.75^2 = 0.5625.  Ties between two classes split the maximum
+    (the tie rule still picks the class nearest the centre)."""
+    def heads(L, dx, dy):
+        z = np.zeros(68)
+        z[16 + dx] = L
+        z[33 + 16 + dy] = L
+        return z
+    z = heads(np.log(128.0), 4, -2)
+    assert abs(oracle.start_confidence(z) - 0.64) < 1e-12
+    assert oracle.cnn_raw_start(z)[:2] == (4, -2)
+    z = heads(np.log(96.0), 4, -2)
+    assert abs(oracle.start_confidence(z) - 0.5625) < 1e-12
+    assert oracle.cnn_raw_start(z)[:2] == (0, 0)
+    # uniform heads: 1/33^2, far below the gate; the prior is still the network's
+    z = np.zeros(68)
+    z[67] = 1.0
+    assert oracle.cnn_raw_start(z) == (0, 0, 1)
+    # a two-way tie at a large margin: each maximum 1/2, so 1/4 < 0.6 -> origin
+    z = np.zeros(68)
+    z[16 - 2] = z[16 + 2] = 40.0
+    z[33 + 16] = 40.0
+    assert abs(oracle.start_confidence(z) - 0.5) < 1e-12
+    assert oracle.cnn_raw_start(z)[:2] == (0, 0)
 
 
 def test_features_closed_form():
