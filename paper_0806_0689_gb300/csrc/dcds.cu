@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
 
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t s_bar[NST];
-    __shared__ int s_tile[NST], s_frame[NST];
+    __shared__ int s_tile[NST];
     __shared__ TileDesc s_desc[NST];
     __shared__ unsigned long long s_part[EVAL ? 8 : 1][6];  // EVAL: the warps' tile sums
     __shared__ int s_ring_n, s_ring_next;
@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
         // a CTA's first tile is its own index (the grid never exceeds the tile
         // count), later ones come from the counter: the launch does not open with
         // every CTA queueing on the counter's one word
-        issue_tile((int)blockIdx.x, frames, nframes, ntiles, smem, cur_off, TH, &s_bar[0], &s_tile[0], &s_frame[0],
+        issue_tile((int)blockIdx.x, frames, nframes, ntiles, smem, cur_off, TH, &s_bar[0], &s_tile[0],
                    &s_desc[0], starve ? 16u : 0u);
     }
     __syncthreads();
@@ -258,7 +258,7 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
             // stage st^1 was last read in the previous tile, which ended with a barrier
             fence_proxy_async();
             issue_tile((int)gridDim.x + atomicAdd(head, 1), frames, nframes, ntiles, smem + (st ^ 1) * stage_bytes,
-                       cur_off, TH, &s_bar[st ^ 1], &s_tile[st ^ 1], &s_frame[st ^ 1], &s_desc[st ^ 1]);
+                       cur_off, TH, &s_bar[st ^ 1], &s_tile[st ^ 1], &s_desc[st ^ 1]);
         }
         // descriptor fields in registers (from the claim's shared copy): the
         // output stores below cannot alias them
@@ -699,7 +699,7 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
         if (NST == 1 && tid == 0) {
             fence_proxy_async();
             issue_tile((int)gridDim.x + atomicAdd(head, 1), frames, nframes, ntiles, smem, cur_off, TH, &s_bar[0],
-                       &s_tile[0], &s_frame[0], &s_desc[0]);
+                       &s_tile[0], &s_desc[0]);
         }
     }
 }

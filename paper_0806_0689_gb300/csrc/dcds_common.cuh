@@ -130,13 +130,13 @@ struct TileDesc {
     int w, h, range, nbx, nby, tile_x, tile_y, first;  // first: the frame's first tile (writes its counts)
 };
 
-// Thread 0: take tile t into stage `st`: publish its index, frame and
-// descriptor, then arm the stage's mbarrier with the byte count and start the
-// two TMA copies.  A tile index past the end completes the phase with no data.
+// Thread 0: take tile t into stage `st`: publish its index and descriptor,
+// then arm the stage's mbarrier with the byte count and start the two TMA
+// copies.  A tile index past the end completes the phase with no data.
 // extra_tx > 0 arms the barrier for more bytes than the copies deliver (the
 // failure-detection test hook: the wait on this stage then runs out).
 __device__ inline void issue_tile(int t, const FrameDev* frames, int nframes, int ntiles, uint8_t* stage,
-                           int cur_off, int tile_h, uint64_t* bar, int* s_tile, int* s_frame, TileDesc* desc,
+                           int cur_off, int tile_h, uint64_t* bar, int* s_tile, TileDesc* desc,
                            uint32_t extra_tx = 0)
 {
     *s_tile = t;
@@ -145,7 +145,6 @@ __device__ inline void issue_tile(int t, const FrameDev* frames, int nframes, in
         return;
     }
     const int f = find_frame(frames, nframes, t);
-    *s_frame = f;
     const FrameDev& F = frames[f];
     const int lt = t - F.tile_base;
     const int ty = lt / F.tiles_x, tx = lt - ty * F.tiles_x;
