@@ -25,7 +25,9 @@
 //     for 8x8) pull blocks from the ring and run the diamond rounds.  A round evaluates every new point of the
 //     current pattern (at most 4) at once, then applies the switching
 //     strategies.  A per-group bitmap of visited points (one bit per
-//     displacement of the +-R window) keeps points from being evaluated or
+//     displacement of the +-R window; for 8x8 blocks a 32 x 32 box of
+//     displacements, a block whose path leaves it being searched again after
+//     the pass with +-R bitmaps) keeps points from being evaluated or
 //     counted twice.  A point evaluated earlier always has a SAD no smaller
 //     than the current centre's (every move lowers the best SAD strictly), so
 //     skipping it leaves the path unchanged.
@@ -109,6 +111,20 @@ __device__ __forceinline__ uint32_t ld_word(const uint8_t* p, const Region& g)
 // slower: 32 lanes reading 32 unrelated rows multiply the bank conflicts.
 __host__ __device__ constexpr int dcds_lanes_per_block(int block) { return block == 16 ? 2 : 4; }
 
+// Visited points of an 8x8 block in phase B, in the box variant (BOX): a
+// 32 x 32 box of displacements (-16 .. 15 on each axis; word y + 16, bit
+// x + 16) instead of the +-R bitmap, which at +-32 is four times larger and,
+// over 64 groups, costs a CTA per SM.  A block that meets a point outside the
+// box is dropped (its ring entry still holds the HCSP result) and searched
+// again from the start after the main pass, by one warp with +-R bitmaps: the
+// same path, the same count.  The groups' boxes lie 33 words apart, so that
+// the same row of eight groups' boxes falls in eight banks.  The launcher
+// takes this variant where it fits more CTAs per SM than the +-R bitmaps
+// (2160p 8x8 +-32, 256 threads: three instead of two, 302 -> 275 us for
+// DCDS, 442 -> 376 us for DCDS^S); where both fit as many, the box's extra
+// registers (80 against 64) cost a CTA and it measured 10-12 % slower.
+constexpr int kBoxWords = 33;
+
 // Lanes of a phase-B group: a block of B x B pixels (B / 4 words per row) is
 // split over LPB lanes, each holding CPL adjacent word columns of RPL rows:
 // rows row0, row0 + RS, row0 + 2 RS, ... from column col0.  With more lanes
@@ -188,10 +204,9 @@ __device__ __forceinline__ void eval_block(int dx, int dy, uint32_t sad, uint32_
     e[4] += (unsigned)bb;
 }
 
-template <int B, bool SIMPL, int NST, bool EVAL>
-__global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ frames, int nframes, int ntiles,
-                                                   int max_range, int* __restrict__ head,
-                                                   unsigned* __restrict__ status)
+template <int B, bool SIMPL, int NST, bool EVAL, bool BOX>
+__device__ __forceinline__ void dcds_tiles(const FrameDev* __restrict__ frames, int nframes, int ntiles, int max_range,
+                                           int* __restrict__ head, unsigned* __restrict__ status)
 {
     constexpr int V = kSadVariant;
     constexpr int TH = kDcdsTileH;        // tile height in pixels (width kTile)
@@ -199,7 +214,6 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
     constexpr int TYB = TH / B;           // block rows per tile
     constexpr int NMB = TXB * TYB;        // blocks per tile
     constexpr int GA = B / 4;             // phase-A lanes per block
-    constexpr int WPB = B / 4;            // 4-byte words per block row
     constexpr int LPB = dcds_lanes_per_block(B);  // phase-B lanes per block
     using GM = GroupMap<B, LPB>;
     constexpr int RPLB = GM::RPL, CPL = GM::CPL, RSB = GM::RS;
@@ -210,7 +224,7 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
     __shared__ int s_tile[NST];
     __shared__ TileDesc s_desc[NST];
     __shared__ unsigned long long s_part[EVAL ? 8 : 1][6];  // EVAL: the warps' tile sums
-    __shared__ int s_ring_n, s_ring_next;
+    __shared__ int s_ring_n, s_ring_next, s_novf, s_ovf_next;
 
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     const int cur_off = win_bytes_max(max_range, TH);
@@ -218,11 +232,17 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
     uint2* ring = reinterpret_cast<uint2*>(smem + NST * stage_bytes);
     const int side_max = 2 * max_range + 1;
     const int nwb = (side_max * side_max + 31) / 32;
-    uint32_t* bm_all = reinterpret_cast<uint32_t*>(ring + NMB);  // one +-R visited bitmap per group
+    const int bw = BOX ? kBoxWords : nwb;  // visited words per group in the main pass
+    // one +-R bitmap or visited box per group; BOX: then +-R bitmaps for
+    // the overflow warp's groups and the tile's overflow list
+    uint32_t* bm_all = reinterpret_cast<uint32_t*>(ring + NMB);
+    uint32_t* bm_full = bm_all + (int)(blockDim.x / LPB) * bw;
+    const int nclear = (int)(blockDim.x / LPB) * bw + (BOX ? (32 / LPB) * nwb : 0);
+    int* ovf = reinterpret_cast<int*>(bm_all + nclear);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
 
-    for (int i = tid; i < (int)(blockDim.x / LPB) * nwb; i += blockDim.x) bm_all[i] = 0u;
+    for (int i = tid; i < nclear; i += blockDim.x) bm_all[i] = 0u;
     // failure-detection test hook (last counter word, zero unless the host set it):
     // the first copy is armed for 16 bytes it never receives and the waits are shortened
     const bool starve = head[kCounterInts - 1] != 0;
@@ -243,7 +263,7 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
     for (int it = 0;; ++it) {
         const int st = (NST == 2) ? (it & 1) : 0;
         const uint32_t par = (NST == 2) ? ((it >> 1) & 1) : (it & 1);
-        if (tid == 0) { s_ring_n = 0; s_ring_next = 0; }
+        if (tid == 0) { s_ring_n = 0; s_ring_next = 0; s_novf = 0; s_ovf_next = 0; }
         const bool ok = mbar_wait(&s_bar[st], par, wait_limit);
         if (__syncthreads_or(!ok)) {
             if (tid == 0 && status) atomicOr(status, STATUS_TIMEOUT);
@@ -408,15 +428,30 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
         // evaluated together, (4) the switching strategies pick the next list.
         // A group is LPB lanes: 2 for 16x16 blocks (a warp serves 16 blocks per
         // round, so a round's control costs half of what 4-lane groups pay per
-        // block), 4 for 8x8 blocks (whose +-32 bitmaps would otherwise halve
-        // the CTAs per SM).
-        {
+        // block), 4 for 8x8 blocks.  The pass runs over the ring (list null)
+        // or, for 8x8 blocks, over the ring entries of the blocks that left
+        // their visited box (FULLM: +-R bitmaps, warp 0 only).
+        auto rounds = [&](const int* list, int nlist, int* next, auto full_c) {
+            constexpr bool FULLM = decltype(full_c)::value;
             constexpr unsigned GMASK = (1u << LPB) - 1u;
             const int gq = tid / LPB, lg = lane % LPB, lead = lane & ~(LPB - 1);
             const int col0 = GM::col0(lg), row0 = GM::row0(lg);
-            uint32_t* bm = bm_all + gq * nwb;
+            uint32_t* bm = (BOX && FULLM) ? bm_full + gq * nwb : bm_all + gq * bw;
+            const int bmw = FULLM ? nwb : bw;  // words of this group's bitmap
             const int side = 2 * R + 1;
-            const int nring = s_ring_n;
+            // visited word and bit of displacement (x, y); false: outside the box
+            auto vbit = [&](int x, int y, int& word, int& bitn) {
+                if constexpr (FULLM) {
+                    const int bit = (y + R) * side + (x + R);
+                    word = bit >> 5;
+                    bitn = bit & 31;
+                    return true;
+                } else {
+                    word = y + 16;
+                    bitn = x + 16;
+                    return (unsigned)(word | bitn) < 32u;
+                }
+            };
 
             // group state, identical in the group's lanes
             int act = 0;  // 0: needs a block, 1: searching, 2: done
@@ -440,14 +475,16 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
                 if (need) {
                     const int first = __ffs(need) - 1;
                     int base = 0;
-                    if (lane == first) base = atomicAdd(&s_ring_next, __popc(need));
+                    if (lane == first) base = atomicAdd(next, __popc(need));
                     base = __shfl_sync(FULL, base, first);
                     int idx = base + __popc(need & ((1u << lane) - 1u));
                     idx = __shfl_sync(FULL, idx, lead);
                     if (act == 0) {
-                        if (idx >= nring || !index_ok(idx, NMB, status)) {
+                        if (idx >= nlist || !index_ok(idx, NMB, status) ||
+                            !index_ok(list ? list[idx] : idx, NMB, status)) {
                             act = 2;
                         } else {
+                            if (list) idx = list[idx];
                             const uint2 e = ring[idx];
                             const int mb = (int)(e.x & 255u), hb = (int)((e.x >> 8) & 7u);
                             const int bxl = mb % TXB, byl = mb / TXB;
@@ -479,11 +516,12 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
                             for (int k = lg; k < 7; k += LPB) {
                                 int ox, oy;
                                 decode(kHcsp, k, ox, oy);
-                                if (ox >= dxlo && ox <= dxhi && oy >= dylo && oy <= dyhi) {
-                                    const int bit = (oy + R) * side + (ox + R);
-                                    if (index_ok(bit >> 5, nwb, status)) atomicOr(&bm[bit >> 5], 1u << (bit & 31));
-                                    wmin = min(wmin, bit >> 5);
-                                    wmax = max(wmax, bit >> 5);
+                                int wd, bn;
+                                // the HCSP points (+-2) always fit the box
+                                if (ox >= dxlo && ox <= dxhi && oy >= dylo && oy <= dyhi && vbit(ox, oy, wd, bn)) {
+                                    if (index_ok(wd, bmw, status)) atomicOr(&bm[wd], 1u << bn);
+                                    wmin = min(wmin, wd);
+                                    wmax = max(wmax, wd);
                                 }
                             }
                         }
@@ -504,11 +542,12 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
                 }
                 const bool counted = !(SIMPL && phase == PH_SIDE);
                 unsigned vb = 0u, nb = 0u;  // valid / new points of the list, bit k = point k
+                bool outbox = false;        // a valid point of this lane's outside the visited box
 #pragma unroll
                 for (int i = 0; i < 4 / LPB; ++i) {
                     const int k = i * LPB + lg;
                     bool valid = false, fresh = false;
-                    int bit = 0;
+                    int wd = 0, bn = 0;
                     if (act == 1 && k < npts) {
                         int ox, oy;
                         decode(code, k, ox, oy);
@@ -516,8 +555,10 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
                         valid = x >= dxlo && x <= dxhi && y >= dylo && y <= dyhi;
                         if (valid) {
                             if (counted) {
-                                bit = (y + R) * side + (x + R);
-                                fresh = index_ok(bit >> 5, nwb, status) && ((bm[bit >> 5] >> (bit & 31)) & 1u) == 0u;
+                                if (vbit(x, y, wd, bn))
+                                    fresh = index_ok(wd, bmw, status) && ((bm[wd] >> bn) & 1u) == 0u;
+                                else
+                                    outbox = true;
                             } else {
                                 fresh = (k == 0 ? ds0 : ds1) == kUnknown;
                             }
@@ -532,10 +573,16 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
                     }
                     // the list's points are distinct: marking one leaves the others' checks unchanged
                     if (counted && fresh) {
-                        if (index_ok(bit >> 5, nwb, status)) atomicOr(&bm[bit >> 5], 1u << (bit & 31));
-                        wmin = min(wmin, bit >> 5);
-                        wmax = max(wmax, bit >> 5);
+                        if (index_ok(wd, bmw, status)) atomicOr(&bm[wd], 1u << bn);
+                        wmin = min(wmin, wd);
+                        wmax = max(wmax, wd);
                     }
+                }
+                // a point outside the box: the group drops the block this round
+                bool drop = false;
+                if constexpr (BOX && !FULLM) {
+                    drop = ((__ballot_sync(FULL, outbox) >> lead) & GMASK) != 0u;
+                    if (drop) nb = 0u;
                 }
                 if (SIMPL && phase == PH_DDSP) {
                     ds0 = (vb & 4u) ? kUnknown : kInvalid;
@@ -571,7 +618,17 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
                 }
 
                 // ---- (4) best point of the list, then switching strategies (Sec. III-B) ----
-                if (act == 1) {
+                if (act == 1 && drop) {
+                    // searched again from its HCSP result in the overflow pass
+                    if (lg == 0) {
+                        const int o = atomicAdd(&s_novf, 1);
+                        if (index_ok(o, NMB, status)) ovf[o] = ridx;
+                    }
+                    for (int i = wmin; i <= wmax; ++i)
+                        if (index_ok(i, bmw, status)) bm[i] = 0u;
+                    wmin = INT_MAX; wmax = -1;
+                    act = 0;
+                } else if (act == 1) {
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
                         if (i < ncand) {
@@ -602,7 +659,7 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
                             if (out_nsp) out_nsp[blk] = (uint16_t)nsp;
                         }
                         for (int i = wmin; i <= wmax; ++i)
-                            if (index_ok(i, nwb, status)) bm[i] = 0u;
+                            if (index_ok(i, bmw, status)) bm[i] = 0u;
                         wmin = INT_MAX; wmax = -1;
                         act = 0;
                         // the ring entry now holds the final result for the evaluation pass
@@ -614,6 +671,14 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
                 }
                 __syncwarp();  // bitmap updates and clears are ordered before the next round
             }
+        };
+        if constexpr (BOX) {
+            rounds(nullptr, s_ring_n, &s_ring_next, std::false_type{});
+            __syncthreads();  // every dropped block is on the overflow list
+            const int novf = s_novf;
+            if (novf > 0 && warp == 0) rounds(ovf, novf, &s_ovf_next, std::true_type{});
+        } else {
+            rounds(nullptr, s_ring_n, &s_ring_next, std::true_type{});
         }
         if constexpr (EVAL) {
             // ---- phase C: squared error of every ring block at its final MV (dense; lanes per
@@ -704,24 +769,70 @@ __global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ 
     }
 }
 
+// The +-R visited bitmaps (every block size, with or without the fused sums).
+template <int B, bool SIMPL, int NST, bool EVAL>
+__global__ void __launch_bounds__(256) dcds_kernel(const FrameDev* __restrict__ frames, int nframes, int ntiles,
+                                                   int max_range, int* __restrict__ head,
+                                                   unsigned* __restrict__ status)
+{
+    dcds_tiles<B, SIMPL, NST, EVAL, false>(frames, nframes, ntiles, max_range, head, status);
+}
+
+// 8x8 blocks with visited boxes (the search alone): at most 80 registers, so
+// that three 256-thread CTAs fit an SM.
+template <bool SIMPL, int NST>
+__global__ void __launch_bounds__(256, 3) dcds_box_kernel(const FrameDev* __restrict__ frames, int nframes,
+                                                          int ntiles, int max_range, int* __restrict__ head,
+                                                          unsigned* __restrict__ status)
+{
+    dcds_tiles<8, SIMPL, NST, false, true>(frames, nframes, ntiles, max_range, head, status);
+}
+
+// Sets the attributes a launch of kern with smem bytes of dynamic shared
+// memory needs; per_sm: its CTAs per SM.
+template <typename K>
+cudaError_t occupancy(K kern, size_t smem, int threads, int& per_sm)
+{
+    per_sm = 0;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+    return e;
+}
+
+template <typename K>
+cudaError_t launch_k(K kern, size_t smem, int per_sm, const FrameDev* frames, int nframes, int ntiles, int max_range,
+                     const Shape& s, int* head, unsigned* status, int num_sms, cudaStream_t st)
+{
+    if (s.ctas_per_sm > 0) per_sm = s.ctas_per_sm;
+    const int grid = std::max(1, std::min(ntiles, std::max(per_sm, 1) * num_sms));
+    kern<<<grid, s.threads, smem, st>>>(frames, nframes, ntiles, max_range, head, status);
+    return cudaGetLastError();
+}
+
 template <int B, bool SIMPL, int NST, bool EVAL>
 cudaError_t launch_t(const FrameDev* frames, int nframes, int ntiles, int max_range, const Shape& s, int* head,
                      unsigned* status, int num_sms, cudaStream_t st)
 {
-    const size_t smem = dcds_smem_bytes(B, max_range, s);
     auto kern = dcds_kernel<B, SIMPL, NST, EVAL>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    const size_t smem = dcds_smem_bytes(B, max_range, s, false);
+    int per_sm = 0;
+    cudaError_t e = occupancy(kern, smem, s.threads, per_sm);
     if (e != cudaSuccess) return e;
-    int per_sm = s.ctas_per_sm;
-    if (per_sm <= 0) {
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, s.threads, smem);
-        if (e != cudaSuccess) return e;
+    if constexpr (B == 8 && !EVAL) {
+        // the visited-box variant where it fits more CTAs per SM
+        auto kbox = dcds_box_kernel<SIMPL, NST>;
+        const size_t smem_box = dcds_smem_bytes(B, max_range, s, true);
+        int per_sm_box = 0;
+        if (occupancy(kbox, smem_box, s.threads, per_sm_box) != cudaSuccess) {
+            (void)cudaGetLastError();  // the bitmap variant runs instead
+        } else if (per_sm_box > per_sm) {
+            return launch_k(kbox, smem_box, per_sm_box, frames, nframes, ntiles, max_range, s, head, status, num_sms,
+                            st);
+        }
     }
-    int grid = std::max(1, std::min(ntiles, std::max(per_sm, 1) * num_sms));
-    kern<<<grid, s.threads, smem, st>>>(frames, nframes, ntiles, max_range, head, status);
-    return cudaGetLastError();
+    return launch_k(kern, smem, per_sm, frames, nframes, ntiles, max_range, s, head, status, num_sms, st);
 }
 
 template <int B, bool SIMPL>
@@ -738,40 +849,20 @@ cudaError_t launch_b(const FrameDev* frames, int nframes, int ntiles, int max_ra
     return launch_t<B, SIMPL, 1, false>(frames, nframes, ntiles, max_range, s, head, status, num_sms, st);
 }
 
-template <int B, bool SIMPL, int NST>
-int occupancy_t(int max_range, const Shape& s)
-{
-    int per_sm = 0;
-    const size_t smem = dcds_smem_bytes(B, max_range, s);
-    auto kern = dcds_kernel<B, SIMPL, NST, false>;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
-        cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared) !=
-            cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, s.threads, smem) != cudaSuccess)
-        return 0;
-    return per_sm;
-}
-
 }  // namespace
 
-size_t dcds_smem_bytes(int block, int max_range, const Shape& s)
+size_t dcds_smem_bytes(int block, int max_range, const Shape& s, bool box)
 {
     const int nst = s.stages == 2 ? 2 : 1;
     const int stage = win_bytes_max(max_range, kDcdsTileH) + kTile * kDcdsTileH;
     const int nmb = (kTile / block) * (kDcdsTileH / block);
     const int side = 2 * max_range + 1;
     const int nwb = (side * side + 31) / 32;
-    return 128 + (size_t)nst * stage + (size_t)nmb * 8 + (size_t)(s.threads / dcds_lanes_per_block(block)) * nwb * 4;
-}
-
-int dcds_ctas_per_sm(int block, int max_range, bool simplified, const Shape& s)
-{
-    const bool two = s.stages == 2;
-    if (block == 16)
-        return simplified ? (two ? occupancy_t<16, true, 2>(max_range, s) : occupancy_t<16, true, 1>(max_range, s))
-                          : (two ? occupancy_t<16, false, 2>(max_range, s) : occupancy_t<16, false, 1>(max_range, s));
-    return simplified ? (two ? occupancy_t<8, true, 2>(max_range, s) : occupancy_t<8, true, 1>(max_range, s))
-                      : (two ? occupancy_t<8, false, 2>(max_range, s) : occupancy_t<8, false, 1>(max_range, s));
+    const size_t groups = (size_t)(s.threads / dcds_lanes_per_block(block));
+    const size_t visited = box ? groups * kBoxWords * 4 + (size_t)(32 / dcds_lanes_per_block(block)) * nwb * 4 +
+                                     (size_t)nmb * 4
+                               : groups * nwb * 4;
+    return 128 + (size_t)nst * stage + (size_t)nmb * 8 + visited;
 }
 
 cudaError_t dcds_preload()
@@ -781,6 +872,8 @@ cudaError_t dcds_preload()
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, dcds_kernel<16, true, 1, false>);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, dcds_kernel<8, false, 1, false>);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, dcds_kernel<8, true, 1, false>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, dcds_box_kernel<false, 1>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, dcds_box_kernel<true, 1>);
     return e;
 }
 

@@ -148,8 +148,8 @@ constexpr int kSadVariant = ME_SAD_VARIANT;
 cudaError_t launch_dcds(const FrameDev* frames, int nframes, int ntiles, int block, int max_range,
                         bool simplified, const Shape& s, int* head, unsigned* status, int num_sms,
                         cudaStream_t st, bool eval = false);
-size_t dcds_smem_bytes(int block, int max_range, const Shape& s);
-int dcds_ctas_per_sm(int block, int max_range, bool simplified, const Shape& s);
+// dynamic shared memory of a DCDS launch; box: the 8x8 visited-box variant
+size_t dcds_smem_bytes(int block, int max_range, const Shape& s, bool box = false);
 // Load (under lazy module loading) the one-stage search-only DCDS kernels
 // for both block sizes and both variants, without launching them.
 cudaError_t dcds_preload();

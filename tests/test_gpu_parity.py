@@ -176,22 +176,27 @@ def smooth_pair(h, w, sx, sy, margin=48):
 @pytest.mark.parametrize("B", [8, 16])
 @pytest.mark.parametrize("algo", ["dcds", "dcds_s"])
 def test_long_diamond_paths(ctx, B, algo):
-    """Long search paths, bit-exact: 8x8 blocks keep their visited points in a
-    box of +-7 around the HCSP winner and send a block whose path leaves it
-    to the overflow pass; here about half of them do (final MVs of 12 and
-    more).  Two pairs in one batch (the overflow list is per tile), and the
-    same search with the Sec. IV sums fused."""
+    """Long search paths, bit-exact: 8x8 blocks at +-32 (256 threads, where
+    the launcher takes the visited-box variant) keep their visited points in
+    a box of displacements -16 .. 15 and send a block whose path leaves it to
+    the overflow pass, which searches it again with +-R bitmaps; a block
+    whose final MV lies outside the box has been through it (149 of the 736
+    here, with many more that left the box and came back).  Two pairs in
+    one batch (the overflow list is per tile), and the same search with the
+    Sec. IV sums fused."""
     pairs = [smooth_pair(128, 176, 13, -9), smooth_pair(96, 256, -17, 6)]
     keep, descs = _batch(ctx, pairs, B, algo, [32, 32])
     ctx.me_estimate_batch(descs, B, algo)
     torch.cuda.synchronize()
-    far = 0
+    far = outside = 0
     for (cur, ref), (c, r, mv, sad, nsp) in zip(pairs, keep):
         got = _host(mv, sad, nsp)
         want = oracle_search(cur, ref, B, 32, algo)
         assert_same(got, want, f"{algo} B{B}")
         far += int((np.abs(got[0]).max(1) >= 12).sum())
+        outside += int(((got[0] < -16) | (got[0] > 15)).any(1).sum())
     assert far > 20, far
+    assert outside > 20, outside
     # fused: the same fields, and sums equal to the oracle's measures of them
     keep2, descs2 = _batch(ctx, pairs, B, algo, [32, 32])
     fs = [_dev(oracle.fs(cur, ref, B, 32)[0]) for cur, ref in pairs]
