@@ -429,8 +429,9 @@ __device__ __forceinline__ void dcds_tiles(const FrameDev* __restrict__ frames, 
         // A group is LPB lanes: 2 for 16x16 blocks (a warp serves 16 blocks per
         // round, so a round's control costs half of what 4-lane groups pay per
         // block), 4 for 8x8 blocks.  The pass runs over the ring (list null)
-        // or, for 8x8 blocks, over the ring entries of the blocks that left
-        // their visited box (FULLM: +-R bitmaps, warp 0 only).
+        // with +-R bitmaps (FULLM) or, in the box variant, with visited boxes;
+        // the box variant then runs it again over the ring entries of the
+        // blocks that left their box (list; FULLM, warp 0 only).
         auto rounds = [&](const int* list, int nlist, int* next, auto full_c) {
             constexpr bool FULLM = decltype(full_c)::value;
             constexpr unsigned GMASK = (1u << LPB) - 1u;
